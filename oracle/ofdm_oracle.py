@@ -1,0 +1,368 @@
+"""FP64 CPU oracle of the OFDM monostatic radar receive chain.
+
+Delamou, Noubir, Dang, Amhoud, "An Efficient OFDM-Based Monostatic Radar
+Design for Multitarget Detection" (arXiv 2209.03883).
+
+TEST INFRASTRUCTURE ONLY.  This module is the slow, plain definition that the
+CUDA path is checked against.  Only the test suite, the smoke check and the
+CPU-baseline leg of the benchmark may import it; the product library never
+does, and the two share no code, tables or constants.
+
+Conventions
+-----------
+* Matrices follow the paper's orientation: a frame is an N x M array indexed
+  [k, l], k = subcarrier (row), l = OFDM symbol (column) (Sec. II-B, Eq. (16)).
+* Everything is complex128 / float64.  DFTs are explicit O(n^2) matrices built
+  from exact integer index products, never an FFT.
+* The range-Doppler map is indexed [r, c] with r = 0..N'-1 the range bin and
+  c = s + M'/2 the column of Doppler bin s in [-M'/2, M'/2) (Eq. (17)).
+
+Readings of the paper taken where it is silent or garbled (each also listed
+in the design notes):
+  A  the radar divides by the *precoded* grid X_p = Z_m A / sqrt(N).
+  B  DFT-CE: IDFT carries 1/N, the DFT back carries no factor (Eqs. (20)-(22)).
+  C  Z_m is N x N, so the ZC length is L = N^2; scaled by 1/sqrt(N) (unitary).
+  D  Eq. (17): R' -> M', S' -> N'; Eq. (19): T_0 -> T_s, r <-> s swapped.
+  E  periodic (DFT-even) Hann / Hamming windows, separable w_k * w_l.
+  F  threshold eta = -sigma_P^2 ln(P_fa) (the printed sign is garbled).
+  G  detections are 8-neighbour local maxima (circular in r and s), ordered by
+     power descending then map index ascending.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+C_LIGHT = 3.0e8  # speed of light used by the paper, Table I
+
+WINDOW_RECT, WINDOW_HANN, WINDOW_HAMMING = 0, 1, 2
+DETECT_TOPK, DETECT_THRESHOLD = 0, 1
+
+STATUS_ZERO_X = 1      # a precoded transmit cell was exactly zero
+STATUS_NONFINITE = 2   # a non-finite input value was seen
+STATUS_OVERFLOW = 4    # threshold mode found more targets than max_targets
+STATUS_FEW_PEAKS = 8   # top-K mode found fewer than K local maxima
+
+
+# --------------------------------------------------------------------------
+# Zadoff-Chu sequence and matrix (Sec. III-B, Eqs. (23)-(24))
+# --------------------------------------------------------------------------
+def zc_sequence(L: int, r: int, q: int = 0) -> np.ndarray:
+    """Zadoff-Chu sequence of length L with root r and shift q, Eq. (23).
+
+    Even L:  exp(j 2 pi r / L * (k^2 / 2 + q k))  = exp(j pi m / L),
+             m = r (k^2 + 2 q k) mod 2L.
+    Odd L:   exp(j 2 pi r / L * (k (k + 1) / 2 + q k)) = exp(j 2 pi m / L),
+             m = r (k (k + 1) / 2 + q k) mod L.
+    The phase index m is reduced with exact int64 arithmetic, so the phase
+    is exact before the one final exp.
+    """
+    if L <= 0:
+        raise ValueError("L must be positive")
+    if math.gcd(r, L) != 1:
+        raise ValueError("ZC root must be coprime to L")
+    if L >= 1 << 26:
+        raise ValueError("L too large for exact int64 phase reduction")
+    k = np.arange(L, dtype=np.int64)
+    if L % 2 == 0:
+        mod = 2 * L
+        base = (k * k + 2 * (q % mod) * k) % mod          # k^2 + 2qk  (mod 2L)
+        m = (base * (r % mod)) % mod                         # < 2^26 * 2^26
+        return np.exp(1j * np.pi * m / L)
+    mod = L
+    base = (k * (k + 1) // 2 + (q % mod) * k) % mod        # k(k+1)/2 + qk  (mod L)
+    m = (base * (r % mod)) % mod
+    return np.exp(2j * np.pi * m / L)
+
+
+def zc_matrix(N: int, r: int, q: int = 0) -> np.ndarray:
+    """Square ZC matrix Z_m(i, j) = Z_seq(i D + j), D = sqrt(L), Eq. (24).
+
+    Reading C: Z_m left-multiplies the N x M symbol grid, so D = N, L = N^2.
+    """
+    seq = zc_sequence(N * N, r, q)
+    # Z_m(i, j) = seq[i N + j]: row-major reshape.
+    return seq.reshape(N, N).copy()
+
+
+def zc_precode(A: np.ndarray, r: int, q: int = 0, inverse: bool = False) -> np.ndarray:
+    """ZC precoding A_p = Z_m A (Sec. III-B) and its undoing by Z_m^{-1}.
+
+    Scaled by 1/sqrt(N) so that the transform is unitary (reading C); the
+    inverse is then the conjugate transpose.  r = 0 means "no precoding".
+    """
+    A = np.asarray(A, dtype=np.complex128)
+    if r == 0:
+        return A.copy()
+    N = A.shape[0]
+    U = zc_matrix(N, r, q) / np.sqrt(N)
+    if inverse:
+        return U.conj().T @ A
+    return U @ A
+
+
+# --------------------------------------------------------------------------
+# Radar processing (Sec. II-B.2) and DFT-CE (Sec. III-A)
+# --------------------------------------------------------------------------
+def ls_divide(Y: np.ndarray, X: np.ndarray):
+    """LS spectral division h_{k,l} = y_{k,l} / x_{k,l}, Eq. (16).
+
+    Cells whose transmit value is exactly zero give 0 and are counted.
+    """
+    Y = np.asarray(Y, dtype=np.complex128)
+    X = np.asarray(X, dtype=np.complex128)
+    zero = X == 0
+    F = np.zeros_like(Y)
+    F[~zero] = Y[~zero] / X[~zero]
+    return F, int(zero.sum())
+
+
+def dft_matrix(n: int) -> np.ndarray:
+    """W[a, b] = exp(-j 2 pi a b / n), with a*b reduced mod n exactly."""
+    idx = np.arange(n, dtype=np.int64)
+    prod = np.outer(idx, idx) % n
+    return np.exp(-2j * np.pi * prod / n)
+
+
+def dft_ce(H: np.ndarray, L_cp: int):
+    """DFT channel estimation, Eqs. (20)-(22), applied to every column.
+
+    h = (1/N) W^H H          (IDFT over subcarriers, Eq. (20))
+    h[n] = 0 for n >= L_cp   (keep the CP-long part, Eq. (21))
+    H' = W h                 (DFT back, no factor -- reading B, Eq. (22))
+    Returns (H', h_truncated).
+    """
+    H = np.asarray(H, dtype=np.complex128)
+    N = H.shape[0]
+    if not 1 <= L_cp <= N:
+        raise ValueError("L_cp must be in [1, N]")
+    W = dft_matrix(N)
+    h = (W.conj() @ H) / N
+    h[L_cp:, :] = 0
+    return W @ h, h
+
+
+def window(n: int, kind: int) -> np.ndarray:
+    """Periodic window of length n (reading E): rect, Hann or Hamming (Sec. IV)."""
+    k = np.arange(n, dtype=np.float64)
+    if kind == WINDOW_RECT:
+        return np.ones(n)
+    if kind == WINDOW_HANN:
+        return 0.5 - 0.5 * np.cos(2 * np.pi * k / n)
+    if kind == WINDOW_HAMMING:
+        return 0.54 - 0.46 * np.cos(2 * np.pi * k / n)
+    raise ValueError("unknown window")
+
+
+def range_profile(Hd: np.ndarray, w_k: np.ndarray, N_pad: int | None = None) -> np.ndarray:
+    """Range transform of Eq. (17) alone: g[r, l] = sum_k w_k H'[k, l] e^{+j2pi k r / N'}."""
+    N, M = Hd.shape
+    N_pad = N if N_pad is None else N_pad
+    G = np.zeros((N_pad, M), dtype=np.complex128)
+    G[:N] = w_k[:, None] * Hd
+    return dft_matrix(N_pad).conj() @ G
+
+
+def periodogram(Hd: np.ndarray, w_k: np.ndarray, w_l: np.ndarray,
+                N_pad: int | None = None, M_pad: int | None = None) -> np.ndarray:
+    """Windowed 2D periodogram, Eq. (17), as an [r, c] map.
+
+    P(s, r) = 1/(NM) |sum_k (sum_l h_{k,l} w_{k,l} e^{-j2pi l s/M'}) e^{+j2pi k r/N'}|^2
+    with w_{k,l} = w_k w_l, h zero-padded to N' x M', and the Doppler axis
+    reordered so that column c holds s = c - M'/2 (reading D).
+    """
+    N, M = Hd.shape
+    N_pad = N if N_pad is None else N_pad
+    M_pad = M if M_pad is None else M_pad
+    if N_pad < N or M_pad < M:
+        raise ValueError("padding must not shrink the grid")
+    G = np.zeros((N_pad, M_pad), dtype=np.complex128)
+    G[:N, :M] = np.outer(w_k, w_l) * Hd
+    D = G @ dft_matrix(M_pad).T            # Doppler DFT over l  (e^{-j...})
+    R = dft_matrix(N_pad).conj() @ D       # range IDFT over k  (e^{+j...}), no 1/N'
+    P = np.abs(R) ** 2 / (N * M)
+    out = np.empty_like(P)
+    half = M_pad // 2
+    for c in range(M_pad):
+        s = c - half
+        out[:, c] = P[:, s % M_pad]
+    return out
+
+
+# --------------------------------------------------------------------------
+# Detection (Eqs. (18)-(19)) -- reading F and G
+# --------------------------------------------------------------------------
+def local_maxima(P: np.ndarray) -> np.ndarray:
+    """8-neighbour local maxima of an [r, c] map, circular in both axes.
+
+    A cell is a local maximum when P > 0 and, against every distinct
+    neighbour n, P > P[n] or (P == P[n] and its flat index is smaller).
+    """
+    P = np.asarray(P)
+    R, C = P.shape
+    idx = np.arange(R * C, dtype=np.int64).reshape(R, C)
+    ok = P > 0
+    for dr in (-1, 0, 1):
+        for dc in (-1, 0, 1):
+            if dr == 0 and dc == 0:
+                continue
+            Pn = np.roll(P, (-dr, -dc), axis=(0, 1))
+            In = np.roll(idx, (-dr, -dc), axis=(0, 1))
+            same = In == idx
+            ok &= same | (P > Pn) | ((P == Pn) & (idx < In))
+    return ok
+
+
+def support_rows(N: int, L_cp: int, window_kind: int) -> np.ndarray:
+    """Range rows that can be non-zero after DFT-CE with N' = N (Eqs. (17), (21)).
+
+    The truncated taps occupy r < L_cp; a periodic Hann/Hamming window over k
+    spreads each tap to its two circular neighbours.
+    """
+    if L_cp >= N:
+        return np.arange(N)
+    if window_kind == WINDOW_RECT:
+        return np.arange(L_cp)
+    return np.array([N - 1] + list(range(L_cp + 1)))
+
+
+def threshold(P: np.ndarray, rows: np.ndarray, pfa: float, noise_var: float) -> np.floating:
+    """Detection threshold eta = -sigma_P^2 ln(P_fa) of Eq. (18) (reading F).
+
+    sigma_P^2 is the caller's noise level when noise_var > 0, otherwise the
+    lower median of P over the given rows divided by ln 2 (the median of an
+    exponential variable is its mean times ln 2).  The arithmetic is done in
+    the map's own precision, so that a float32 map gives the float32 eta.
+    """
+    dt = P.dtype.type
+    if noise_var > 0:
+        return dt(noise_var) * dt(-math.log(pfa))
+    vals = np.sort(P[rows, :].ravel())
+    med = vals[(vals.size - 1) // 2]
+    return dt(med) * dt(-math.log(pfa) / math.log(2.0))
+
+
+@dataclass
+class Detection:
+    r: np.ndarray        # range bin 0..N'-1
+    s: np.ndarray        # Doppler bin -M'/2..M'/2-1
+    power: np.ndarray
+    status: int = 0
+    next_power: float = 0.0   # power of the first candidate not reported
+    count: int = 0            # candidates found before truncation
+
+
+def detect(P: np.ndarray, mode: int, max_targets: int, eta=None) -> Detection:
+    """Peak picking on the map (Eq. (18)).
+
+    mode DETECT_TOPK: the max_targets strongest local maxima.
+    mode DETECT_THRESHOLD: local maxima with P >= eta, strongest first,
+    at most max_targets of them.
+    Order: power descending, then flat map index ascending (reading G).
+    """
+    R, C = P.shape
+    lm = local_maxima(P)
+    if mode == DETECT_THRESHOLD:
+        lm &= P >= eta
+    flat = np.flatnonzero(lm.ravel())
+    vals = P.ravel()[flat]
+    order = np.lexsort((flat, -vals.astype(np.float64)))
+    flat, vals = flat[order], vals[order]
+    status = 0
+    if mode == DETECT_TOPK and flat.size < max_targets:
+        status |= STATUS_FEW_PEAKS
+    if mode == DETECT_THRESHOLD and flat.size > max_targets:
+        status |= STATUS_OVERFLOW
+    nxt = float(vals[max_targets]) if flat.size > max_targets else 0.0
+    keep = flat[:max_targets]
+    r = keep // C
+    s = keep % C - C // 2
+    return Detection(r=r, s=s, power=vals[:max_targets], status=status,
+                     next_power=nxt, count=int(flat.size))
+
+
+def symbol_time(N: int, n_cp: int, df_hz: float) -> float:
+    """T_s = T + T_cp = (N + N_cp) / (N df), with T = 1/df (Sec. II-B)."""
+    return (N + n_cp) / (N * df_hz)
+
+
+def estimates(r, s, N_pad: int, M_pad: int, df_hz: float, fc_hz: float, Ts: float):
+    """Eq. (19) (reading D): d = c r / (2 N' df), v = c s / (2 fc M' T_s)."""
+    r = np.asarray(r, dtype=np.float64)
+    s = np.asarray(s, dtype=np.float64)
+    return C_LIGHT * r / (2 * N_pad * df_hz), C_LIGHT * s / (2 * fc_hz * M_pad * Ts)
+
+
+def resolution(N: int, M: int, df_hz: float, fc_hz: float, Ts: float):
+    """Eq. (15): range and velocity resolution."""
+    return C_LIGHT / (2 * N * df_hz), C_LIGHT / (2 * M * fc_hz * Ts)
+
+
+def unambiguous(df_hz: float, fc_hz: float, Ts: float):
+    """Eq. (14): unambiguous range and velocity."""
+    return C_LIGHT / (2 * df_hz), C_LIGHT / (2 * fc_hz * Ts)
+
+
+# --------------------------------------------------------------------------
+# Whole chain
+# --------------------------------------------------------------------------
+@dataclass
+class Params:
+    N: int
+    M: int
+    L_cp: int
+    zc_root: int = 1
+    zc_q: int = 0
+    x_is_precoded: bool = False
+    window: int = WINDOW_HANN
+    detect_mode: int = DETECT_TOPK
+    max_targets: int = 8
+    pfa: float = 1e-2
+    noise_var: float = -1.0
+    N_pad: int = 0
+    M_pad: int = 0
+    n_cp: int = 0              # physical CP length for T_s; 0 -> L_cp
+    fc_hz: float = 77e9
+    df_hz: float = 240e3
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def Np(self):
+        return self.N_pad or self.N
+
+    @property
+    def Mp(self):
+        return self.M_pad or self.M
+
+
+def process(Y: np.ndarray, A: np.ndarray, p: Params) -> dict:
+    """The receive chain on one N x M frame, in the paper's order.
+
+    ZC precoding of the known grid (Sec. III-B) -> LS division (Eq. (16)) ->
+    DFT-CE (Eqs. (20)-(22)) -> windowed periodogram (Eq. (17)) ->
+    detection (Eq. (18)) -> range / velocity estimates (Eq. (19)).
+    """
+    Y = np.asarray(Y, dtype=np.complex128)
+    A = np.asarray(A, dtype=np.complex128)
+    if p.zc_root and not p.x_is_precoded:
+        Xp = zc_precode(A, p.zc_root, p.zc_q)
+    else:
+        Xp = A.copy()
+    F, nzero = ls_divide(Y, Xp)
+    Hd, h = dft_ce(F, p.L_cp)
+    w_k = window(p.N, p.window)
+    w_l = window(p.M, p.window)
+    P = periodogram(Hd, w_k, w_l, p.Np, p.Mp)
+    rows = support_rows(p.N, p.L_cp, p.window) if p.Np == p.N else np.arange(p.Np)
+    eta = None
+    if p.detect_mode == DETECT_THRESHOLD:
+        eta = threshold(P, rows, p.pfa, p.noise_var)
+    det = detect(P, p.detect_mode, p.max_targets, eta)
+    if nzero:
+        det.status |= STATUS_ZERO_X
+    Ts = symbol_time(p.N, p.n_cp or p.L_cp, p.df_hz)
+    d, v = estimates(det.r, det.s, p.Np, p.Mp, p.df_hz, p.fc_hz, Ts)
+    return dict(Xp=Xp, F=F, h=h, Hd=Hd, P=P, det=det, eta=eta, d=d, v=v,
+                g=range_profile(Hd, w_k), rows=rows)

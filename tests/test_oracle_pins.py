@@ -1,0 +1,331 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each check is independent of the oracle's own formulas: closed forms,
+invariants (CAZAC, unitarity, Parseval), brute force on tiny inputs, a
+library routine on a special case, a time-domain simulation of the OFDM
+link, and the numbers printed in the paper's Table I.  The last test plants
+mistakes in the oracle and checks that these pins catch each one.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import ofdm_synth as syn
+from oracle import ofdm_oracle as o
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- ZC (Sec. III-B)
+def _periodic_autocorr(x):
+    L = x.size
+    return np.array([np.vdot(x, np.roll(x, -tau)) for tau in range(L)])
+
+
+def check_zc_cazac(L, r, q=0):
+    z = o.zc_sequence(L, r, q)
+    assert np.allclose(np.abs(z), 1.0, atol=1e-12)
+    ac = _periodic_autocorr(z)
+    assert abs(ac[0] - L) < 1e-9 * L
+    assert np.max(np.abs(ac[1:])) < 1e-8 * L, "ZC periodic autocorrelation must vanish off zero lag"
+
+
+@pytest.mark.parametrize("L,r,q", [(16, 1, 0), (64, 3, 0), (64, 5, 2), (1024, 1, 0),
+                                   (1024, 7, 3), (13, 1, 0), (63, 2, 1), (139, 5, 0)])
+def test_zc_cazac(L, r, q):
+    check_zc_cazac(L, r, q)
+
+
+def check_zc_unitary(N, r, q=0):
+    Z = o.zc_matrix(N, r, q)
+    assert np.allclose(Z @ Z.conj().T, N * np.eye(N), atol=1e-9 * N)
+
+
+@pytest.mark.parametrize("N,r,q", [(4, 1, 0), (8, 3, 0), (16, 5, 1), (64, 1, 0), (64, 7, 2)])
+def test_zc_matrix_unitary(N, r, q):
+    check_zc_unitary(N, r, q)
+
+
+def test_zc_precode_roundtrip_and_norm():
+    rng = np.random.default_rng(0)
+    A = rng.standard_normal((32, 5)) + 1j * rng.standard_normal((32, 5))
+    Xp = o.zc_precode(A, 3, 1)
+    assert np.allclose(np.linalg.norm(Xp, axis=0), np.linalg.norm(A, axis=0))
+    assert np.allclose(o.zc_precode(Xp, 3, 1, inverse=True), A)
+
+
+def test_zc_matrix_entries_bruteforce():
+    # Z_m(i, j) is the (iN + j)-th sequence entry; the sequence phase is
+    # checked against a pure-python evaluation with fractions of 2*pi.
+    from fractions import Fraction
+    N, r, q = 4, 3, 1
+    Z = o.zc_matrix(N, r, q)
+    L = N * N
+    for i in range(N):
+        for j in range(N):
+            k = i * N + j
+            ph = Fraction(r, L) * (Fraction(k * k, 2) + q * k)   # turns (units of 2 pi)
+            ph -= math.floor(ph)
+            want = complex(math.cos(2 * math.pi * ph), math.sin(2 * math.pi * ph))
+            assert abs(Z[i, j] - want) < 1e-12
+
+
+# ---------------------------------------------------------------- DFTs
+def _dft_loops(x, sign):
+    n = len(x)
+    return [sum(x[k] * complex(math.cos(sign * 2 * math.pi * j * k / n),
+                               math.sin(sign * 2 * math.pi * j * k / n)) for k in range(n))
+            for j in range(n)]
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 8, 16])
+def test_dft_matrix_bruteforce(n):
+    rng = np.random.default_rng(n)
+    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    W = o.dft_matrix(n)
+    assert np.allclose(W @ x, _dft_loops(list(x), -1), atol=1e-12)
+    assert np.allclose(W.conj() @ x, _dft_loops(list(x), +1), atol=1e-12)
+
+
+def test_dft_matrix_matches_library_fft():
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal(256) + 1j * rng.standard_normal(256)
+    assert np.allclose(o.dft_matrix(256) @ x, np.fft.fft(x), atol=1e-9)
+
+
+# ---------------------------------------------------------------- DFT-CE (Sec. III-A)
+def check_dft_ce_identity():
+    rng = np.random.default_rng(2)
+    H = rng.standard_normal((32, 4)) + 1j * rng.standard_normal((32, 4))
+    Hd, _ = o.dft_ce(H, 32)
+    assert np.allclose(Hd, H, atol=1e-12), "DFT-CE with L_cp = N is the identity"
+
+
+def test_dft_ce_identity():
+    check_dft_ce_identity()
+
+
+def test_dft_ce_keeps_on_grid_targets_in_cp():
+    N, M = 64, 8
+    H = syn.channel([3.0, 11.0], [1.0, -2.0], [1.0, 0.5j], N, M)
+    Hd, h = o.dft_ce(H, 16)
+    assert np.allclose(Hd, H, atol=1e-12)
+    # a target beyond the CP part is removed entirely
+    H2 = syn.channel([20.0], [0.0], [1.0], N, M)
+    Hd2, _ = o.dft_ce(H2, 16)
+    assert np.max(np.abs(Hd2)) < 1e-12
+
+
+# ---------------------------------------------------------------- periodogram (Eq. (17))
+def _noiseless_point(N, M, L_cp, rho, nu, b, zc_root, window):
+    syn_rng = np.random.default_rng(7)
+    A = syn.qam_symbols(syn_rng, (N, M), 16)
+    Xp = o.zc_precode(A, zc_root) if zc_root else A
+    H = syn.channel([rho], [nu], [b], N, M)
+    Y = Xp * H
+    p = o.Params(N=N, M=M, L_cp=L_cp, zc_root=zc_root, window=window, max_targets=1)
+    return o.process(Y, A, p)
+
+
+def check_point_target_rect(N=64, M=16, rho=5, nu=-3, zc_root=1):
+    out = _noiseless_point(N, M, 8, rho, nu, 0.8 * np.exp(0.7j), zc_root, o.WINDOW_RECT)
+    P = out["P"]
+    c = nu + M // 2
+    assert abs(P[rho, c] - N * M * 0.64) < 1e-9 * N * M
+    Q = P.copy()
+    Q[rho, c] = 0
+    assert Q.max() < 1e-18 * N * M
+    det = out["det"]
+    assert (int(det.r[0]), int(det.s[0])) == (rho, nu)
+
+
+@pytest.mark.parametrize("zc_root", [0, 1, 3])
+def test_point_target_rect_closed_form(zc_root):
+    check_point_target_rect(zc_root=zc_root)
+
+
+def check_point_target_hann(N=64, M=32, rho=4, nu=6, window=o.WINDOW_HANN):
+    out = _noiseless_point(N, M, 16, rho, nu, 1.0, 1, window)
+    P = out["P"]
+    c = nu + M // 2
+    c0, c1 = (0.5, 0.25) if window == o.WINDOW_HANN else (0.54, 0.23)
+    want = np.zeros_like(P)
+    for dr, wr in ((-1, c1), (0, c0), (1, c1)):
+        for dc, wc in ((-1, c1), (0, c0), (1, c1)):
+            want[(rho + dr) % N, (c + dc) % M] = N * M * (wr * wc) ** 2
+    assert np.allclose(P, want, atol=1e-9 * N * M)
+
+
+@pytest.mark.parametrize("window", [o.WINDOW_HANN, o.WINDOW_HAMMING])
+def test_point_target_window_closed_form(window):
+    check_point_target_hann(window=window)
+
+
+def test_parseval():
+    rng = np.random.default_rng(3)
+    N, M = 32, 16
+    Hd = rng.standard_normal((N, M)) + 1j * rng.standard_normal((N, M))
+    wk, wl = o.window(N, o.WINDOW_HANN), o.window(M, o.WINDOW_HANN)
+    P = o.periodogram(Hd, wk, wl)
+    G = np.outer(wk, wl) * Hd
+    assert abs(P.sum() - np.sum(np.abs(G) ** 2)) < 1e-9 * P.sum()
+
+
+def test_periodogram_bruteforce_tiny():
+    rng = np.random.default_rng(4)
+    N, M, Np, Mp = 4, 4, 8, 4
+    h = rng.standard_normal((N, M)) + 1j * rng.standard_normal((N, M))
+    wk, wl = o.window(N, o.WINDOW_HAMMING), o.window(M, o.WINDOW_HAMMING)
+    P = o.periodogram(h, wk, wl, Np, Mp)
+    for r in range(Np):
+        for s in range(-Mp // 2, Mp // 2):
+            acc = 0j
+            for k in range(N):
+                inner = 0j
+                for l in range(M):
+                    inner += h[k, l] * wk[k] * wl[l] * complex(
+                        math.cos(-2 * math.pi * l * s / Mp), math.sin(-2 * math.pi * l * s / Mp))
+                acc += inner * complex(math.cos(2 * math.pi * k * r / Np),
+                                       math.sin(2 * math.pi * k * r / Np))
+            assert abs(P[r, s + Mp // 2] - abs(acc) ** 2 / (N * M)) < 1e-10
+
+
+def test_zero_padding_interpolates():
+    rng = np.random.default_rng(5)
+    N, M = 16, 8
+    Hd = rng.standard_normal((N, M)) + 1j * rng.standard_normal((N, M))
+    wk, wl = o.window(N, o.WINDOW_HANN), o.window(M, o.WINDOW_HANN)
+    P = o.periodogram(Hd, wk, wl)
+    P2 = o.periodogram(Hd, wk, wl, 2 * N, 2 * M)
+    for r in range(N):
+        for s in range(-M // 2, M // 2):
+            assert abs(P2[2 * r, 2 * s + M] - P[r, s + M // 2]) < 1e-9 * (1 + P.max())
+
+
+# ---------------------------------------------------------------- detection (Eqs. (18)-(19))
+def _local_max_loops(P):
+    R, C = P.shape
+    out = np.zeros_like(P, dtype=bool)
+    for r in range(R):
+        for c in range(C):
+            if not P[r, c] > 0:
+                continue
+            ok = True
+            me = r * C + c
+            for dr in (-1, 0, 1):
+                for dc in (-1, 0, 1):
+                    rr, cc = (r + dr) % R, (c + dc) % C
+                    other = rr * C + cc
+                    if other == me:
+                        continue
+                    if P[rr, cc] > P[r, c] or (P[rr, cc] == P[r, c] and other < me):
+                        ok = False
+            out[r, c] = ok
+    return out
+
+
+@pytest.mark.parametrize("shape,seed", [((8, 8), 0), ((5, 7), 1), ((2, 6), 2), ((16, 4), 3)])
+def test_local_maxima_bruteforce(shape, seed):
+    rng = np.random.default_rng(seed)
+    P = np.round(rng.random(shape) * 4) / 4      # many exact ties
+    P[0, 0] = 0
+    assert np.array_equal(o.local_maxima(P), _local_max_loops(P))
+
+
+def test_detect_order_ties_and_status():
+    P = np.zeros((6, 6))
+    P[1, 1] = P[4, 4] = 5.0       # tie: smaller flat index first
+    P[1, 4] = 7.0
+    det = o.detect(P, o.DETECT_TOPK, 3)
+    assert list(zip(det.r, det.s)) == [(1, 1), (1, -2), (4, 1)]
+    det = o.detect(P, o.DETECT_TOPK, 5)
+    assert det.status & o.STATUS_FEW_PEAKS and det.r.size == 3
+    det = o.detect(P, o.DETECT_THRESHOLD, 1, eta=5.0)
+    assert det.status & o.STATUS_OVERFLOW and det.count == 3 and det.r.size == 1
+
+
+def test_threshold_float32_lower_median():
+    P = np.array([[4.0, 1.0, 3.0, 2.0]], dtype=np.float32)
+    eta = o.threshold(P, np.array([0]), 1e-2, -1.0)
+    assert eta.dtype == np.float32
+    assert eta == np.float32(2.0) * np.float32(-math.log(1e-2) / math.log(2.0))
+
+
+# ---------------------------------------------------------------- Table I (Eqs. (14)-(15), (19))
+def test_table1_resolutions():
+    g = json.load(open(os.path.join(GOLDEN, "table1.json")))
+    p, pr = g["params"], g["printed"]
+    assert p["N"] * p["df_hz"] == pytest.approx(p["B_hz"])
+    Ts = o.symbol_time(p["N"], p["N_cp"], p["df_hz"])
+    dd, dv = o.resolution(p["N"], p["M"], p["df_hz"], p["fc_hz"], Ts)
+    assert abs(dd - pr["range_resolution_m"]["value"]) < pr["range_resolution_m"]["tol"]
+    assert abs(dv - pr["velocity_resolution_mps"]["value"]) < pr["velocity_resolution_mps"]["tol"]
+    assert abs(p["N_cp"] * dd - pr["max_range_m"]["value"]) < pr["max_range_m"]["tol"]
+    # max range as the CP-limited delay c*T_cp/2 (Eq. (13))
+    Tcp = 0.07 / p["df_hz"]
+    assert abs(o.C_LIGHT * Tcp / 2 - pr["max_range_normal_cp_m"]["value"]) < pr["max_range_normal_cp_m"]["tol"]
+    dun, vun = o.unambiguous(p["df_hz"], p["fc_hz"], Ts)
+    assert dun == pytest.approx(p["N"] * dd) and vun == pytest.approx(p["M"] * dv)
+
+
+def test_detected_bin_to_physics():
+    # A noiseless on-grid target at (rho0, nu0) converts back to rho0*dd, nu0*dv.
+    N, M = 64, 32
+    out = _noiseless_point(N, M, 16, 9, -5, 1.0, 1, o.WINDOW_RECT)
+    Ts = o.symbol_time(N, 16, 240e3)
+    dd, dv = o.resolution(N, M, 240e3, 77e9, Ts)
+    assert out["d"][0] == pytest.approx(9 * dd) and out["v"][0] == pytest.approx(-5 * dv)
+
+
+# ---------------------------------------------------------------- time-domain link (Eqs. (1)-(2), (12))
+def test_time_domain_link_matches_frequency_model():
+    """OFDM modulation with CP, an integer-sample delay and a per-symbol Doppler
+    phase, CP removal and FFT reproduce Y = X * H of the generator's model."""
+    N, M, Ncp = 32, 6, 8
+    rng = np.random.default_rng(6)
+    A = syn.qam_symbols(rng, (N, M), 4)
+    d, nu, b = 5, 1.5, 0.7 * np.exp(0.3j)
+    n = np.arange(N)
+    tx = []
+    for l in range(M):
+        x = np.array([sum(A[k, l] * np.exp(2j * np.pi * nn * k / N) for k in range(N)) for nn in n])
+        tx.append(np.concatenate([x[-Ncp:], x]))          # CP + symbol, Eq. (2)
+    tx = np.concatenate(tx)
+    rx = np.zeros_like(tx)
+    rx[d:] = tx[:-d]                                        # round-trip delay of d samples
+    Y = np.zeros((N, M), dtype=complex)
+    for l in range(M):
+        seg = rx[l * (N + Ncp) + Ncp: (l + 1) * (N + Ncp)] * b * np.exp(2j * np.pi * l * nu / M)
+        Y[:, l] = np.array([sum(seg[nn] * np.exp(-2j * np.pi * nn * k / N) for nn in n)
+                            for k in range(N)]) / N
+    H = syn.channel([d], [nu], [b], N, M)
+    assert np.allclose(Y, A * H, atol=1e-9)
+
+
+# ---------------------------------------------------------------- the pins bite
+MUTATIONS = {
+    "zc_phase_doubled": ("zc_sequence", lambda f: (lambda L, r, q=0: f(L, r, q) ** 2)),
+    "dft_conjugated": ("dft_matrix", lambda f: (lambda n: f(n).conj())),
+    "dft_ce_no_truncation": ("dft_ce", lambda f: (lambda H, L: f(H, H.shape[0]))),
+    "dft_ce_extra_scale": ("dft_ce", lambda f: (lambda H, L: tuple(x / H.shape[0] for x in f(H, L)))),
+    "window_symmetric": ("window", lambda f: (lambda n, k: f(n + 1, k)[:n] if k else f(n, k))),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_catch_planted_mistakes(name, monkeypatch):
+    attr, wrap = MUTATIONS[name]
+    monkeypatch.setattr(o, attr, wrap(getattr(o, attr)))
+    checks = [lambda: check_zc_cazac(64, 3), lambda: check_zc_unitary(16, 3),
+              check_dft_ce_identity, check_point_target_rect, check_point_target_hann,
+              lambda: test_dft_ce_keeps_on_grid_targets_in_cp()]
+    caught = 0
+    for c in checks:
+        try:
+            c()
+        except (AssertionError, ValueError, IndexError):
+            caught += 1
+    assert caught > 0, f"planted mistake {name} went unnoticed"
