@@ -1,0 +1,167 @@
+/*
+ * ofdm_radar.h -- C ABI of the GB300 OFDM monostatic radar receive chain.
+ *
+ * The chain follows Delamou, Noubir, Dang, Amhoud, "An Efficient OFDM-Based
+ * Monostatic Radar Design for Multitarget Detection" (arXiv 2209.03883):
+ * the radar knows the transmitted grid and receives its echo (Sec. II-A), so
+ * every call takes the received grid Y and the known transmit grid X and
+ * returns the range-Doppler map and the detected targets.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Grids are complex64 (interleaved re, im), laid out [frame][l][k]: for each
+ *   frame, M OFDM symbols l of N subcarriers k each, k contiguous.
+ * - Unless a function says "host", every pointer is a DEVICE pointer owned by
+ *   the caller; the plan owns only its tables and workspace.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   Calls are asynchronous on it; no output is valid before the caller syncs.
+ * - Return value: OFDM_OK (0) or a negative OFDM_ERR_* code.  Invalid sizes
+ *   or pointers are rejected before anything is launched.
+ * - No entry point except ofdm_radar_plan_create and the *_host helpers
+ *   allocates device memory.
+ * - Per-frame `status` words carry OFDM_STATUS_* bits.
+ */
+#ifndef OFDM_RADAR_H
+#define OFDM_RADAR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { float re, im; } ofdm_c32;
+
+enum {
+  OFDM_OK = 0,
+  OFDM_ERR_INVALID_ARG = -1,      /* NULL plan/pointer, bad enum, frames out of range */
+  OFDM_ERR_UNSUPPORTED_SIZE = -2, /* N, M, padding or L_cp outside what is built */
+  OFDM_ERR_CUDA = -3,             /* a CUDA runtime call failed (message via strerror) */
+  OFDM_ERR_TIMEOUT = -4,          /* a bounded device wait ran out */
+  OFDM_ERR_NO_MEMORY = -5         /* plan workspace allocation failed */
+};
+
+enum { OFDM_WINDOW_RECT = 0, OFDM_WINDOW_HANN = 1, OFDM_WINDOW_HAMMING = 2 };
+enum { OFDM_DETECT_TOPK = 0, OFDM_DETECT_THRESHOLD = 1 };
+enum { OFDM_PREC_FP32 = 0, OFDM_PREC_SPLIT_BF16 = 1 };
+
+enum {
+  OFDM_STATUS_ZERO_X = 1u,     /* a precoded transmit cell was exactly 0; its F was set to 0 */
+  OFDM_STATUS_NONFINITE = 2u,  /* a non-finite value reached the range profile */
+  OFDM_STATUS_OVERFLOW = 4u,   /* threshold mode: more targets than max_targets */
+  OFDM_STATUS_FEW_PEAKS = 8u   /* top-K mode: fewer than max_targets local maxima */
+};
+
+/* Parameters of one plan.  ofdm_radar_default_params fills the paper's
+ * Table I physical constants and the defaults noted here. */
+typedef struct {
+  int32_t N, M;          /* subcarriers, OFDM symbols; powers of two, N in [64, 4096], M in [16, 1024] */
+  int32_t N_pad, M_pad;  /* N', M' of Eq. (17); 0 -> N, M.  This build: N' = N, M' a power of 2 >= M */
+  int32_t L_cp;          /* DFT-CE taps kept (Eq. (21)), 1..N; L_cp == N is plain LS estimation */
+  int32_t n_cp;          /* physical CP length for T_s in Eq. (19); 0 -> L_cp */
+  int32_t zc_root;       /* ZC root r' of Sec. III-B (odd, so coprime to N^2); 0 -> no precoding */
+  int32_t zc_q;          /* ZC shift q' (default 0) */
+  int32_t x_is_precoded; /* 1 -> X already holds the precoded grid Z_m A / sqrt(N) */
+  int32_t window;        /* OFDM_WINDOW_*, periodic, applied in both dimensions (Eq. (17)) */
+  int32_t detect_mode;   /* OFDM_DETECT_* */
+  int32_t max_targets;   /* 1..32: K of top-K mode, or the cap of threshold mode */
+  int32_t max_frames;    /* workspace capacity: frames per call, >= 1 */
+  int32_t precision;     /* OFDM_PREC_*; OFDM_PREC_FP32 is the plain FP32 FFT path */
+  float pfa;             /* false-alarm probability of Eq. (18), default 1e-2 */
+  float noise_var;       /* per-cell noise power of the map; <= 0 -> estimate from the map */
+  double fc_hz, df_hz;   /* carrier and subcarrier spacing (Table I: 77 GHz, 240 kHz) */
+} ofdm_radar_params;
+
+/* One detection.  r = range bin 0..N'-1, s = Doppler bin -M'/2..M'/2-1,
+ * power = P at that cell, range_m / vel_mps from Eq. (19). */
+typedef struct { int32_t r, s; float power, range_m, vel_mps; } ofdm_target;
+
+typedef struct ofdm_radar_plan ofdm_radar_plan;
+
+/* Fill *p with defaults: window Hann, top-K detection, 8 targets, zc_root 1,
+ * pfa 1e-2, fc 77 GHz, df 240 kHz, max_frames 1.  Sizes are left 0. */
+void ofdm_radar_default_params(ofdm_radar_params* p);
+
+/* Validate *p, build the FP64-derived tables (ZC chirps, twiddles, windows)
+ * and allocate the workspace for max_frames frames on the CURRENT device.
+ * On success *out owns them; release with ofdm_radar_plan_destroy. */
+int ofdm_radar_plan_create(const ofdm_radar_params* p, ofdm_radar_plan** out);
+
+/* Free the plan's device memory (after the caller's work on it finished). */
+void ofdm_radar_plan_destroy(ofdm_radar_plan* plan);
+
+/* Number of range rows that can be non-zero (the DFT-CE support of Eqs.
+ * (17), (21)) and, if rows != NULL, their range bins in workspace order. */
+int ofdm_radar_support_rows(const ofdm_radar_plan* plan, int32_t* rows);
+
+/* Whole receive chain on `frames` frames (Sec. II-B.2, III-A, III-B):
+ * ZC precoding of X, F = Y / X_p (Eq. (16)), DFT-CE (Eqs. (20)-(22)), the
+ * windowed periodogram (Eq. (17)), detection (Eq. (18)) and the estimates of
+ * Eq. (19).
+ *   Y, X         [frames][M][N] complex64 (X = QAM grid, or X_p if x_is_precoded)
+ *   out_map      [frames][N'][M'] float32, column c holds Doppler bin c - M'/2; may be NULL
+ *   out_targets  [frames][max_targets]; may be NULL
+ *   n_targets    [frames] number of valid entries of out_targets; may be NULL
+ *   status       [frames] OFDM_STATUS_* bits; may be NULL
+ * 1 <= frames <= max_frames. */
+int ofdm_radar_process(ofdm_radar_plan* plan, const ofdm_c32* Y, const ofdm_c32* X,
+                       int32_t frames, float* out_map, ofdm_target* out_targets,
+                       int32_t* n_targets, uint32_t* status, void* stream);
+
+/* Same as ofdm_radar_process with HOST buffers (pinned memory gives
+ * asynchronous, overlapped copies).  The plan allocates device staging for
+ * max_frames on the first call; copies run in chunks overlapped with the
+ * kernels on two internal streams ordered after `stream`; the call returns
+ * after everything, copies included, has finished.  NULL outputs are skipped. */
+int ofdm_radar_process_host(ofdm_radar_plan* plan, const ofdm_c32* Y_host,
+                            const ofdm_c32* X_host, int32_t frames, float* map_host,
+                            ofdm_target* targets_host, int32_t* n_targets_host,
+                            uint32_t* status_host, void* stream);
+
+/* ZC precoding of Sec. III-B on every symbol: Xp = Z_m A / sqrt(N)
+ * (inverse = 0) or A = (Z_m A / sqrt(N))^{-1} applied to Xp (inverse = 1,
+ * undoing the precoding as the paper's receiver does with Z_m^{-1}).
+ * in, out: [frames][M][N] complex64; in == out is not allowed. */
+int ofdm_zc_precode(ofdm_radar_plan* plan, const ofdm_c32* in, ofdm_c32* out,
+                    int32_t frames, int32_t inverse, void* stream);
+
+/* Steps a1-a5 only: the windowed range profile
+ *   g[r, l] = sum_k w_k H'[k, l] e^{+j 2 pi k r / N}   (inner range sum of Eq. (17))
+ * on the support rows, written as strip[frames][rows][M] complex64 with rows
+ * in ofdm_radar_support_rows order.  No Doppler window is applied. */
+int ofdm_radar_range_profile(ofdm_radar_plan* plan, const ofdm_c32* Y, const ofdm_c32* X,
+                             int32_t frames, ofdm_c32* strip, void* stream);
+
+/* Step a6 only: Doppler DFT with the window over l, |.|^2 / (N M) (Eq. (17))
+ * of a strip from ofdm_radar_range_profile into out_map (full map, zero rows
+ * included). */
+int ofdm_radar_doppler(ofdm_radar_plan* plan, const ofdm_c32* strip, int32_t frames,
+                       float* out_map, void* stream);
+
+/* Step a7 only: detection (Eq. (18)) and estimates (Eq. (19)) on full maps
+ * [frames][N'][M'] float32 given by the caller. */
+int ofdm_radar_detect(ofdm_radar_plan* plan, const float* map, int32_t frames,
+                      ofdm_target* out_targets, int32_t* n_targets, uint32_t* status,
+                      void* stream);
+
+/* Kernel launches made by the last successful call on this plan. */
+int ofdm_radar_last_launch_count(const ofdm_radar_plan* plan);
+
+/* Per-kernel timing for profiling.  enable = 1 makes every later call on
+ * the plan record a CUDA event pair around each of its kernels on the
+ * launching stream (up to 4096 launches, then recording stops); enable = 0
+ * stops.  ofdm_radar_timing_read waits for the recorded events, writes up to
+ * `n` entries of per-kernel-kind totals (milliseconds) and launch counts in
+ * the order column, zero_rows, doppler, detect, zct, and clears the record.
+ * Returns the number of kinds written. */
+int ofdm_radar_timing_enable(ofdm_radar_plan* plan, int32_t enable);
+int ofdm_radar_timing_read(ofdm_radar_plan* plan, float* total_ms, int32_t* launches, int32_t n);
+
+/* Static description of an error code; for OFDM_ERR_CUDA the last CUDA
+ * error string of the calling thread is appended. */
+const char* ofdm_radar_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OFDM_RADAR_H */

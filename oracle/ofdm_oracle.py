@@ -221,7 +221,8 @@ def support_rows(N: int, L_cp: int, window_kind: int) -> np.ndarray:
     The truncated taps occupy r < L_cp; a periodic Hann/Hamming window over k
     spreads each tap to its two circular neighbours.
     """
-    if L_cp >= N:
+    spread = 0 if window_kind == WINDOW_RECT else 2
+    if L_cp + spread >= N:
         return np.arange(N)
     if window_kind == WINDOW_RECT:
         return np.arange(L_cp)

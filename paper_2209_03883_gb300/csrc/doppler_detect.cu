@@ -1,0 +1,293 @@
+// doppler_detect.cu -- the per-range-row half of the chain (steps a6-a7).
+//
+// doppler_kernel: one warp per (frame, support row r): the window over l,
+//   the M'-point Doppler DFT  D[s] = sum_l w_l g[r, l] e^{-2 pi i l s / M'}
+//   and P = |D|^2 / (N M) (Eq. (17)); column c = s + M'/2 (mod M').  Each row
+//   goes to the compact power strip used by detection and, when asked, to the
+//   full map.
+// zero_rows_kernel: the map rows outside the DFT-CE support are exactly zero.
+// detect_kernel: one CTA per frame: 8-neighbour local maxima (circular in r
+//   and s), optional threshold eta = -sigma^2 ln(P_fa) with sigma^2 from the
+//   lower median (Eq. (18)), top-K by (power desc, map index asc), Eq. (19).
+#include <float.h>
+
+#include "fft.cuh"
+#include "internal.h"
+
+namespace ofdm {
+
+constexpr int kDopWarps = 8;
+
+template <int MP>
+__global__ void __launch_bounds__(32 * kDopWarps)
+doppler_kernel(const float2* __restrict__ strip, float* __restrict__ map, float* __restrict__ pow,
+               DopplerArgs a) {
+  const int warp = threadIdx.x >> 5, t = threadIdx.x & 31;
+  const long task = (long)blockIdx.x * kDopWarps + warp;
+  if (task >= (long)a.frames * a.rows) return;
+  const int f = (int)(task / a.rows);
+  const int ri = (int)(task % a.rows);
+  const int r = (a.row0 + ri) % a.Np;
+  const float2* g = strip + task * a.M;
+  float* prow = pow + task * MP;
+  float* mrow = map ? map + ((long)f * a.Np + r) * MP : nullptr;
+
+  if constexpr (MP <= 32) {
+    // Direct DFT: lane s computes one bin; g[l] is broadcast by shuffles.
+    float2 gl = make_float2(0.f, 0.f);
+    if (t < a.M) gl = cscale(g[t], __ldg(a.wl + t));
+    float2 acc = make_float2(0.f, 0.f);
+    for (int l = 0; l < a.M; ++l) {
+      float2 x;
+      x.x = __shfl_sync(0xffffffffu, gl.x, l);
+      x.y = __shfl_sync(0xffffffffu, gl.y, l);
+      float2 w = __ldg(a.tw + ((l * t) & (MP - 1)));
+      w.y = -w.y;
+      acc = cadd(acc, cmul(x, w));
+    }
+    if (t < MP) {
+      const int c = (t + MP / 2) & (MP - 1);
+      const float p = (acc.x * acc.x + acc.y * acc.y) * a.inv_nm;
+      prow[c] = p;
+      if (mrow) mrow[c] = p;
+    }
+  } else {
+    constexpr int E = MP / 32;
+    extern __shared__ float2 smem[];
+    float2* sm = smem + warp * smem_elems(MP);
+    float2 v[E];
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      const int l = t + 32 * q;
+      v[q] = (l < a.M) ? cscale(g[l], __ldg(a.wl + l)) : make_float2(0.f, 0.f);
+    }
+    group_fft<MP, 32, -1>(v, sm, a.tw, t, 0);
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      const int s = t + 32 * q;
+      const int c = (s + MP / 2) & (MP - 1);
+      const float p = (v[q].x * v[q].x + v[q].y * v[q].y) * a.inv_nm;
+      prow[c] = p;
+      if (mrow) __stcs(mrow + c, p);
+    }
+  }
+}
+
+__global__ void zero_rows_kernel(float* __restrict__ map, int frames, long frame_floats, long z_off,
+                                 long z_floats) {
+  // z_off and z_floats are multiples of 4 floats (M' >= 16).
+  const long per = z_floats / 4;
+  const long total = per * frames;
+  const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+    const long f = i / per, j = i % per;
+    __stcs(reinterpret_cast<float4*>(map + f * frame_floats + z_off) + j, z);
+  }
+}
+
+// ---------------------------------------------------------------- detection
+constexpr int kDetThreads = 1024;
+
+__device__ __forceinline__ uint64_t shfl_u64(uint64_t v, int src) {
+  uint32_t lo = __shfl_sync(0xffffffffu, (uint32_t)v, src);
+  uint32_t hi = __shfl_sync(0xffffffffu, (uint32_t)(v >> 32), src);
+  return ((uint64_t)hi << 32) | lo;
+}
+__device__ __forceinline__ uint64_t shfl_up_u64(uint64_t v) {
+  uint32_t lo = __shfl_up_sync(0xffffffffu, (uint32_t)v, 1);
+  uint32_t hi = __shfl_up_sync(0xffffffffu, (uint32_t)(v >> 32), 1);
+  return ((uint64_t)hi << 32) | lo;
+}
+
+// Insert the lanes' candidate keys into the warp's descending top-K list
+// (lane i holds the i-th best key; 0 = empty).  Keys are unique.
+__device__ __forceinline__ void warp_topk_insert(uint64_t& list, uint64_t key, int K, int lane) {
+  uint64_t thresh = shfl_u64(list, K - 1);
+  unsigned m = __ballot_sync(0xffffffffu, key > thresh);
+  while (m) {
+    const int src = __ffs(m) - 1;
+    m &= m - 1;
+    const uint64_t kk = shfl_u64(key, src);
+    if (kk > thresh) {
+      const int p = __popc(__ballot_sync(0xffffffffu, list > kk));
+      const uint64_t up = shfl_up_u64(list);
+      if (lane > p) list = up;
+      else if (lane == p) list = kk;
+      if (lane >= K) list = 0;
+      thresh = shfl_u64(list, K - 1);
+    }
+  }
+}
+
+__device__ __forceinline__ float det_value(const float* base, const DetectArgs& a, int ri, int c) {
+  const int row = a.compact ? ri : (a.row0 + ri) % a.Np;
+  return base[(long)row * a.Mp + c];
+}
+
+__global__ void __launch_bounds__(kDetThreads)
+detect_kernel(const float* __restrict__ src, ofdm_target* __restrict__ out, int32_t* __restrict__ n_out,
+              uint32_t* __restrict__ status, uint32_t* __restrict__ wstatus, DetectArgs a) {
+  __shared__ uint32_t hist[256];
+  __shared__ uint64_t lists[kDetThreads / 32][32];
+  __shared__ uint32_t s_prefix, s_rank, s_count;
+  const int f = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const float* base = src + (long)f * a.frame_stride;
+  const int n = a.rows * a.Mp;
+
+  float eta = 0.f;
+  if (a.mode == OFDM_DETECT_THRESHOLD) {
+    if (a.use_fixed_eta) {
+      eta = a.eta_fixed;
+    } else {
+      // Lower median (rank (n-1)/2) of P over the scanned rows by an 8-bit
+      // MSB-first radix select on the float bits (P >= 0 sorts as uint).
+      if (tid == 0) { s_prefix = 0; s_rank = (uint32_t)(n - 1) / 2; }
+      uint32_t mask = 0;
+      for (int shift = 24; shift >= 0; shift -= 8) {
+        for (int i = tid; i < 256; i += kDetThreads) hist[i] = 0;
+        __syncthreads();
+        const uint32_t prefix = s_prefix;
+        for (int e = tid; e < n; e += kDetThreads) {
+          const uint32_t u = __float_as_uint(det_value(base, a, e / a.Mp, e % a.Mp));
+          if ((u & mask) == prefix) atomicAdd(&hist[(u >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        if (tid == 0) {
+          uint32_t rank = s_rank, d = 0;
+          for (; d < 255; ++d) {
+            if (hist[d] > rank) break;
+            rank -= hist[d];
+          }
+          s_rank = rank;
+          s_prefix = prefix | (d << shift);
+        }
+        mask |= 255u << shift;
+        __syncthreads();
+      }
+      eta = __fmul_rn(__uint_as_float(s_prefix), a.eta_factor);
+    }
+  }
+
+  if (tid == 0) s_count = 0;
+  __syncthreads();
+
+  uint64_t list = 0;
+  uint32_t count = 0;
+  const int K = a.K;
+  for (int base_e = 0; base_e < n; base_e += kDetThreads) {
+    const int e = base_e + tid;
+    uint64_t key = 0;
+    if (e < n) {
+      const int ri = e / a.Mp, c = e % a.Mp;
+      const float p = det_value(base, a, ri, c);
+      bool ok = p > 0.f && (a.mode != OFDM_DETECT_THRESHOLD || p >= eta);
+      if (ok) {
+        const int r = (a.row0 + ri) % a.Np;
+        const uint32_t idx = (uint32_t)r * a.Mp + c;
+#pragma unroll
+        for (int dr = -1; dr <= 1; ++dr) {
+          int rj = ri + dr;
+          bool inside = true;
+          if (a.full) rj = (rj + a.rows) % a.rows;
+          else inside = rj >= 0 && rj < a.rows;
+          const int rn = (r + dr + a.Np) % a.Np;
+#pragma unroll
+          for (int dc = -1; dc <= 1; ++dc) {
+            if (dr == 0 && dc == 0) continue;
+            const int cn = (c + dc + a.Mp) % a.Mp;
+            const uint32_t in_idx = (uint32_t)rn * a.Mp + cn;
+            if (in_idx == idx) continue;
+            const float pn = inside ? det_value(base, a, rj, cn) : 0.f;
+            ok = ok && (p > pn || (p == pn && idx < in_idx));
+          }
+        }
+        if (ok) key = ((uint64_t)__float_as_uint(p) << 32) | (uint64_t)(~idx);
+      }
+    }
+    count += key ? 1u : 0u;
+    warp_topk_insert(list, key, K, lane);
+  }
+  count = __reduce_add_sync(0xffffffffu, count);
+  if (lane == 0) atomicAdd(&s_count, count);
+  lists[warp][lane] = list;
+  __syncthreads();
+
+  if (warp == 0) {
+    for (int w = 1; w < kDetThreads / 32; ++w) warp_topk_insert(list, lists[w][lane], K, lane);
+    const bool valid = lane < K && list != 0;
+    const int nv = __popc(__ballot_sync(0xffffffffu, valid));
+    if (valid && out) {
+      const uint32_t idx = ~(uint32_t)(list & 0xffffffffu);
+      const float p = __uint_as_float((uint32_t)(list >> 32));
+      ofdm_target tg;
+      tg.r = (int32_t)(idx / (uint32_t)a.Mp);
+      tg.s = (int32_t)(idx % (uint32_t)a.Mp) - a.Mp / 2;
+      tg.power = p;
+      tg.range_m = (float)tg.r * a.dd;
+      tg.vel_mps = (float)tg.s * a.dv;
+      out[(long)f * K + lane] = tg;
+    }
+    if (lane == 0) {
+      const uint32_t cnt = s_count;
+      uint32_t st = wstatus ? wstatus[f] : 0u;
+      if (a.mode == OFDM_DETECT_TOPK && cnt < (uint32_t)K) st |= OFDM_STATUS_FEW_PEAKS;
+      if (a.mode == OFDM_DETECT_THRESHOLD && cnt > (uint32_t)K) st |= OFDM_STATUS_OVERFLOW;
+      if (status) status[f] = st;
+      if (n_out) n_out[f] = nv;
+      if (wstatus) wstatus[f] = 0u;  // ready for the next call
+    }
+  }
+}
+
+// ---------------------------------------------------------------- launchers
+template <int MP>
+static cudaError_t launch_doppler_m(const float2* strip, float* map, float* pow, const DopplerArgs& a,
+                                    cudaStream_t s) {
+  size_t smem = MP <= 32 ? 0 : (size_t)kDopWarps * smem_elems(MP) * sizeof(float2);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(doppler_kernel<MP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  const long tasks = (long)a.frames * a.rows;
+  const long blocks = (tasks + kDopWarps - 1) / kDopWarps;
+  doppler_kernel<MP><<<(unsigned)blocks, 32 * kDopWarps, smem, s>>>(strip, map, pow, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_doppler(int Mp, const float2* strip, float* map, float* pow, const DopplerArgs& a,
+                           cudaStream_t s, int* launches) {
+  ++*launches;
+  switch (Mp) {
+    case 16: return launch_doppler_m<16>(strip, map, pow, a, s);
+    case 32: return launch_doppler_m<32>(strip, map, pow, a, s);
+    case 64: return launch_doppler_m<64>(strip, map, pow, a, s);
+    case 128: return launch_doppler_m<128>(strip, map, pow, a, s);
+    case 256: return launch_doppler_m<256>(strip, map, pow, a, s);
+    case 512: return launch_doppler_m<512>(strip, map, pow, a, s);
+    case 1024: return launch_doppler_m<1024>(strip, map, pow, a, s);
+    default: --*launches; return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_zero_rows(float* map, int frames, int Np, int Mp, int z0, int nz, cudaStream_t s,
+                             int* launches) {
+  if (nz <= 0) return cudaSuccess;
+  ++*launches;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long frame_floats = (long)Np * Mp;
+  zero_rows_kernel<<<sms * 4, 256, 0, s>>>(map, frames, frame_floats, (long)z0 * Mp, (long)nz * Mp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_detect(const float* pow, ofdm_target* out, int32_t* n_out, uint32_t* status,
+                          uint32_t* wstatus, const DetectArgs& a, cudaStream_t s, int* launches) {
+  ++*launches;
+  detect_kernel<<<a.frames, kDetThreads, 0, s>>>(pow, out, n_out, status, wstatus, a);
+  return cudaGetLastError();
+}
+
+}  // namespace ofdm

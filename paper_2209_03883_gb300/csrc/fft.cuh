@@ -1,0 +1,240 @@
+// fft.cuh -- register/shared-memory FFT building blocks for sm_103a.
+//
+// A transform of N = 2^p points is computed by T cooperating threads, each
+// holding E = N / T points in registers in the layout
+//     thread t holds x[t + T q],  q = 0 .. E-1,
+// which is also the coalesced global-memory pattern (for every q the T
+// threads touch T consecutive complex values).  The transform is a sequence
+// of Stockham auto-sort passes of radix R <= E; inside a pass every thread
+// runs G = E / R radix-R DFTs fully in registers (compile-time twiddles),
+// and passes exchange data through a padded shared-memory buffer.  The first
+// pass reads its operands straight from the registers and the last pass
+// leaves its results in registers in the same layout, so only
+// (passes - 1) shared-memory exchanges happen (one for N = 1024).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <utility>
+
+namespace ofdm {
+
+// ---------------------------------------------------------------- constexpr math
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+constexpr double cx_reduce(double x) {
+  while (x > kPi) x -= 2.0 * kPi;
+  while (x < -kPi) x += 2.0 * kPi;
+  return x;
+}
+constexpr double cx_sin(double x) {
+  x = cx_reduce(x);
+  double term = x, sum = x;
+  for (int n = 1; n < 24; ++n) {
+    term *= -x * x / ((2.0 * n) * (2.0 * n + 1.0));
+    sum += term;
+  }
+  return sum;
+}
+constexpr double cx_cos(double x) {
+  x = cx_reduce(x);
+  double term = 1.0, sum = 1.0;
+  for (int n = 1; n < 24; ++n) {
+    term *= -x * x / ((2.0 * n - 1.0) * (2.0 * n));
+    sum += term;
+  }
+  return sum;
+}
+constexpr int cx_log2(int n) { return n <= 1 ? 0 : 1 + cx_log2(n / 2); }
+constexpr int cx_brev(int i, int bits) {
+  int r = 0;
+  for (int b = 0; b < bits; ++b) r = (r << 1) | ((i >> b) & 1);
+  return r;
+}
+
+// ---------------------------------------------------------------- pass schedule
+// Radix of pass p for an N-point transform with E points per thread: as many
+// radix-E passes as divide N, then the remainder.  Shared by the host table
+// builder and the kernels.
+__host__ __device__ constexpr int pass_radix(int N, int E, int p) {
+  int rem = N, r = 1;
+  for (int i = 0; i <= p; ++i) {
+    r = E < rem ? E : rem;
+    while (rem % r) r /= 2;
+    rem /= r;
+  }
+  return r;
+}
+__host__ __device__ constexpr int num_passes(int N, int E) {
+  int rem = N, n = 0;
+  while (rem > 1) {
+    int r = E < rem ? E : rem;
+    while (rem % r) r /= 2;
+    rem /= r;
+    ++n;
+  }
+  return n;
+}
+__host__ __device__ constexpr int pass_ns(int N, int E, int p) {
+  int ns = 1;
+  for (int i = 0; i < p; ++i) ns *= pass_radix(N, E, i);
+  return ns;
+}
+// Twiddle table offset of pass p (pass 0 needs none):
+// tab[off(p) + r * Ns + u] = exp(+2 pi i u r / (Ns R)), u < Ns, r < R.
+__host__ __device__ constexpr int tw_offset(int N, int E, int p) {
+  int off = 0;
+  for (int i = 1; i < p; ++i) off += pass_ns(N, E, i) * pass_radix(N, E, i);
+  return off;
+}
+__host__ __device__ constexpr int tw_size(int N, int E) { return tw_offset(N, E, num_passes(N, E)); }
+
+// Padded shared-memory index: one spare slot per 32 elements keeps the
+// stride-32 writes of the first pass free of bank conflicts.
+__host__ __device__ constexpr int smem_elems(int N) { return N + N / 32; }
+__device__ __forceinline__ int pad32(int i) { return i + (i >> 5); }
+
+// ---------------------------------------------------------------- complex helpers
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
+  return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+
+// Streaming load for data read exactly once (keeps L2 for the workspace).
+__device__ __forceinline__ float2 ld_stream(const float2* p) { return __ldcs(p); }
+
+// ---------------------------------------------------------------- register DFT
+template <int LEN, int K, int DIR>
+__device__ __forceinline__ float2 tw_const_mul(float2 b) {
+  if constexpr (K == 0) {
+    return b;
+  } else if constexpr (4 * K == LEN) {  // exp(DIR i pi / 2) = DIR * i
+    return DIR > 0 ? make_float2(-b.y, b.x) : make_float2(b.y, -b.x);
+  } else {
+    constexpr float c = (float)cx_cos(2.0 * kPi * K / LEN);
+    constexpr float s = (float)(DIR * cx_sin(2.0 * kPi * K / LEN));
+    return make_float2(b.x * c - b.y * s, b.x * s + b.y * c);
+  }
+}
+
+template <int R, int LEN, int K, int DIR>
+__device__ __forceinline__ void bfly_k(float2* v) {
+#pragma unroll
+  for (int i = 0; i < R; i += LEN) {
+    const float2 a = v[i + K];
+    const float2 b = tw_const_mul<LEN, K, DIR>(v[i + K + LEN / 2]);
+    v[i + K] = cadd(a, b);
+    v[i + K + LEN / 2] = csub(a, b);
+  }
+}
+template <int R, int LEN, int DIR, int... Ks>
+__device__ __forceinline__ void dit_stage(float2* v, std::integer_sequence<int, Ks...>) {
+  (bfly_k<R, LEN, Ks, DIR>(v), ...);
+}
+template <int R, int DIR, int LEN>
+__device__ __forceinline__ void dit_stages(float2* v) {
+  if constexpr (LEN <= R) {
+    dit_stage<R, LEN, DIR>(v, std::make_integer_sequence<int, LEN / 2>{});
+    dit_stages<R, DIR, LEN * 2>(v);
+  }
+}
+template <int I, int B>
+struct Brev { static constexpr int value = cx_brev(I, B); };
+
+template <int R, int... Is>
+__device__ __forceinline__ void brev_perm(float2* v, std::integer_sequence<int, Is...>) {
+  float2 t[R];
+  ((t[Is] = v[Brev<Is, cx_log2(R)>::value]), ...);
+  ((v[Is] = t[Is]), ...);
+}
+
+// In-place R-point DFT  v[b] <- sum_a v[a] exp(DIR 2 pi i a b / R), natural order.
+template <int R, int DIR>
+__device__ __forceinline__ void dft_reg(float2* v) {
+  if constexpr (R > 1) {
+    brev_perm<R>(v, std::make_integer_sequence<int, R>{});
+    dit_stages<R, DIR, 2>(v);
+  }
+}
+
+// ---------------------------------------------------------------- group barrier
+// T threads of one transform group; groups are warp-aligned.
+template <int T>
+__device__ __forceinline__ void group_sync(int group) {
+  if constexpr (T <= 32) {
+    __syncwarp();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(group + 1), "r"(T) : "memory");
+  }
+}
+
+// ---------------------------------------------------------------- Stockham passes
+template <int N, int T, int DIR, int P>
+__device__ __forceinline__ void stockham_pass(float2* v, float2* sm, const float2* __restrict__ tw,
+                                              int t, int group) {
+  constexpr int E = N / T;
+  constexpr int R = pass_radix(N, E, P);
+  constexpr int NS = pass_ns(N, E, P);
+  constexpr int G = E / R;
+  constexpr int NP = num_passes(N, E);
+  static_assert(G * R == E, "pass does not tile the thread's points");
+  if constexpr (P > 0) {
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[g + r * G] = sm[pad32(t + T * g + r * (N / R))];
+  }
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    float2 w[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) w[r] = v[g + r * G];
+    if constexpr (P > 0) {
+      const int u = (t + T * g) & (NS - 1);
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        float2 tv = __ldg(tw + tw_offset(N, E, P) + r * NS + u);
+        if (DIR < 0) tv.y = -tv.y;
+        w[r] = cmul(w[r], tv);
+      }
+    }
+    dft_reg<R, DIR>(w);
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[g + r * G] = w[r];
+  }
+  if constexpr (P < NP - 1) {
+    group_sync<T>(group);  // previous readers of sm are done
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int j = t + T * g;
+      const int u = j & (NS - 1);
+      const int base = (j / NS) * NS * R + u;
+#pragma unroll
+      for (int r = 0; r < R; ++r) sm[pad32(base + r * NS)] = v[g + r * G];
+    }
+    group_sync<T>(group);
+  }
+}
+
+template <int N, int T, int DIR, int... Ps>
+__device__ __forceinline__ void run_passes(float2* v, float2* sm, const float2* __restrict__ tw, int t,
+                                           int group, std::integer_sequence<int, Ps...>) {
+  (stockham_pass<N, T, DIR, Ps>(v, sm, tw, t, group), ...);
+}
+
+// Unnormalised N-point DFT  X[m] = sum_n x[n] exp(DIR 2 pi i m n / N)
+// on the group's registers (layout t + T q in and out).  `sm` holds
+// smem_elems(N) float2 private to the group; `tw` is the host-built table
+// for DIR = +1 (conjugated on the fly for DIR = -1).
+template <int N, int T, int DIR>
+__device__ __forceinline__ void group_fft(float2* v, float2* sm, const float2* __restrict__ tw, int t,
+                                          int group) {
+  static_assert(N % T == 0 && N / T >= 2, "at least two points per thread");
+  run_passes<N, T, DIR>(v, sm, tw, t, group, std::make_integer_sequence<int, num_passes(N, N / T)>{});
+}
+
+}  // namespace ofdm

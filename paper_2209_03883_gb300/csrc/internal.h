@@ -1,0 +1,61 @@
+// internal.h -- plan layout and kernel launchers shared by the library's
+// translation units (not part of the public ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ofdm_radar.h"
+
+namespace ofdm {
+
+// Arguments of the column kernel (steps a1-a5 on every OFDM symbol).
+struct ColumnArgs {
+  int M, L_cp, rows, row0, full;  // support rows; full = rows cover all N bins (circular stencil)
+  int frames;
+  int zc;       // 1: apply the ZC transform to X
+  int rinv;     // r'^{-1} mod N (the ZC transform's output permutation, moved to the input)
+  float c0, c1; // range-window stencil: g[r] = c0 h[r] + c1 (h[r-1] + h[r+1])
+  float sqrtN;
+  const float2* pre;       // [N] pre-chirp exp(i pi r'(k^2 + 2q'k)/N^2)
+  const float2* post_conj; // [N] conj of the post factor (-1)^{r'i} exp(i 2 pi r'q' i/N)
+  const float2* tw;        // N-point pass twiddles (DIR = +1)
+};
+
+struct ZctArgs {
+  int frames, M, rinv, dir;
+  float scale;
+  const float2* in_tab;   // multiplies the (permuted) input
+  const float2* out_tab;  // multiplies the output
+  const float2* tw;
+};
+
+struct DopplerArgs {
+  int N, Np, M, Mp, rows, row0, frames;
+  float inv_nm;           // 1 / (N M)
+  const float* wl;        // [M] window over l
+  const float2* tw;       // Mp-point pass twiddles (DIR = +1), or the Mp roots for Mp <= 32
+};
+
+struct DetectArgs {
+  int Np, Mp, rows, row0, full;   // rows scanned, starting at range bin row0 (circular)
+  long frame_stride;              // floats between frames of the input
+  int compact;                    // 1: input rows are the support strip; 0: full map rows
+  int frames;
+  int mode, K;
+  int use_fixed_eta;
+  float eta_fixed, eta_factor;
+  float dd, dv;                   // metres / (m/s) per bin, Eq. (19)
+};
+
+cudaError_t launch_column(int N, const float2* Y, const float2* X, float2* strip, uint32_t* wstatus,
+                          const ColumnArgs& a, cudaStream_t s, int* launches);
+cudaError_t launch_zct(int N, const float2* in, float2* out, const ZctArgs& a, cudaStream_t s,
+                       int* launches);
+cudaError_t launch_doppler(int Mp, const float2* strip, float* map, float* pow, const DopplerArgs& a,
+                           cudaStream_t s, int* launches);
+cudaError_t launch_zero_rows(float* map, int frames, int Np, int Mp, int z0, int nz, cudaStream_t s,
+                             int* launches);
+cudaError_t launch_detect(const float* pow, ofdm_target* out, int32_t* n_out, uint32_t* status,
+                          uint32_t* wstatus, const DetectArgs& a, cudaStream_t s, int* launches);
+
+}  // namespace ofdm

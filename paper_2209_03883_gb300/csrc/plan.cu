@@ -1,0 +1,563 @@
+// plan.cu -- plan creation (parameter checks, FP64-derived tables,
+// workspace), the C ABI entry points and the host-buffer pipeline.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <complex>
+#include <vector>
+
+#include "fft.cuh"
+#include "internal.h"
+
+using ofdm::ColumnArgs;
+using ofdm::DetectArgs;
+using ofdm::DopplerArgs;
+using ofdm::ZctArgs;
+
+struct ofdm_radar_plan {
+  ofdm_radar_params p;
+  int Np, Mp;
+  int rows, row0, full;        // DFT-CE support (Eqs. (17), (21))
+  int z0, nz;                  // contiguous zero rows of the map
+  int rinv;
+  float c0, c1;
+  float2* d_tables = nullptr;  // one allocation: pre, post, pre_conj, post_conj, twN, twM
+  float2 *pre, *post, *pre_conj, *post_conj, *twN, *twM;
+  float* d_wl = nullptr;
+  float2* d_strip = nullptr;   // [max_frames][rows][M]
+  float* d_pow = nullptr;      // [max_frames][rows][M']
+  uint32_t* d_wstatus = nullptr;
+  // host-buffer path (allocated on first use)
+  float2* d_Y = nullptr;
+  float2* d_X = nullptr;
+  float* d_map = nullptr;
+  ofdm_target* d_tg = nullptr;
+  int32_t* d_nt = nullptr;
+  uint32_t* d_st = nullptr;
+  cudaStream_t hs[2] = {nullptr, nullptr};
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  int last_launches = 0;
+  // per-kernel timing (ofdm_radar_timing_enable)
+  int timing = 0;
+  int nrec = 0;
+  cudaEvent_t* tev = nullptr;  // 2 * kMaxTimed events
+  int* tkind = nullptr;
+};
+
+namespace {
+constexpr int kMaxTimed = 4096;
+constexpr int kKinds = 5;  // column, zero_rows, doppler, detect, zct
+enum { K_COLUMN = 0, K_ZERO = 1, K_DOPPLER = 2, K_DETECT = 3, K_ZCT = 4 };
+
+// Records an event pair around one launch when timing is enabled.
+struct ScopedTimer {
+  ofdm_radar_plan* pl;
+  cudaStream_t s;
+  int idx = -1;
+  ScopedTimer(ofdm_radar_plan* p, cudaStream_t st, int kind) : pl(p), s(st) {
+    if (pl->timing && pl->nrec < kMaxTimed) {
+      idx = pl->nrec++;
+      pl->tkind[idx] = kind;
+      cudaEventRecord(pl->tev[2 * idx], s);
+    }
+  }
+  ~ScopedTimer() {
+    if (idx >= 0) cudaEventRecord(pl->tev[2 * idx + 1], s);
+  }
+};
+}  // namespace
+
+namespace {
+
+thread_local char g_errbuf[512];
+
+bool is_pow2(long v) { return v > 0 && (v & (v - 1)) == 0; }
+
+int cuda_fail(cudaError_t e) {
+  snprintf(g_errbuf, sizeof g_errbuf, "CUDA error: %s", cudaGetErrorString(e));
+  return OFDM_ERR_CUDA;
+}
+
+// exp(i pi m / half) for an exact integer phase index m in [0, 2 half).
+float2 unit_phase(long long m, long long half) {
+  const double a = M_PI * (double)m / (double)half;
+  return make_float2((float)cos(a), (float)sin(a));
+}
+
+long long mod_ll(long long a, long long m) {
+  long long r = a % m;
+  return r < 0 ? r + m : r;
+}
+
+// Pass twiddles of the Stockham schedule in fft.cuh, for DIR = +1.
+void build_twiddles(std::vector<float2>& out, int n, int e) {
+  out.assign((size_t)ofdm::tw_size(n, e) + 1, make_float2(1.f, 0.f));
+  const int np = ofdm::num_passes(n, e);
+  for (int p = 1; p < np; ++p) {
+    const int R = ofdm::pass_radix(n, e, p), NS = ofdm::pass_ns(n, e, p), off = ofdm::tw_offset(n, e, p);
+    const long long span = (long long)NS * R;
+    for (int r = 0; r < R; ++r)
+      for (int u = 0; u < NS; ++u) {
+        const long long m = ((long long)u * r) % span;
+        const double a = 2.0 * M_PI * (double)m / (double)span;
+        out[(size_t)off + r * NS + u] = make_float2((float)cos(a), (float)sin(a));
+      }
+  }
+}
+
+int column_points_per_thread(int N) { return N <= 1024 ? N / 32 : 32; }
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count) {
+  return cudaMalloc((void**)p, count * sizeof(T) + 16);
+}
+
+}  // namespace
+
+extern "C" {
+
+void ofdm_radar_default_params(ofdm_radar_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof *p);
+  p->zc_root = 1;
+  p->window = OFDM_WINDOW_HANN;
+  p->detect_mode = OFDM_DETECT_TOPK;
+  p->max_targets = 8;
+  p->max_frames = 1;
+  p->precision = OFDM_PREC_FP32;
+  p->pfa = 1e-2f;
+  p->noise_var = -1.f;
+  p->fc_hz = 77e9;
+  p->df_hz = 240e3;
+}
+
+const char* ofdm_radar_strerror(int code) {
+  switch (code) {
+    case OFDM_OK: return "ok";
+    case OFDM_ERR_INVALID_ARG: return "invalid argument";
+    case OFDM_ERR_UNSUPPORTED_SIZE: return "unsupported size";
+    case OFDM_ERR_CUDA: return g_errbuf[0] ? g_errbuf : "CUDA error";
+    case OFDM_ERR_TIMEOUT: return "device wait timed out";
+    case OFDM_ERR_NO_MEMORY: return "out of device memory";
+    default: return "unknown error";
+  }
+}
+
+void ofdm_radar_plan_destroy(ofdm_radar_plan* plan) {
+  if (!plan) return;
+  cudaFree(plan->d_tables);
+  cudaFree(plan->d_wl);
+  cudaFree(plan->d_strip);
+  cudaFree(plan->d_pow);
+  cudaFree(plan->d_wstatus);
+  cudaFree(plan->d_Y);
+  cudaFree(plan->d_X);
+  cudaFree(plan->d_map);
+  cudaFree(plan->d_tg);
+  cudaFree(plan->d_nt);
+  cudaFree(plan->d_st);
+  for (auto& s : plan->hs)
+    if (s) cudaStreamDestroy(s);
+  for (auto& e : plan->ev)
+    if (e) cudaEventDestroy(e);
+  if (plan->tev) {
+    for (int i = 0; i < 2 * kMaxTimed; ++i) cudaEventDestroy(plan->tev[i]);
+    delete[] plan->tev;
+    delete[] plan->tkind;
+  }
+  delete plan;
+}
+
+int ofdm_radar_plan_create(const ofdm_radar_params* pin, ofdm_radar_plan** out) {
+  if (!pin || !out) return OFDM_ERR_INVALID_ARG;
+  *out = nullptr;
+  const ofdm_radar_params& p = *pin;
+  const int N = p.N, M = p.M;
+  const int Np = p.N_pad ? p.N_pad : N, Mp = p.M_pad ? p.M_pad : M;
+  if (!is_pow2(N) || N < 64 || N > 4096) return OFDM_ERR_UNSUPPORTED_SIZE;
+  if (!is_pow2(M) || M < 16 || M > 1024) return OFDM_ERR_UNSUPPORTED_SIZE;
+  if (Np != N) return OFDM_ERR_UNSUPPORTED_SIZE;  // range zero-padding is not built
+  if (!is_pow2(Mp) || Mp < M || Mp > 1024) return OFDM_ERR_UNSUPPORTED_SIZE;
+  if (p.L_cp < 1 || p.L_cp > N) return OFDM_ERR_INVALID_ARG;
+  if (p.n_cp < 0) return OFDM_ERR_INVALID_ARG;
+  if (p.zc_root < 0 || (p.zc_root > 0 && (p.zc_root % 2) == 0)) return OFDM_ERR_INVALID_ARG;
+  if (p.window < OFDM_WINDOW_RECT || p.window > OFDM_WINDOW_HAMMING) return OFDM_ERR_INVALID_ARG;
+  if (p.detect_mode != OFDM_DETECT_TOPK && p.detect_mode != OFDM_DETECT_THRESHOLD) return OFDM_ERR_INVALID_ARG;
+  if (p.max_targets < 1 || p.max_targets > 32) return OFDM_ERR_INVALID_ARG;
+  if (p.max_frames < 1) return OFDM_ERR_INVALID_ARG;
+  if (p.precision != OFDM_PREC_FP32) return OFDM_ERR_UNSUPPORTED_SIZE;
+  if (!(p.pfa > 0.f && p.pfa < 1.f)) return OFDM_ERR_INVALID_ARG;
+  if (!(p.fc_hz > 0.0 && p.df_hz > 0.0)) return OFDM_ERR_INVALID_ARG;
+
+  ofdm_radar_plan* pl = new ofdm_radar_plan();
+  pl->p = p;
+  pl->Np = Np;
+  pl->Mp = Mp;
+  // Support rows: taps n < L_cp (Eq. (21)); a periodic Hann/Hamming window
+  // over k spreads each tap to r - 1 and r + 1 (circular).
+  const int spread = p.window == OFDM_WINDOW_RECT ? 0 : 2;
+  if (p.L_cp + spread >= N) {
+    pl->rows = N; pl->row0 = 0; pl->full = 1;
+  } else {
+    pl->rows = p.L_cp + spread; pl->row0 = spread ? N - 1 : 0; pl->full = 0;
+  }
+  pl->nz = N - pl->rows;
+  pl->z0 = (pl->row0 + pl->rows) % N;
+  if (p.window == OFDM_WINDOW_HANN) { pl->c0 = 0.5f; pl->c1 = -0.25f; }
+  else if (p.window == OFDM_WINDOW_HAMMING) { pl->c0 = 0.54f; pl->c1 = -0.23f; }
+  else { pl->c0 = 1.f; pl->c1 = 0.f; }
+
+  // ZC tables (Sec. III-B, Eqs. (23)-(24)) with exact int64 phase indices:
+  //   Z_m(i, j) = exp(i pi m / N^2),
+  //   m = r' [ (i mod 2) N^2 + 2 N (i j mod N) + j^2 + 2 q' (i N + j) ]  mod 2 N^2
+  // which factors into pre_j = exp(i pi r'(j^2 + 2q'j)/N^2), the DFT kernel
+  // exp(2 pi i r' i j / N) and post_i = exp(i pi r'((i mod 2) N^2 + 2q' i N)/N^2).
+  const long long NN = (long long)N * N, two = 2 * NN;
+  const int r = p.zc_root ? p.zc_root : 1;
+  const long long rr = mod_ll(r, two), qq = mod_ll(p.zc_q, two);
+  std::vector<float2> pre(N), post(N), prec(N), postc(N);
+  for (int j = 0; j < N; ++j) {
+    const long long base = mod_ll((long long)j * j + 2 * qq % two * j % two, two);
+    const long long m = (rr * base) % two;
+    pre[j] = unit_phase(m, NN);
+    prec[j] = make_float2(pre[j].x, -pre[j].y);
+  }
+  for (int i = 0; i < N; ++i) {
+    const long long base = mod_ll((long long)(i & 1) * NN + (2 * qq % two) * ((long long)i * N % two) % two, two);
+    const long long m = (rr * base) % two;
+    post[i] = unit_phase(m, NN);
+    postc[i] = make_float2(post[i].x, -post[i].y);
+  }
+  // r'^{-1} mod N (r' odd, N a power of two)
+  int rinv = 1;
+  for (int c = 1; c < N; c += 2)
+    if (((long long)c * r) % N == 1) { rinv = c; break; }
+  pl->rinv = rinv;
+
+  std::vector<float2> twN, twM;
+  build_twiddles(twN, N, column_points_per_thread(N));
+  if (Mp <= 32) {
+    twM.resize(Mp);
+    for (int m = 0; m < Mp; ++m) {
+      const double a = 2.0 * M_PI * m / Mp;
+      twM[m] = make_float2((float)cos(a), (float)sin(a));
+    }
+  } else {
+    build_twiddles(twM, Mp, Mp / 32);
+  }
+  std::vector<float> wl(M);
+  for (int l = 0; l < M; ++l) {
+    const double c = cos(2.0 * M_PI * l / M);
+    wl[l] = p.window == OFDM_WINDOW_HANN ? (float)(0.5 - 0.5 * c)
+          : p.window == OFDM_WINDOW_HAMMING ? (float)(0.54 - 0.46 * c) : 1.f;
+  }
+
+  const size_t ntab = 4 * (size_t)N + twN.size() + twM.size();
+  cudaError_t e = dalloc(&pl->d_tables, ntab);
+  if (e == cudaSuccess) e = dalloc(&pl->d_wl, (size_t)M);
+  if (e == cudaSuccess) e = dalloc(&pl->d_strip, (size_t)p.max_frames * pl->rows * M);
+  if (e == cudaSuccess) e = dalloc(&pl->d_pow, (size_t)p.max_frames * pl->rows * Mp);
+  if (e == cudaSuccess) e = dalloc(&pl->d_wstatus, (size_t)p.max_frames);
+  if (e != cudaSuccess) {
+    ofdm_radar_plan_destroy(pl);
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? OFDM_ERR_NO_MEMORY : cuda_fail(e);
+  }
+  pl->pre = pl->d_tables;
+  pl->post = pl->pre + N;
+  pl->pre_conj = pl->post + N;
+  pl->post_conj = pl->pre_conj + N;
+  pl->twN = pl->post_conj + N;
+  pl->twM = pl->twN + twN.size();
+  std::vector<float2> host(ntab);
+  memcpy(host.data(), pre.data(), N * sizeof(float2));
+  memcpy(host.data() + N, post.data(), N * sizeof(float2));
+  memcpy(host.data() + 2 * N, prec.data(), N * sizeof(float2));
+  memcpy(host.data() + 3 * N, postc.data(), N * sizeof(float2));
+  memcpy(host.data() + 4 * N, twN.data(), twN.size() * sizeof(float2));
+  memcpy(host.data() + 4 * N + twN.size(), twM.data(), twM.size() * sizeof(float2));
+  e = cudaMemcpy(pl->d_tables, host.data(), ntab * sizeof(float2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(pl->d_wl, wl.data(), M * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(pl->d_wstatus, 0, (size_t)p.max_frames * sizeof(uint32_t));
+  if (e != cudaSuccess) {
+    ofdm_radar_plan_destroy(pl);
+    return cuda_fail(e);
+  }
+  *out = pl;
+  return OFDM_OK;
+}
+
+int ofdm_radar_support_rows(const ofdm_radar_plan* plan, int32_t* rows) {
+  if (!plan) return OFDM_ERR_INVALID_ARG;
+  if (rows)
+    for (int i = 0; i < plan->rows; ++i) rows[i] = (plan->row0 + i) % plan->p.N;
+  return plan->rows;
+}
+
+int ofdm_radar_last_launch_count(const ofdm_radar_plan* plan) {
+  return plan ? plan->last_launches : OFDM_ERR_INVALID_ARG;
+}
+
+int ofdm_radar_timing_enable(ofdm_radar_plan* pl, int32_t enable) {
+  if (!pl) return OFDM_ERR_INVALID_ARG;
+  if (enable && !pl->tev) {
+    pl->tev = new cudaEvent_t[2 * kMaxTimed]();
+    pl->tkind = new int[kMaxTimed]();
+    for (int i = 0; i < 2 * kMaxTimed; ++i) {
+      cudaError_t e = cudaEventCreate(&pl->tev[i]);
+      if (e != cudaSuccess) return cuda_fail(e);
+    }
+  }
+  pl->timing = enable ? 1 : 0;
+  return OFDM_OK;
+}
+
+int ofdm_radar_timing_read(ofdm_radar_plan* pl, float* total_ms, int32_t* launches, int32_t n) {
+  if (!pl || n < 0) return OFDM_ERR_INVALID_ARG;
+  float tot[kKinds] = {0};
+  int cnt[kKinds] = {0};
+  for (int i = 0; i < pl->nrec; ++i) {
+    cudaError_t e = cudaEventSynchronize(pl->tev[2 * i + 1]);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, pl->tev[2 * i], pl->tev[2 * i + 1]);
+    if (e != cudaSuccess) return cuda_fail(e);
+    tot[pl->tkind[i]] += ms;
+    cnt[pl->tkind[i]] += 1;
+  }
+  pl->nrec = 0;
+  const int m = n < kKinds ? n : kKinds;
+  for (int k = 0; k < m; ++k) {
+    if (total_ms) total_ms[k] = tot[k];
+    if (launches) launches[k] = cnt[k];
+  }
+  return m;
+}
+
+}  // extern "C"
+
+namespace {
+
+ColumnArgs column_args(const ofdm_radar_plan* pl, int frames) {
+  ColumnArgs a;
+  a.M = pl->p.M;
+  a.L_cp = pl->p.L_cp;
+  a.rows = pl->rows;
+  a.row0 = pl->row0;
+  a.full = pl->full;
+  a.frames = frames;
+  a.zc = (pl->p.zc_root > 0 && !pl->p.x_is_precoded) ? 1 : 0;
+  a.rinv = pl->rinv;
+  a.c0 = pl->c0;
+  a.c1 = pl->c1;
+  a.sqrtN = (float)sqrt((double)pl->p.N);
+  a.pre = pl->pre;
+  a.post_conj = pl->post_conj;
+  a.tw = pl->twN;
+  return a;
+}
+
+DopplerArgs doppler_args(const ofdm_radar_plan* pl, int frames) {
+  DopplerArgs a;
+  a.N = pl->p.N;
+  a.Np = pl->Np;
+  a.M = pl->p.M;
+  a.Mp = pl->Mp;
+  a.rows = pl->rows;
+  a.row0 = pl->row0;
+  a.frames = frames;
+  a.inv_nm = (float)(1.0 / ((double)pl->p.N * (double)pl->p.M));
+  a.wl = pl->d_wl;
+  a.tw = pl->twM;
+  return a;
+}
+
+DetectArgs detect_args(const ofdm_radar_plan* pl, int frames, int compact) {
+  const ofdm_radar_params& p = pl->p;
+  DetectArgs a;
+  a.Np = pl->Np;
+  a.Mp = pl->Mp;
+  a.rows = pl->rows;
+  a.row0 = pl->row0;
+  a.full = pl->full;
+  a.compact = compact;
+  a.frame_stride = compact ? (long)pl->rows * pl->Mp : (long)pl->Np * pl->Mp;
+  a.frames = frames;
+  a.mode = p.detect_mode;
+  a.K = p.max_targets;
+  a.use_fixed_eta = p.noise_var > 0.f ? 1 : 0;
+  // eta = sigma^2 (-ln P_fa) (Eq. (18), reading of the garbled sign), in FP32.
+  const float lnp = (float)(-log((double)p.pfa));
+  a.eta_fixed = p.noise_var * lnp;
+  a.eta_factor = (float)(-log((double)p.pfa) / log(2.0));
+  const double c = 3.0e8;
+  const int ncp = p.n_cp ? p.n_cp : p.L_cp;
+  const double Ts = (double)(p.N + ncp) / ((double)p.N * p.df_hz);
+  a.dd = (float)(c / (2.0 * pl->Np * p.df_hz));
+  a.dv = (float)(c / (2.0 * p.fc_hz * pl->Mp * Ts));
+  return a;
+}
+
+bool bad_frames(const ofdm_radar_plan* pl, int frames) { return frames < 1 || frames > pl->p.max_frames; }
+
+int finish(ofdm_radar_plan* pl, int launches, cudaError_t e) {
+  if (e != cudaSuccess) return cuda_fail(e);
+  pl->last_launches = launches;
+  return OFDM_OK;
+}
+
+// The chain on device buffers; shared by the device and host entry points.
+cudaError_t run_chain(ofdm_radar_plan* pl, const float2* Y, const float2* X, int frames, float* map,
+                      ofdm_target* tg, int32_t* nt, uint32_t* st, cudaStream_t s, int* launches) {
+  cudaError_t e;
+  {
+    ScopedTimer tm(pl, s, K_COLUMN);
+    e = ofdm::launch_column(pl->p.N, Y, X, pl->d_strip, pl->d_wstatus, column_args(pl, frames), s, launches);
+  }
+  if (e != cudaSuccess) return e;
+  if (map && pl->nz > 0) {
+    ScopedTimer tm(pl, s, K_ZERO);
+    e = ofdm::launch_zero_rows(map, frames, pl->Np, pl->Mp, pl->z0, pl->nz, s, launches);
+    if (e != cudaSuccess) return e;
+  }
+  {
+    ScopedTimer tm(pl, s, K_DOPPLER);
+    e = ofdm::launch_doppler(pl->Mp, pl->d_strip, map, pl->d_pow, doppler_args(pl, frames), s, launches);
+  }
+  if (e != cudaSuccess) return e;
+  ScopedTimer tm(pl, s, K_DETECT);
+  return ofdm::launch_detect(pl->d_pow, tg, nt, st, pl->d_wstatus, detect_args(pl, frames, 1), s, launches);
+}
+
+}  // namespace
+
+extern "C" {
+
+int ofdm_radar_process(ofdm_radar_plan* pl, const ofdm_c32* Y, const ofdm_c32* X, int32_t frames,
+                       float* out_map, ofdm_target* out_targets, int32_t* n_targets, uint32_t* status,
+                       void* stream) {
+  if (!pl || !Y || !X || bad_frames(pl, frames)) return OFDM_ERR_INVALID_ARG;
+  int launches = 0;
+  cudaError_t e = run_chain(pl, (const float2*)Y, (const float2*)X, frames, out_map, out_targets, n_targets,
+                            status, (cudaStream_t)stream, &launches);
+  return finish(pl, launches, e);
+}
+
+int ofdm_zc_precode(ofdm_radar_plan* pl, const ofdm_c32* in, ofdm_c32* out, int32_t frames, int32_t inverse,
+                    void* stream) {
+  if (!pl || !in || !out || in == out || bad_frames(pl, frames)) return OFDM_ERR_INVALID_ARG;
+  if (pl->p.zc_root <= 0) return OFDM_ERR_INVALID_ARG;
+  ZctArgs a;
+  a.frames = frames;
+  a.M = pl->p.M;
+  a.rinv = pl->rinv;
+  a.dir = inverse ? -1 : +1;
+  a.scale = (float)(1.0 / sqrt((double)pl->p.N));
+  a.in_tab = inverse ? pl->post_conj : pl->pre;
+  a.out_tab = inverse ? pl->pre_conj : pl->post;
+  a.tw = pl->twN;
+  int launches = 0;
+  cudaError_t e;
+  {
+    ScopedTimer tm(pl, (cudaStream_t)stream, K_ZCT);
+    e = ofdm::launch_zct(pl->p.N, (const float2*)in, (float2*)out, a, (cudaStream_t)stream, &launches);
+  }
+  return finish(pl, launches, e);
+}
+
+int ofdm_radar_range_profile(ofdm_radar_plan* pl, const ofdm_c32* Y, const ofdm_c32* X, int32_t frames,
+                             ofdm_c32* strip, void* stream) {
+  if (!pl || !Y || !X || !strip || bad_frames(pl, frames)) return OFDM_ERR_INVALID_ARG;
+  int launches = 0;
+  cudaError_t e = ofdm::launch_column(pl->p.N, (const float2*)Y, (const float2*)X, (float2*)strip,
+                                      pl->d_wstatus, column_args(pl, frames), (cudaStream_t)stream, &launches);
+  // the status words of this call are not reported; clear them
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(pl->d_wstatus, 0, (size_t)frames * sizeof(uint32_t), (cudaStream_t)stream);
+  return finish(pl, launches, e);
+}
+
+int ofdm_radar_doppler(ofdm_radar_plan* pl, const ofdm_c32* strip, int32_t frames, float* out_map,
+                       void* stream) {
+  if (!pl || !strip || !out_map || bad_frames(pl, frames)) return OFDM_ERR_INVALID_ARG;
+  int launches = 0;
+  cudaError_t e = ofdm::launch_zero_rows(out_map, frames, pl->Np, pl->Mp, pl->z0, pl->nz, (cudaStream_t)stream,
+                                         &launches);
+  if (e == cudaSuccess)
+    e = ofdm::launch_doppler(pl->Mp, (const float2*)strip, out_map, pl->d_pow, doppler_args(pl, frames),
+                             (cudaStream_t)stream, &launches);
+  return finish(pl, launches, e);
+}
+
+int ofdm_radar_detect(ofdm_radar_plan* pl, const float* map, int32_t frames, ofdm_target* out_targets,
+                      int32_t* n_targets, uint32_t* status, void* stream) {
+  if (!pl || !map || bad_frames(pl, frames)) return OFDM_ERR_INVALID_ARG;
+  int launches = 0;
+  cudaError_t e = ofdm::launch_detect(map, out_targets, n_targets, status, nullptr, detect_args(pl, frames, 0),
+                                      (cudaStream_t)stream, &launches);
+  return finish(pl, launches, e);
+}
+
+int ofdm_radar_process_host(ofdm_radar_plan* pl, const ofdm_c32* Yh, const ofdm_c32* Xh, int32_t frames,
+                            float* map_h, ofdm_target* tg_h, int32_t* nt_h, uint32_t* st_h, void* stream) {
+  if (!pl || !Yh || !Xh || bad_frames(pl, frames)) return OFDM_ERR_INVALID_ARG;
+  const ofdm_radar_params& p = pl->p;
+  const size_t grid = (size_t)p.N * p.M, mapn = (size_t)pl->Np * pl->Mp;
+  cudaError_t e = cudaSuccess;
+  if (!pl->d_Y) {
+    e = dalloc(&pl->d_Y, grid * p.max_frames);
+    if (e == cudaSuccess) e = dalloc(&pl->d_X, grid * p.max_frames);
+    if (e == cudaSuccess) e = dalloc(&pl->d_map, mapn * p.max_frames);
+    if (e == cudaSuccess) e = dalloc(&pl->d_tg, (size_t)p.max_targets * p.max_frames);
+    if (e == cudaSuccess) e = dalloc(&pl->d_nt, (size_t)p.max_frames);
+    if (e == cudaSuccess) e = dalloc(&pl->d_st, (size_t)p.max_frames);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&pl->hs[i], cudaStreamNonBlocking);
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&pl->ev[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      cudaFree(pl->d_Y); pl->d_Y = nullptr;
+      cudaGetLastError();
+      return e == cudaErrorMemoryAllocation ? OFDM_ERR_NO_MEMORY : cuda_fail(e);
+    }
+  }
+  cudaStream_t s0 = (cudaStream_t)stream;
+  // Chunks of frames alternate between two streams so that the copies of one
+  // chunk overlap the kernels of the other.
+  const int chunk = frames >= 8 ? (frames + 3) / 4 : frames;
+  e = cudaEventRecord(pl->ev[0], s0);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(pl->hs[i], pl->ev[0], 0);
+  int launches = 0, k = 0;
+  for (int f0 = 0; f0 < frames && e == cudaSuccess; f0 += chunk, ++k) {
+    const int nf = frames - f0 < chunk ? frames - f0 : chunk;
+    cudaStream_t s = pl->hs[k & 1];
+    const size_t g0 = grid * f0, gn = grid * nf;
+    e = cudaMemcpyAsync(pl->d_Y + g0, Yh + g0, gn * sizeof(float2), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(pl->d_X + g0, Xh + g0, gn * sizeof(float2), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) break;
+    // The chunk uses its own slice of the workspace (frame offset f0).
+    ofdm_radar_plan view = *pl;
+    view.d_strip = pl->d_strip + (size_t)f0 * pl->rows * p.M;
+    view.d_pow = pl->d_pow + (size_t)f0 * pl->rows * pl->Mp;
+    view.d_wstatus = pl->d_wstatus + f0;
+    e = run_chain(&view, pl->d_Y + g0, pl->d_X + g0, nf, map_h ? pl->d_map + mapn * f0 : nullptr,
+                  pl->d_tg + (size_t)p.max_targets * f0, pl->d_nt + f0, pl->d_st + f0, s, &launches);
+    if (e != cudaSuccess) break;
+    if (map_h)
+      e = cudaMemcpyAsync(map_h + mapn * f0, pl->d_map + mapn * f0, mapn * nf * sizeof(float),
+                          cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && tg_h)
+      e = cudaMemcpyAsync(tg_h + (size_t)p.max_targets * f0, pl->d_tg + (size_t)p.max_targets * f0,
+                          (size_t)p.max_targets * nf * sizeof(ofdm_target), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && nt_h)
+      e = cudaMemcpyAsync(nt_h + f0, pl->d_nt + f0, nf * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && st_h)
+      e = cudaMemcpyAsync(st_h + f0, pl->d_st + f0, nf * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+  }
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+    e = cudaEventRecord(pl->ev[1 + i], pl->hs[i]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s0, pl->ev[1 + i], 0);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s0);
+  return finish(pl, launches, e);
+}
+
+}  // extern "C"

@@ -1,0 +1,247 @@
+"""Thin ctypes binding of libofdm_radar.so (include/ofdm_radar.h).
+
+Argument marshalling only: every step of the receive chain runs in the CUDA
+library.  Functions keep the C names; device buffers are torch CUDA tensors
+passed by data_ptr(), the stream is torch's current stream unless given.
+If the library is missing the import of this module raises -- there is no
+fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libofdm_radar.so")
+HEADER = os.path.join(os.path.dirname(PKG), "include", "ofdm_radar.h")
+
+OFDM_OK = 0
+ERRORS = {-1: "INVALID_ARG", -2: "UNSUPPORTED_SIZE", -3: "CUDA", -4: "TIMEOUT", -5: "NO_MEMORY"}
+WINDOW_RECT, WINDOW_HANN, WINDOW_HAMMING = 0, 1, 2
+DETECT_TOPK, DETECT_THRESHOLD = 0, 1
+PREC_FP32, PREC_SPLIT_BF16 = 0, 1
+STATUS_ZERO_X, STATUS_NONFINITE, STATUS_OVERFLOW, STATUS_FEW_PEAKS = 1, 2, 4, 8
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int32), ("M", ctypes.c_int32),
+                ("N_pad", ctypes.c_int32), ("M_pad", ctypes.c_int32),
+                ("L_cp", ctypes.c_int32), ("n_cp", ctypes.c_int32),
+                ("zc_root", ctypes.c_int32), ("zc_q", ctypes.c_int32),
+                ("x_is_precoded", ctypes.c_int32), ("window", ctypes.c_int32),
+                ("detect_mode", ctypes.c_int32), ("max_targets", ctypes.c_int32),
+                ("max_frames", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("pfa", ctypes.c_float), ("noise_var", ctypes.c_float),
+                ("fc_hz", ctypes.c_double), ("df_hz", ctypes.c_double)]
+
+
+class Target(ctypes.Structure):
+    _fields_ = [("r", ctypes.c_int32), ("s", ctypes.c_int32), ("power", ctypes.c_float),
+                ("range_m", ctypes.c_float), ("vel_mps", ctypes.c_float)]
+
+
+TARGET_BYTES = ctypes.sizeof(Target)   # 20
+
+
+class OfdmError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        msg = _lib.ofdm_radar_strerror(code).decode() if _lib else ERRORS.get(code, str(code))
+        super().__init__(f"{where}: {ERRORS.get(code, code)} ({msg})")
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run __graft_entry__.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32 = ctypes.c_void_p, ctypes.c_int32
+    P = ctypes.POINTER
+    lib.ofdm_radar_default_params.argtypes = [P(Params)]
+    lib.ofdm_radar_default_params.restype = None
+    lib.ofdm_radar_plan_create.argtypes = [P(Params), P(vp)]
+    lib.ofdm_radar_plan_destroy.argtypes = [vp]
+    lib.ofdm_radar_plan_destroy.restype = None
+    lib.ofdm_radar_support_rows.argtypes = [vp, vp]
+    lib.ofdm_radar_process.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp, vp]
+    lib.ofdm_radar_process_host.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp, vp]
+    lib.ofdm_zc_precode.argtypes = [vp, vp, vp, i32, i32, vp]
+    lib.ofdm_radar_range_profile.argtypes = [vp, vp, vp, i32, vp, vp]
+    lib.ofdm_radar_doppler.argtypes = [vp, vp, i32, vp, vp]
+    lib.ofdm_radar_detect.argtypes = [vp, vp, i32, vp, vp, vp, vp]
+    lib.ofdm_radar_last_launch_count.argtypes = [vp]
+    lib.ofdm_radar_timing_enable.argtypes = [vp, i32]
+    lib.ofdm_radar_timing_read.argtypes = [vp, vp, vp, i32]
+    lib.ofdm_radar_strerror.argtypes = [ctypes.c_int]
+    lib.ofdm_radar_strerror.restype = ctypes.c_char_p
+    for name in ("ofdm_radar_plan_create", "ofdm_radar_support_rows", "ofdm_radar_process",
+                 "ofdm_radar_process_host", "ofdm_zc_precode", "ofdm_radar_range_profile",
+                 "ofdm_radar_doppler", "ofdm_radar_detect", "ofdm_radar_last_launch_count",
+                 "ofdm_radar_timing_enable", "ofdm_radar_timing_read"):
+        getattr(lib, name).restype = ctypes.c_int
+    return lib
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def declared_functions(header: str = HEADER):
+    """Names of the functions declared in the public header."""
+    text = open(header).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ofdm_[a-z0-9_]+)\s*\(", text)))
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    _lib.ofdm_radar_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+def _check(code, where):
+    if code < 0:
+        raise OfdmError(code, where)
+    return code
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(getattr(stream, "cuda_stream", stream))
+
+
+class Plan:
+    """Owns an ofdm_radar_plan (tables + workspace on the current device)."""
+
+    def __init__(self, params: Params | None = None, **kw):
+        self.params = params if params is not None else default_params(**kw)
+        h = ctypes.c_void_p()
+        _check(_lib.ofdm_radar_plan_create(ctypes.byref(self.params), ctypes.byref(h)),
+               "ofdm_radar_plan_create")
+        self._h = h
+        p = self.params
+        self.N, self.M = p.N, p.M
+        self.Np, self.Mp = p.N_pad or p.N, p.M_pad or p.M
+        self.max_targets, self.max_frames = p.max_targets, p.max_frames
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.ofdm_radar_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def support_rows(self):
+        n = _check(_lib.ofdm_radar_support_rows(self._h, None), "ofdm_radar_support_rows")
+        arr = (ctypes.c_int32 * n)()
+        _lib.ofdm_radar_support_rows(self._h, ctypes.cast(arr, ctypes.c_void_p))
+        return list(arr)
+
+    def last_launch_count(self):
+        return _lib.ofdm_radar_last_launch_count(self._h)
+
+    KERNEL_KINDS = ("column", "zero_rows", "doppler", "detect", "zct")
+
+    def timing_enable(self, on=True):
+        _check(_lib.ofdm_radar_timing_enable(self._h, int(bool(on))), "ofdm_radar_timing_enable")
+
+    def timing_read(self):
+        """{kind: (total_ms, launches)} of the launches recorded since the last read."""
+        n = len(self.KERNEL_KINDS)
+        ms = (ctypes.c_float * n)()
+        cnt = (ctypes.c_int32 * n)()
+        m = _check(_lib.ofdm_radar_timing_read(self._h, ctypes.cast(ms, ctypes.c_void_p),
+                                                ctypes.cast(cnt, ctypes.c_void_p), n),
+                   "ofdm_radar_timing_read")
+        return {self.KERNEL_KINDS[k]: (float(ms[k]), int(cnt[k])) for k in range(m)}
+
+
+def ofdm_radar_process(plan: Plan, Y, X, frames, out_map=None, out_targets=None, n_targets=None,
+                       status=None, stream=None):
+    return _check(_lib.ofdm_radar_process(plan.handle, _ptr(Y), _ptr(X), frames, _ptr(out_map),
+                                          _ptr(out_targets), _ptr(n_targets), _ptr(status),
+                                          _stream(stream)), "ofdm_radar_process")
+
+
+def ofdm_radar_process_host(plan: Plan, Y_host, X_host, frames, map_host=None, targets_host=None,
+                            n_targets_host=None, status_host=None, stream=None):
+    return _check(_lib.ofdm_radar_process_host(plan.handle, _ptr(Y_host), _ptr(X_host), frames,
+                                               _ptr(map_host), _ptr(targets_host),
+                                               _ptr(n_targets_host), _ptr(status_host),
+                                               _stream(stream)), "ofdm_radar_process_host")
+
+
+def ofdm_zc_precode(plan: Plan, inp, out, frames, inverse=False, stream=None):
+    return _check(_lib.ofdm_zc_precode(plan.handle, _ptr(inp), _ptr(out), frames, int(bool(inverse)),
+                                       _stream(stream)), "ofdm_zc_precode")
+
+
+def ofdm_radar_range_profile(plan: Plan, Y, X, frames, strip, stream=None):
+    return _check(_lib.ofdm_radar_range_profile(plan.handle, _ptr(Y), _ptr(X), frames, _ptr(strip),
+                                                _stream(stream)), "ofdm_radar_range_profile")
+
+
+def ofdm_radar_doppler(plan: Plan, strip, frames, out_map, stream=None):
+    return _check(_lib.ofdm_radar_doppler(plan.handle, _ptr(strip), frames, _ptr(out_map),
+                                          _stream(stream)), "ofdm_radar_doppler")
+
+
+def ofdm_radar_detect(plan: Plan, map_, frames, out_targets=None, n_targets=None, status=None,
+                      stream=None):
+    return _check(_lib.ofdm_radar_detect(plan.handle, _ptr(map_), frames, _ptr(out_targets),
+                                         _ptr(n_targets), _ptr(status), _stream(stream)),
+                  "ofdm_radar_detect")
+
+
+def targets_view(raw, frames, max_targets):
+    """Decode a uint8 tensor/array of [frames][max_targets] ofdm_target records
+    into numpy arrays (r, s, power, range_m, vel_mps)."""
+    import numpy as np
+    dt = np.dtype([("r", "<i4"), ("s", "<i4"), ("power", "<f4"), ("range_m", "<f4"),
+                   ("vel_mps", "<f4")])
+    a = raw.cpu().numpy() if hasattr(raw, "cpu") else np.asarray(raw)
+    return a.view(dt).reshape(frames, max_targets)
+
+
+# ------------------------------------------------------------- torch helpers
+def alloc_outputs(plan: Plan, frames: int, device="cuda", with_map=True):
+    import torch
+    out = {
+        "map": torch.empty((frames, plan.Np, plan.Mp), dtype=torch.float32, device=device)
+        if with_map else None,
+        "targets": torch.zeros((frames * plan.max_targets * TARGET_BYTES,), dtype=torch.uint8,
+                               device=device),
+        "n_targets": torch.zeros((frames,), dtype=torch.int32, device=device),
+        "status": torch.zeros((frames,), dtype=torch.int32, device=device),
+    }
+    return out
+
+
+def process(plan: Plan, Y, X, frames=None, with_map=True, stream=None):
+    """Run the chain on complex64 CUDA tensors [frames, M, N]; returns the outputs dict."""
+    frames = Y.shape[0] if frames is None else frames
+    out = alloc_outputs(plan, frames, Y.device, with_map)
+    ofdm_radar_process(plan, Y, X, frames, out["map"], out["targets"], out["n_targets"],
+                       out["status"], stream)
+    return out

@@ -1,0 +1,66 @@
+"""CPU-side checks of the C ABI: the library builds, loads and exports every
+function the header declares; parameter validation rejects bad plans before
+any device work.  No kernel is launched here."""
+import ctypes
+
+import pytest
+
+import __graft_entry__
+
+
+@pytest.fixture(scope="module")
+def radar():
+    __graft_entry__.build()
+    from paper_2209_03883_gb300 import radar as r
+    return r
+
+
+def test_exports_every_declared_function(radar):
+    names = radar.declared_functions()
+    assert len(names) >= 12
+    lib = radar.lib()
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in include/ofdm_radar.h but not exported"
+
+
+def test_struct_layouts(radar):
+    assert ctypes.sizeof(radar.Params) == 16 * 4 + 2 * 8
+    assert ctypes.sizeof(radar.Target) == 20
+
+
+def test_default_params(radar):
+    p = radar.default_params()
+    assert p.zc_root == 1 and p.window == radar.WINDOW_HANN and p.max_targets == 8
+    assert abs(p.pfa - 1e-2) < 1e-9 and p.fc_hz == 77e9 and p.df_hz == 240e3
+
+
+BAD = [
+    (dict(N=1000, M=256, L_cp=128), -2),      # N not a power of two
+    (dict(N=8192, M=256, L_cp=128), -2),      # N too large
+    (dict(N=1024, M=8, L_cp=128), -2),        # M too small
+    (dict(N=1024, M=256, L_cp=0), -1),
+    (dict(N=1024, M=256, L_cp=2048), -1),
+    (dict(N=1024, M=256, L_cp=128, zc_root=2), -1),   # even root is not coprime to N^2
+    (dict(N=1024, M=256, L_cp=128, window=7), -1),
+    (dict(N=1024, M=256, L_cp=128, max_targets=0), -1),
+    (dict(N=1024, M=256, L_cp=128, max_targets=33), -1),
+    (dict(N=1024, M=256, L_cp=128, max_frames=0), -1),
+    (dict(N=1024, M=256, L_cp=128, pfa=0.0), -1),
+    (dict(N=1024, M=256, L_cp=128, N_pad=2048), -2),  # range padding not built
+    (dict(N=1024, M=256, L_cp=128, M_pad=200), -2),
+]
+
+
+@pytest.mark.parametrize("kw,code", BAD)
+def test_plan_rejects_bad_params(radar, kw, code):
+    with pytest.raises(radar.OfdmError) as ei:
+        radar.Plan(**kw)
+    assert ei.value.code == code
+
+
+def test_null_arguments_rejected(radar):
+    lib = radar.lib()
+    assert lib.ofdm_radar_process(None, None, None, 1, None, None, None, None, None) == -1
+    assert lib.ofdm_zc_precode(None, None, None, 1, 0, None) == -1
+    assert lib.ofdm_radar_plan_create(None, None) == -1
+    assert lib.ofdm_radar_strerror(-2).decode() == "unsupported size"

@@ -1,0 +1,312 @@
+"""GPU parity of the CUDA chain against the FP64 oracle, through the C ABI.
+
+Every step is compared element by element on seeded frames: the ZC
+transform, the range-profile strip (steps a1-a5), the full periodogram
+(a6) and the detections (a7), on the five workloads' shapes (the largest
+on sampled outputs) and on the edge cases of the method.
+"""
+import numpy as np
+import pytest
+
+import ofdm_synth as syn
+from oracle import ofdm_oracle as o
+from radar_cases import (MAP_TOL, check_detections_vs_fp64, make_frames, oracle_params,
+                               plan_kwargs, rel_l2, stack_lk)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2209_03883_gb300 import radar
+    return radar, torch, torch.device("cuda:0")
+
+
+def to_dev(torch, dev, arr):
+    return torch.from_numpy(np.ascontiguousarray(arr)).to(dev)
+
+
+def run_chain(env, p, Ys, As, with_map=True, plan=None):
+    radar, torch, dev = env
+    frames = len(Ys)
+    plan = plan or radar.Plan(**plan_kwargs(p, frames))
+    Y = to_dev(torch, dev, stack_lk(Ys))
+    X = to_dev(torch, dev, stack_lk(As))
+    out = radar.process(plan, Y, X, with_map=with_map)
+    torch.cuda.synchronize()
+    res = dict(plan=plan,
+               map=out["map"].cpu().numpy() if with_map else None,
+               tg=radar.targets_view(out["targets"], frames, p.max_targets),
+               n=out["n_targets"].cpu().numpy(), status=out["status"].cpu().numpy().view(np.uint32),
+               launches=plan.last_launch_count())
+    return res
+
+
+def gpu_strip(env, p, Ys, As):
+    radar, torch, dev = env
+    frames = len(Ys)
+    plan = radar.Plan(**plan_kwargs(p, frames))
+    rows = plan.support_rows()
+    Y = to_dev(torch, dev, stack_lk(Ys))
+    X = to_dev(torch, dev, stack_lk(As))
+    strip = torch.empty((frames, len(rows), p.M), dtype=torch.complex64, device=dev)
+    radar.ofdm_radar_range_profile(plan, Y, X, frames, strip)
+    torch.cuda.synchronize()
+    return rows, strip.cpu().numpy()
+
+
+def oracle_strip(p, Y, A):
+    ref = o.process(Y, A, p)
+    return ref["g"], ref
+
+
+# ------------------------------------------------------------------ ZC transform
+@pytest.mark.parametrize("N,M,r,q", [(1024, 256, 1, 0), (256, 16, 3, 2), (64, 16, 5, 1),
+                                     (4096, 16, 1, 0), (2048, 16, 7, 3)])
+def test_zc_precode_forward_inverse(env, N, M, r, q):
+    radar, torch, dev = env
+    rng = np.random.default_rng(N + r)
+    A = syn.qam_symbols(rng, (N, M), 16)
+    p = o.Params(N=N, M=M, L_cp=N // 8, zc_root=r, zc_q=q)
+    plan = radar.Plan(**plan_kwargs(p, 1))
+    Ad = to_dev(torch, dev, syn.to_lk(A)[None])
+    Xd = torch.empty_like(Ad)
+    Bd = torch.empty_like(Ad)
+    radar.ofdm_zc_precode(plan, Ad, Xd, 1, inverse=False)
+    radar.ofdm_zc_precode(plan, Xd, Bd, 1, inverse=True)
+    torch.cuda.synchronize()
+    want = o.zc_precode(A, r, q)
+    got = Xd[0].cpu().numpy().T
+    assert rel_l2(got, want) < MAP_TOL
+    back = Bd[0].cpu().numpy().T
+    assert rel_l2(back, o.zc_precode(got.astype(np.complex128), r, q, inverse=True)) < MAP_TOL
+    assert rel_l2(back, A) < 2 * MAP_TOL
+
+
+# ------------------------------------------------------------------ range profile (a1-a5)
+@pytest.mark.parametrize("ci,frames", [(1, 1), (2, 2), (3, 1)])
+def test_range_profile_matches_oracle(env, ci, frames):
+    cfg, fr = make_frames(ci, frames)
+    p = oracle_params(cfg)
+    rows, strip = gpu_strip(env, p, [f[2] for f in fr], [f[0].A for f in fr])
+    for i, (frm, Xp, Y) in enumerate(fr):
+        g, _ = oracle_strip(p, Y, frm.A)
+        assert rel_l2(strip[i], g[rows, :]) < MAP_TOL
+        others = np.setdiff1d(np.arange(cfg.N), rows)
+        assert np.max(np.abs(g[others])) < 1e-9 * np.max(np.abs(g)), "oracle support mismatch"
+
+
+# ------------------------------------------------------------------ full chain (a1-a7)
+@pytest.mark.parametrize("ci,frames", [(1, 1), (2, 3), (3, 2)])
+def test_chain_matches_oracle(env, ci, frames):
+    cfg, fr = make_frames(ci, frames)
+    p = oracle_params(cfg)
+    res = run_chain(env, p, [f[2] for f in fr], [f[0].A for f in fr])
+    assert res["launches"] >= 3
+    for i, (frm, Xp, Y) in enumerate(fr):
+        ref = o.process(Y, frm.A, p)
+        assert rel_l2(res["map"][i], ref["P"]) < MAP_TOL
+        n = int(res["n"][i])
+        rs = [(int(t["r"]), int(t["s"])) for t in res["tg"][i][:n]]
+        check_detections_vs_fp64(rs, res["tg"][i]["power"][:n], ref["det"])
+        # the detection step itself is exact on the GPU's own map (same FP32 decisions)
+        det32 = o.detect(res["map"][i], p.detect_mode, p.max_targets)
+        assert rs == list(zip(det32.r.tolist(), det32.s.tolist()))
+        assert np.array_equal(res["tg"][i]["power"][:n], det32.power.astype(np.float32))
+        assert int(res["status"][i]) == det32.status
+
+
+def test_chain_full_batch_sampled(env):
+    """The benchmark's launch: 64 frames of 1024 x 256 in one call; frames
+    0, 31 and 63 are checked in full against the oracle."""
+    cfg, fr = make_frames(2, 64)
+    p = oracle_params(cfg)
+    res = run_chain(env, p, [f[2] for f in fr], [f[0].A for f in fr])
+    for i in (0, 31, 63):
+        frm, Xp, Y = fr[i]
+        ref = o.process(Y, frm.A, p)
+        assert rel_l2(res["map"][i], ref["P"]) < MAP_TOL
+        n = int(res["n"][i])
+        rs = [(int(t["r"]), int(t["s"])) for t in res["tg"][i][:n]]
+        check_detections_vs_fp64(rs, res["tg"][i]["power"][:n], ref["det"])
+    # every frame finds its targets (one-bin tolerance for off-grid truth)
+    hits = 0
+    for i, (frm, _, _) in enumerate(fr):
+        n = int(res["n"][i])
+        got = [(int(t["r"]), int(t["s"])) for t in res["tg"][i][:n]]
+        for rho, nu in zip(frm.rho, frm.nu):
+            hits += any(abs(r - rho) <= 1.0 and abs(((s - nu) + 128) % 256 - 128) <= 1.0 for r, s in got)
+    assert hits >= 0.8 * 5 * 64
+
+
+def test_largest_workload_sampled(env):
+    """4096 x 1024 with L_cp = 512: the strip is checked on sampled symbols
+    against the oracle computed column by column."""
+    radar, torch, dev = env
+    cfg = syn.CONFIGS[5]
+    fr = syn.draw_frame(cfg, syn.seed_for(5, 0))
+    Xp = o.zc_precode(fr.A, 1)
+    Y = syn.received(fr, Xp)
+    p = oracle_params(cfg)
+    rows, strip = gpu_strip(env, p, [Y], [fr.A])
+    cols = [0, 1, 511, 1023]
+    F, _ = o.ls_divide(Y[:, cols], Xp[:, cols])
+    Hd, _ = o.dft_ce(F, p.L_cp)
+    g = o.range_profile(Hd, o.window(p.N, p.window))
+    assert rel_l2(strip[0][:, cols], g[rows, :]) < MAP_TOL
+
+
+# ------------------------------------------------------------------ variants and edge cases
+VARIANTS = [
+    ("lcp_eq_N_rect", dict(N=64, M=16, L_cp=64, window=o.WINDOW_RECT)),
+    ("lcp_eq_N_hann", dict(N=128, M=32, L_cp=128, window=o.WINDOW_HANN)),
+    ("lcp_N_minus_1_hann", dict(N=64, M=64, L_cp=63, window=o.WINDOW_HANN)),
+    ("hamming", dict(N=256, M=64, L_cp=32, window=o.WINDOW_HAMMING)),
+    ("no_zcp", dict(N=512, M=128, L_cp=64, zc_root=0)),
+    ("zc_root3_q2", dict(N=256, M=32, L_cp=32, zc_root=3, zc_q=2)),
+    ("doppler_pad", dict(N=256, M=64, L_cp=32, M_pad=128)),
+    ("n2048", dict(N=2048, M=64, L_cp=256)),
+    ("n4096_m16", dict(N=4096, M=16, L_cp=512, window=o.WINDOW_RECT)),
+    ("m32_direct", dict(N=128, M=32, L_cp=16)),
+    ("lcp_1", dict(N=64, M=16, L_cp=1, window=o.WINDOW_HANN)),
+]
+
+
+@pytest.mark.parametrize("name,kw", VARIANTS, ids=[v[0] for v in VARIANTS])
+def test_variants(env, name, kw):
+    base = syn.FrameConfig(N=kw["N"], M=kw["M"], L_cp=kw["L_cp"], qam=16,
+                           zc_root=kw.get("zc_root", 1), n_targets=3, on_grid=False,
+                           amp_db=(-6.0, 0.0), snr_db=(0.0, 0.0), window=kw.get("window", 1),
+                           detect_k=4)
+    if kw["L_cp"] < 8:
+        base.n_targets = 0
+    frames = 2
+    fr = []
+    for f in range(frames):
+        d = syn.draw_frame(base, 7000 + f, n_targets=base.n_targets)
+        Xp = o.zc_precode(d.A, base.zc_root, kw.get("zc_q", 0)) if base.zc_root else d.A
+        fr.append((d, Xp, syn.received(d, Xp)))
+    p = o.Params(N=kw["N"], M=kw["M"], L_cp=kw["L_cp"], zc_root=base.zc_root, zc_q=kw.get("zc_q", 0),
+                 window=base.window, max_targets=4, M_pad=kw.get("M_pad", 0))
+    res = run_chain(env, p, [f[2] for f in fr], [f[0].A for f in fr])
+    for i, (d, Xp, Y) in enumerate(fr):
+        ref = o.process(Y, d.A, p)
+        assert rel_l2(res["map"][i], ref["P"]) < MAP_TOL, name
+        det32 = o.detect(res["map"][i], p.detect_mode, p.max_targets)
+        n = int(res["n"][i])
+        assert [(int(t["r"]), int(t["s"])) for t in res["tg"][i][:n]] == \
+            list(zip(det32.r.tolist(), det32.s.tolist()))
+
+
+def test_x_is_precoded_equals_internal_precoding(env):
+    cfg, fr = make_frames(1, 1)
+    frm, Xp, Y = fr[0]
+    p = oracle_params(cfg)
+    a = run_chain(env, p, [Y], [frm.A])
+    p2 = oracle_params(cfg, x_is_precoded=True)
+    b = run_chain(env, p2, [Y], [Xp])
+    assert rel_l2(b["map"][0], a["map"][0]) < MAP_TOL
+
+
+def test_threshold_mode(env):
+    cfg, fr = make_frames(2, 2)
+    for noise_var in (-1.0, 40.0):
+        p = oracle_params(cfg, detect_mode=o.DETECT_THRESHOLD, max_targets=16, noise_var=noise_var)
+        res = run_chain(env, p, [f[2] for f in fr], [f[0].A for f in fr])
+        rows = o.support_rows(p.N, p.L_cp, p.window)
+        for i in range(2):
+            P32 = res["map"][i]
+            # the library takes P_fa as float32; the oracle gets the same value
+            eta = o.threshold(P32, rows, float(np.float32(p.pfa)), p.noise_var)
+            det32 = o.detect(P32, o.DETECT_THRESHOLD, p.max_targets, eta)
+            n = int(res["n"][i])
+            assert [(int(t["r"]), int(t["s"])) for t in res["tg"][i][:n]] == \
+                list(zip(det32.r.tolist(), det32.s.tolist()))
+            assert int(res["status"][i]) == det32.status
+
+
+def test_zero_and_nonfinite_cells_flagged(env):
+    cfg, fr = make_frames(1, 2)
+    p = oracle_params(cfg, zc_root=0)
+    A0 = fr[0][0].A.copy()
+    A0[5, 3] = 0.0                       # a zero transmit cell
+    Y1 = fr[1][2].copy()
+    Y1[7, 2] = np.nan                    # a non-finite received cell
+    res = run_chain(env, p, [fr[0][2], Y1], [A0, fr[1][0].A])
+    assert res["status"][0] & o.STATUS_ZERO_X
+    assert not res["status"][0] & o.STATUS_NONFINITE
+    assert res["status"][1] & o.STATUS_NONFINITE
+    ref = o.process(fr[0][2], A0, p)     # F = 0 at the zero cell on both sides
+    assert rel_l2(res["map"][0], ref["P"]) < MAP_TOL
+    # status words do not leak into the next call on the same plan
+    res2 = run_chain(env, p, [fr[0][2], fr[1][2]], [fr[0][0].A, fr[1][0].A], plan=res["plan"])
+    assert (res2["status"] & (o.STATUS_ZERO_X | o.STATUS_NONFINITE) == 0).all()
+
+
+def test_noiseless_point_target_lands_on_its_bin(env):
+    N, M = 1024, 256
+    rng = np.random.default_rng(11)
+    A = syn.qam_symbols(rng, (N, M), 16)
+    Xp = o.zc_precode(A, 1)
+    H = syn.channel([37.0], [-21.0], [1.0], N, M)
+    p = o.Params(N=N, M=M, L_cp=128, window=o.WINDOW_HANN, max_targets=1)
+    res = run_chain(env, p, [Xp * H], [A])
+    t = res["tg"][0][0]
+    assert (int(t["r"]), int(t["s"])) == (37, -21)
+    assert abs(t["power"] - N * M / 16) < 1e-4 * N * M / 16
+    Ts = o.symbol_time(N, 128, 240e3)
+    dd, dv = o.resolution(N, M, 240e3, 77e9, Ts)
+    assert t["range_m"] == pytest.approx(37 * dd, rel=1e-5)
+    assert t["vel_mps"] == pytest.approx(-21 * dv, rel=1e-5)
+
+
+def test_detect_entry_point_on_given_map(env):
+    radar, torch, dev = env
+    cfg, fr = make_frames(1, 1)
+    p = oracle_params(cfg)
+    ref = o.process(fr[0][2], fr[0][0].A, p)
+    P32 = ref["P"].astype(np.float32)
+    plan = radar.Plan(**plan_kwargs(p, 1))
+    out = radar.alloc_outputs(plan, 1, dev, with_map=False)
+    radar.ofdm_radar_detect(plan, to_dev(torch, dev, P32[None]), 1, out["targets"], out["n_targets"],
+                            out["status"])
+    torch.cuda.synchronize()
+    det32 = o.detect(P32, p.detect_mode, p.max_targets)
+    tg = radar.targets_view(out["targets"], 1, p.max_targets)[0]
+    n = int(out["n_targets"][0])
+    assert [(int(t["r"]), int(t["s"])) for t in tg[:n]] == list(zip(det32.r.tolist(), det32.s.tolist()))
+
+
+def test_host_buffer_path_matches_device_path(env):
+    radar, torch, dev = env
+    cfg, fr = make_frames(2, 8)
+    p = oracle_params(cfg)
+    dres = run_chain(env, p, [f[2] for f in fr], [f[0].A for f in fr])
+    plan = radar.Plan(**plan_kwargs(p, 8))
+    Yh = torch.from_numpy(stack_lk([f[2] for f in fr])).pin_memory()
+    Xh = torch.from_numpy(stack_lk([f[0].A for f in fr])).pin_memory()
+    mh = torch.empty((8, p.N, p.M), dtype=torch.float32).pin_memory()
+    th = torch.zeros((8 * p.max_targets * radar.TARGET_BYTES,), dtype=torch.uint8).pin_memory()
+    nh = torch.zeros((8,), dtype=torch.int32).pin_memory()
+    sh = torch.zeros((8,), dtype=torch.int32).pin_memory()
+    radar.ofdm_radar_process_host(plan, Yh, Xh, 8, mh, th, nh, sh)
+    assert np.array_equal(mh.numpy(), dres["map"])
+    assert np.array_equal(nh.numpy(), dres["n"])
+    tv = radar.targets_view(th, 8, p.max_targets)
+    for i in range(8):
+        n = int(nh[i])
+        assert np.array_equal(tv[i][:n], dres["tg"][i][:n])
+
+
+def test_frames_out_of_range_rejected(env):
+    radar, torch, dev = env
+    p = o.Params(N=64, M=16, L_cp=8)
+    plan = radar.Plan(**plan_kwargs(p, 2))
+    Y = torch.zeros((3, 16, 64), dtype=torch.complex64, device=dev)
+    with pytest.raises(radar.OfdmError):
+        radar.process(plan, Y, Y, frames=3)

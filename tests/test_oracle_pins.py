@@ -329,3 +329,15 @@ def test_pins_catch_planted_mistakes(name, monkeypatch):
         except (AssertionError, ValueError, IndexError):
             caught += 1
     assert caught > 0, f"planted mistake {name} went unnoticed"
+
+
+@pytest.mark.parametrize("N,L,w", [(64, 8, 0), (64, 8, 1), (64, 62, 1), (64, 63, 1), (64, 64, 0), (64, 63, 0)])
+def test_support_rows_cover_nonzero_rows_once(N, L, w):
+    rng = np.random.default_rng(N + L)
+    H = rng.standard_normal((N, 4)) + 1j * rng.standard_normal((N, 4))
+    Hd, _ = o.dft_ce(H, L)
+    g = o.range_profile(Hd, o.window(N, w))
+    rows = o.support_rows(N, L, w)
+    assert len(set(rows.tolist())) == len(rows)
+    nz = np.flatnonzero(np.abs(g).max(axis=1) > 1e-9 * np.abs(g).max())
+    assert set(nz.tolist()) <= set(rows.tolist())
