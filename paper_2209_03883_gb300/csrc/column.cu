@@ -28,6 +28,223 @@ struct ColCfg {
   static constexpr size_t SMEM = (size_t)GROUPS * smem_elems(N) * sizeof(float2);
 };
 
+// Pipelined configuration for N <= 1024 (one warp per symbol): each warp
+// owns two stages of [A row (+ FFT exchange padding) | Y row] in shared
+// memory; the next symbol's stage streams in with cp.async while the
+// current one is computed.
+template <int N>
+struct PipeCfg {
+  static constexpr int E = N / 32;
+  static constexpr int STAGE = smem_elems(N) + N;  // float2 per stage
+  static constexpr int FIT = (int)((227u * 1024u) / (2u * STAGE * sizeof(float2)));
+  static constexpr int WARPS = FIT < 8 ? FIT : 8;
+  static constexpr int THREADS = 32 * WARPS;
+  static constexpr size_t SMEM = (size_t)WARPS * 2 * STAGE * sizeof(float2);
+};
+
+__device__ __forceinline__ uint64_t evict_first_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src, uint64_t pol) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem_src), "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int K>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(K) : "memory"); }
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// B_i = sum_k pre_k A_k exp(+2 pi i r' i k / N) in double-float by the whole
+// warp (lane handles k = lane, lane + 32, ...), rounded once to float.  Used
+// for precoded cells so small that the FP32 FFT's normwise rounding would be
+// amplified by the LS division (|X_p|^2 < tau * mean).
+template <int N>
+__device__ __noinline__ float2 refine_cell(const float2* __restrict__ x, int i, const ColumnArgs& a, int lane) {
+  cdf acc = {{0.f, 0.f}, {0.f, 0.f}};
+  for (int k = lane; k < N; k += 32) {
+    const cdf b = cdf_mulf(cdf_ld(a.pre_df + k), __ldg(x + k));
+    const unsigned m = ((unsigned)a.rprime * (unsigned)i * (unsigned)k) & (unsigned)(N - 1);
+    acc = cdf_add(acc, cdf_mul(b, cdf_ld(a.w_df + m)));
+  }
+#pragma unroll
+  for (int off = 16; off; off >>= 1) {
+    acc.re = df_add(acc.re, df_shfl_xor(acc.re, off));
+    acc.im = df_add(acc.im, df_shfl_xor(acc.im, off));
+  }
+  return make_float2(acc.re.hi + acc.re.lo, acc.im.hi + acc.im.lo);
+}
+
+// After the ZC FFT: find this warp's ill-conditioned cells and recompute them.
+// Thread t of a T-thread group holds positions i = t + T q.
+template <int N, int T, int E>
+__device__ __forceinline__ void refine_small_cells(float2* v, const float2* __restrict__ x, const ColumnArgs& a,
+                                                   int t, int lane) {
+  float s2 = 0.f;
+#pragma unroll
+  for (int q = 0; q < E; ++q) s2 += v[q].x * v[q].x + v[q].y * v[q].y;
+#pragma unroll
+  for (int off = 16; off; off >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+  const float thr = a.refine_tau * s2 * (1.f / (32.f * E));
+  unsigned flags = 0;
+#pragma unroll
+  for (int q = 0; q < E; ++q) flags |= (v[q].x * v[q].x + v[q].y * v[q].y < thr) ? (1u << q) : 0u;
+  unsigned pending = __ballot_sync(0xffffffffu, flags != 0);
+  while (pending) {
+    const int src = __ffs(pending) - 1;
+    const unsigned fm = __shfl_sync(0xffffffffu, flags, src);
+    const int q = __ffs(fm) - 1;
+    const int tsrc = __shfl_sync(0xffffffffu, t, src);
+    const float2 val = refine_cell<N>(x, tsrc + T * q, a, lane);
+    if (lane == src) {
+#pragma unroll
+      for (int qq = 0; qq < E; ++qq)
+        if (qq == q) v[qq] = val;
+      flags &= ~(1u << q);
+    }
+    pending = __ballot_sync(0xffffffffu, flags != 0);
+  }
+}
+
+// F_i = Y_i / X_p,i with X_p,i = post_i B_i / sqrt(N), B in v:
+//   F_i = Y_i conj(post_i) sqrt(N) conj(B_i) / |B_i|^2   (Eq. (16)).
+template <int T, int E>
+__device__ __forceinline__ uint32_t divide_precoded(float2* v, const float2* yrow, bool y_in_smem,
+                                                    const ColumnArgs& a, int t) {
+  uint32_t flags = 0;
+  const float sgn = (a.post_sign && (t & 1)) ? -a.sqrtN : a.sqrtN;
+#pragma unroll
+  for (int q = 0; q < E; ++q) {
+    const int i = t + T * q;
+    float2 yv = y_in_smem ? yrow[i] : ld_stream(yrow + i);
+    if (!a.post_sign) yv = cmul(yv, __ldg(a.post_conj + i));
+    const float d2 = v[q].x * v[q].x + v[q].y * v[q].y;
+    flags |= (d2 == 0.f) ? OFDM_STATUS_ZERO_X : 0u;
+    const float inv = (d2 > 0.f) ? sgn * rcp_approx(d2) : 0.f;
+    v[q] = cscale(cmulc(yv, v[q]), inv);
+  }
+  return flags;
+}
+
+template <int T, int E>
+__device__ __forceinline__ uint32_t divide_plain(float2* v, const float2* xrow, const float2* yrow, bool in_smem,
+                                                 int t) {
+  uint32_t flags = 0;
+#pragma unroll
+  for (int q = 0; q < E; ++q) {
+    const int i = t + T * q;
+    const float2 xv = in_smem ? xrow[i] : ld_stream(xrow + i);
+    const float2 yv = in_smem ? yrow[i] : ld_stream(yrow + i);
+    const float d2 = xv.x * xv.x + xv.y * xv.y;
+    flags |= (d2 == 0.f) ? OFDM_STATUS_ZERO_X : 0u;
+    const float inv = (d2 > 0.f) ? rcp_approx(d2) : 0.f;
+    v[q] = cscale(cmulc(yv, xv), inv);
+  }
+  return flags;
+}
+
+// Keep taps n < L_cp (Eq. (21)) and write the support rows of the windowed
+// range profile, g[r] = c0 h[r] + c1 (h[r-1] + h[r+1]) (Eqs. (17), (22)).
+template <int N, int T, int E>
+__device__ __forceinline__ uint32_t stencil_write(const float2* v, float2* sm, float2* __restrict__ strip,
+                                                  const ColumnArgs& a, int f, int l, int t, int group) {
+  group_sync<T>(group);  // the last FFT pass finished reading sm
+#pragma unroll
+  for (int q = 0; q < E; ++q) {
+    const int n = t + T * q;
+    if (n < a.L_cp) sm[pad32(n)] = v[q];
+  }
+  group_sync<T>(group);
+  uint32_t flags = 0;
+  for (int ri = t; ri < a.rows; ri += T) {
+    const int r = (a.row0 + ri) & (N - 1);
+    const int rm = (r - 1) & (N - 1), rp = (r + 1) & (N - 1);
+    const float2 z = make_float2(0.f, 0.f);
+    const float2 h0 = r < a.L_cp ? sm[pad32(r)] : z;
+    const float2 hm = rm < a.L_cp ? sm[pad32(rm)] : z;
+    const float2 hp = rp < a.L_cp ? sm[pad32(rp)] : z;
+    float2 g;
+    g.x = a.c0 * h0.x + a.c1 * (hm.x + hp.x);
+    g.y = a.c0 * h0.y + a.c1 * (hm.y + hp.y);
+    flags |= (isfinite(g.x) && isfinite(g.y)) ? 0u : OFDM_STATUS_NONFINITE;
+    strip[((long)f * a.rows + ri) * a.M + l] = g;
+  }
+  return flags;
+}
+
+// ---------------------------------------------------------------- N <= 1024: pipelined, one warp per symbol
+template <int N>
+__global__ void __launch_bounds__(PipeCfg<N>::THREADS)
+column_pipe_kernel(const float2* __restrict__ Y, const float2* __restrict__ X, float2* __restrict__ strip,
+                   uint32_t* __restrict__ wstatus, ColumnArgs a) {
+  using C = PipeCfg<N>;
+  constexpr int E = C::E;
+  extern __shared__ float2 smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float2* base = smem + (size_t)warp * 2 * C::STAGE;
+  const long total = (long)a.frames * a.M;
+  const long stride = (long)gridDim.x * C::WARPS;
+  const uint64_t pol = evict_first_policy();
+
+  auto issue = [&](long sym, float2* st) {
+    const char* ga = reinterpret_cast<const char*>(X + sym * N);
+    const char* gy = reinterpret_cast<const char*>(Y + sym * N);
+    char* sa = reinterpret_cast<char*>(st);
+    char* sy = reinterpret_cast<char*>(st + smem_elems(N));
+#pragma unroll
+    for (int c = lane; c < N / 2; c += 32) {
+      cp_async16(sa + 16 * c, ga + 16 * c, pol);
+      cp_async16(sy + 16 * c, gy + 16 * c, pol);
+    }
+  };
+
+  long sym = (long)blockIdx.x * C::WARPS + warp;
+  if (sym < total) issue(sym, base);
+  cp_async_commit();
+  for (int it = 0; sym < total; ++it, sym += stride) {
+    float2* cur = base + (it & 1) * C::STAGE;
+    const long nxt = sym + stride;
+    if (nxt < total) issue(nxt, base + ((it + 1) & 1) * C::STAGE);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncwarp();
+    const int f = (int)(sym / a.M);
+    const int l = (int)(sym % a.M);
+    float2* sa = cur;                    // A row, then the FFT exchange buffer
+    const float2* sy = cur + smem_elems(N);
+    float2 v[E];
+    uint32_t flags = 0;
+    if (a.zc) {
+#pragma unroll
+      for (int q = 0; q < E; ++q) {
+        const int k = lane + 32 * q;
+        const int s = (a.rinv == 1) ? k : (int)(((unsigned)a.rinv * (unsigned)k) & (N - 1));
+        v[q] = cmul(sa[s], __ldg(a.pre + s));
+      }
+      group_fft<N, 32, +1>(v, sa, a.tw, lane, 0);
+      if (a.refine_tau > 0.f) refine_small_cells<N, 32, E>(v, X + sym * N, a, lane, lane);
+      flags |= divide_precoded<32, E>(v, sy, true, a, lane);
+    } else {
+      flags |= divide_plain<32, E>(v, sa, sy, true, lane);
+      __syncwarp();
+    }
+    group_fft<N, 32, +1>(v, sa, a.tw, lane, 0);   // N h[n] = sum_i F_i e^{+2 pi i n i / N} (Eq. (20))
+    flags |= stencil_write<N, 32, E>(v, sa, strip, a, f, l, lane, 0);
+    flags = __reduce_or_sync(0xffffffffu, flags);
+    if (lane == 0 && flags) atomicOr(wstatus + f, flags);
+    __syncwarp();  // every lane is done with this stage before it is refilled
+  }
+  cp_async_wait<0>();
+}
+
+// ---------------------------------------------------------------- N >= 2048: multi-warp groups
 template <int N>
 __global__ void __launch_bounds__(ColCfg<N>::THREADS)
 column_kernel(const float2* __restrict__ Y, const float2* __restrict__ X, float2* __restrict__ strip,
@@ -37,6 +254,7 @@ column_kernel(const float2* __restrict__ Y, const float2* __restrict__ X, float2
   extern __shared__ float2 smem[];
   const int group = threadIdx.x / T;
   const int t = threadIdx.x % T;
+  const int lane = threadIdx.x & 31;
   float2* sm = smem + group * smem_elems(N);
   const long total = (long)a.frames * a.M;
 
@@ -47,7 +265,6 @@ column_kernel(const float2* __restrict__ Y, const float2* __restrict__ X, float2
     const float2* y = Y + sym * N;
     float2 v[E];
     uint32_t flags = 0;
-
     if (a.zc) {
       // b~[k'] = pre[s] A[s], s = r'^{-1} k' mod N, so that the DFT below
       // yields B[r' i] = sum_k pre_k A_k e^{+2 pi i r' i k / N} at position i.
@@ -59,63 +276,14 @@ column_kernel(const float2* __restrict__ Y, const float2* __restrict__ X, float2
         v[q] = cmul(xv, __ldg(a.pre + s));
       }
       group_fft<N, T, +1>(v, sm, a.tw, t, group);
-      // F_i = Y_i / X_p,i with X_p,i = post_i B / sqrt(N):
-      //     F_i = Y_i conj(post_i) sqrt(N) conj(B) / |B|^2.
-#pragma unroll
-      for (int q = 0; q < E; ++q) {
-        const int i = t + T * q;
-        const float2 yv = cmul(ld_stream(y + i), __ldg(a.post_conj + i));
-        const float d2 = v[q].x * v[q].x + v[q].y * v[q].y;
-        flags |= (d2 == 0.f) ? OFDM_STATUS_ZERO_X : 0u;
-        const float inv = (d2 > 0.f) ? a.sqrtN / d2 : 0.f;
-        v[q] = cscale(cmulc(yv, v[q]), inv);
-      }
+      if (a.refine_tau > 0.f) refine_small_cells<N, T, E>(v, x, a, t, lane);
+      flags |= divide_precoded<T, E>(v, y, false, a, t);
     } else {
-#pragma unroll
-      for (int q = 0; q < E; ++q) {
-        const int i = t + T * q;
-        const float2 xv = ld_stream(x + i);
-        const float2 yv = ld_stream(y + i);
-        const float d2 = xv.x * xv.x + xv.y * xv.y;
-        flags |= (d2 == 0.f) ? OFDM_STATUS_ZERO_X : 0u;
-        const float inv = (d2 > 0.f) ? 1.f / d2 : 0.f;
-        v[q] = cscale(cmulc(yv, xv), inv);
-      }
+      flags |= divide_plain<T, E>(v, x, y, false, t);
     }
-
-    // N h[n] = sum_i F_i e^{+2 pi i n i / N}   (Eq. (20) times N)
     group_fft<N, T, +1>(v, sm, a.tw, t, group);
-
-    group_sync<T>(group);  // the last FFT pass finished reading sm
-#pragma unroll
-    for (int q = 0; q < E; ++q) {
-      const int n = t + T * q;
-      if (n < a.L_cp) sm[pad32(n)] = v[q];
-    }
-    group_sync<T>(group);
-
-    // g[r] = c0 h[r] + c1 (h[r-1] + h[r+1]), h zero beyond the kept taps.
-    for (int ri = t; ri < a.rows; ri += T) {
-      const int r = (a.row0 + ri) & (N - 1);
-      const int rm = (r - 1) & (N - 1), rp = (r + 1) & (N - 1);
-      const float2 z = make_float2(0.f, 0.f);
-      const float2 h0 = r < a.L_cp ? sm[pad32(r)] : z;
-      const float2 hm = rm < a.L_cp ? sm[pad32(rm)] : z;
-      const float2 hp = rp < a.L_cp ? sm[pad32(rp)] : z;
-      float2 g;
-      g.x = a.c0 * h0.x + a.c1 * (hm.x + hp.x);
-      g.y = a.c0 * h0.y + a.c1 * (hm.y + hp.y);
-      flags |= (isfinite(g.x) && isfinite(g.y)) ? 0u : OFDM_STATUS_NONFINITE;
-      strip[((long)f * a.rows + ri) * a.M + l] = g;
-    }
-
-    // One atomic per group and only when something was flagged.
-    if constexpr (T <= 32) {
-      flags = __reduce_or_sync(0xffffffffu, flags);
-      if (t == 0 && flags) atomicOr(wstatus + f, flags);
-    } else {
-      if (flags) atomicOr(wstatus + f, flags);
-    }
+    flags |= stencil_write<N, T, E>(v, sm, strip, a, f, l, t, group);
+    if (flags) atomicOr(wstatus + f, flags);
   }
 }
 
@@ -154,13 +322,30 @@ zct_kernel(const float2* __restrict__ in, float2* __restrict__ out, ZctArgs a) {
 template <int N>
 static cudaError_t launch_column_n(const float2* Y, const float2* X, float2* strip, uint32_t* wstatus,
                                    const ColumnArgs& a, cudaStream_t s) {
-  using C = ColCfg<N>;
-  cudaError_t e = cudaFuncSetAttribute(column_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)C::SMEM);
-  if (e != cudaSuccess) return e;
   const long total = (long)a.frames * a.M;
-  const long blocks = (total + C::GROUPS - 1) / C::GROUPS;
-  column_kernel<N><<<(unsigned)blocks, C::THREADS, C::SMEM, s>>>(Y, X, strip, wstatus, a);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if constexpr (N <= 1024) {
+    using C = PipeCfg<N>;
+    cudaError_t e = cudaFuncSetAttribute(column_pipe_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)C::SMEM);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, column_pipe_kernel<N>, C::THREADS, C::SMEM);
+    if (e != cudaSuccess) return e;
+    long blocks = (long)sms * (per_sm > 0 ? per_sm : 1);
+    const long need = (total + C::WARPS - 1) / C::WARPS;
+    if (blocks > need) blocks = need;
+    column_pipe_kernel<N><<<(unsigned)blocks, C::THREADS, C::SMEM, s>>>(Y, X, strip, wstatus, a);
+  } else {
+    using C = ColCfg<N>;
+    cudaError_t e = cudaFuncSetAttribute(column_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)C::SMEM);
+    if (e != cudaSuccess) return e;
+    const long blocks = (total + C::GROUPS - 1) / C::GROUPS;
+    column_kernel<N><<<(unsigned)blocks, C::THREADS, C::SMEM, s>>>(Y, X, strip, wstatus, a);
+  }
   return cudaGetLastError();
 }
 

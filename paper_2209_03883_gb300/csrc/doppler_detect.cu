@@ -87,60 +87,51 @@ __global__ void zero_rows_kernel(float* __restrict__ map, int frames, long frame
 
 // ---------------------------------------------------------------- detection
 constexpr int kDetThreads = 1024;
-
-__device__ __forceinline__ uint64_t shfl_u64(uint64_t v, int src) {
-  uint32_t lo = __shfl_sync(0xffffffffu, (uint32_t)v, src);
-  uint32_t hi = __shfl_sync(0xffffffffu, (uint32_t)(v >> 32), src);
-  return ((uint64_t)hi << 32) | lo;
-}
-__device__ __forceinline__ uint64_t shfl_up_u64(uint64_t v) {
-  uint32_t lo = __shfl_up_sync(0xffffffffu, (uint32_t)v, 1);
-  uint32_t hi = __shfl_up_sync(0xffffffffu, (uint32_t)(v >> 32), 1);
-  return ((uint64_t)hi << 32) | lo;
-}
-
-// Insert the lanes' candidate keys into the warp's descending top-K list
-// (lane i holds the i-th best key; 0 = empty).  Keys are unique.
-__device__ __forceinline__ void warp_topk_insert(uint64_t& list, uint64_t key, int K, int lane) {
-  uint64_t thresh = shfl_u64(list, K - 1);
-  unsigned m = __ballot_sync(0xffffffffu, key > thresh);
-  while (m) {
-    const int src = __ffs(m) - 1;
-    m &= m - 1;
-    const uint64_t kk = shfl_u64(key, src);
-    if (kk > thresh) {
-      const int p = __popc(__ballot_sync(0xffffffffu, list > kk));
-      const uint64_t up = shfl_up_u64(list);
-      if (lane > p) list = up;
-      else if (lane == p) list = kk;
-      if (lane >= K) list = 0;
-      thresh = shfl_u64(list, K - 1);
-    }
-  }
-}
+constexpr int kCandCap = 4096;   // shared-memory candidate keys (32 KB)
 
 __device__ __forceinline__ float det_value(const float* base, const DetectArgs& a, int ri, int c) {
   const int row = a.compact ? ri : (a.row0 + ri) % a.Np;
   return base[(long)row * a.Mp + c];
 }
 
+// Block-wide bitonic sort of buf[0..kCandCap) in DESCENDING key order.
+__device__ void bitonic_desc(uint64_t* buf) {
+  for (int k = 2; k <= kCandCap; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < kCandCap; i += kDetThreads) {
+        const int p = i ^ j;
+        if (p > i) {
+          const uint64_t a = buf[i], b = buf[p];
+          const bool desc = (i & k) == 0;
+          if (desc ? (a < b) : (a > b)) { buf[i] = b; buf[p] = a; }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Keys: (float bits of P) << 32 | ~(flat map index): descending key order is
+// power descending, then index ascending; 0 marks an empty slot.
 __global__ void __launch_bounds__(kDetThreads)
 detect_kernel(const float* __restrict__ src, ofdm_target* __restrict__ out, int32_t* __restrict__ n_out,
               uint32_t* __restrict__ status, uint32_t* __restrict__ wstatus, DetectArgs a) {
+  __shared__ uint64_t buf[kCandCap];
   __shared__ uint32_t hist[256];
-  __shared__ uint64_t lists[kDetThreads / 32][32];
-  __shared__ uint32_t s_prefix, s_rank, s_count;
+  __shared__ uint32_t s_prefix, s_rank, s_n, s_total;
+  __shared__ uint64_t s_floor;
   const int f = blockIdx.x;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x, lane = tid & 31;
   const float* base = src + (long)f * a.frame_stride;
   const int n = a.rows * a.Mp;
+  const int K = a.K;
 
   float eta = 0.f;
   if (a.mode == OFDM_DETECT_THRESHOLD) {
     if (a.use_fixed_eta) {
       eta = a.eta_fixed;
     } else {
-      // Lower median (rank (n-1)/2) of P over the scanned rows by an 8-bit
+      // Lower median (rank (n-1)/2) of P over the scanned rows: 8-bit
       // MSB-first radix select on the float bits (P >= 0 sorts as uint).
       if (tid == 0) { s_prefix = 0; s_rank = (uint32_t)(n - 1) / 2; }
       uint32_t mask = 0;
@@ -169,12 +160,10 @@ detect_kernel(const float* __restrict__ src, ofdm_target* __restrict__ out, int3
     }
   }
 
-  if (tid == 0) s_count = 0;
+  for (int i = tid; i < kCandCap; i += kDetThreads) buf[i] = 0;
+  if (tid == 0) { s_n = 0; s_total = 0; s_floor = 0; }
   __syncthreads();
 
-  uint64_t list = 0;
-  uint32_t count = 0;
-  const int K = a.K;
   for (int base_e = 0; base_e < n; base_e += kDetThreads) {
     const int e = base_e + tid;
     uint64_t key = 0;
@@ -205,31 +194,44 @@ detect_kernel(const float* __restrict__ src, ofdm_target* __restrict__ out, int3
         if (ok) key = ((uint64_t)__float_as_uint(p) << 32) | (uint64_t)(~idx);
       }
     }
-    count += key ? 1u : 0u;
-    warp_topk_insert(list, key, K, lane);
+    // count every candidate, keep only those above the current floor
+    const unsigned cand = __ballot_sync(0xffffffffu, key != 0);
+    if (lane == 0 && cand) atomicAdd(&s_total, (uint32_t)__popc(cand));
+    const bool keep = key != 0 && key > s_floor;
+    const unsigned km = __ballot_sync(0xffffffffu, keep);
+    uint32_t wbase = 0;
+    if (lane == 0 && km) wbase = atomicAdd(&s_n, (uint32_t)__popc(km));
+    wbase = __shfl_sync(0xffffffffu, wbase, 0);
+    if (keep) buf[wbase + __popc(km & ((1u << lane) - 1u))] = key;
+    __syncthreads();
+    const uint32_t nn = s_n;  // every thread takes the same decision below
+    __syncthreads();
+    // room for the next chunk of kDetThreads keys: compact to the best K
+    if (nn > (uint32_t)(kCandCap - kDetThreads)) {
+      bitonic_desc(buf);
+      for (int i = K + tid; i < kCandCap; i += kDetThreads) buf[i] = 0;
+      if (tid == 0) { s_n = K; s_floor = buf[K - 1]; }
+      __syncthreads();
+    }
   }
-  count = __reduce_add_sync(0xffffffffu, count);
-  if (lane == 0) atomicAdd(&s_count, count);
-  lists[warp][lane] = list;
-  __syncthreads();
+  bitonic_desc(buf);
 
-  if (warp == 0) {
-    for (int w = 1; w < kDetThreads / 32; ++w) warp_topk_insert(list, lists[w][lane], K, lane);
-    const bool valid = lane < K && list != 0;
+  if (tid < 32) {
+    const uint64_t key = lane < K ? buf[lane] : 0;
+    const bool valid = key != 0;
     const int nv = __popc(__ballot_sync(0xffffffffu, valid));
     if (valid && out) {
-      const uint32_t idx = ~(uint32_t)(list & 0xffffffffu);
-      const float p = __uint_as_float((uint32_t)(list >> 32));
+      const uint32_t idx = ~(uint32_t)(key & 0xffffffffu);
       ofdm_target tg;
       tg.r = (int32_t)(idx / (uint32_t)a.Mp);
       tg.s = (int32_t)(idx % (uint32_t)a.Mp) - a.Mp / 2;
-      tg.power = p;
+      tg.power = __uint_as_float((uint32_t)(key >> 32));
       tg.range_m = (float)tg.r * a.dd;
       tg.vel_mps = (float)tg.s * a.dv;
       out[(long)f * K + lane] = tg;
     }
     if (lane == 0) {
-      const uint32_t cnt = s_count;
+      const uint32_t cnt = s_total;
       uint32_t st = wstatus ? wstatus[f] : 0u;
       if (a.mode == OFDM_DETECT_TOPK && cnt < (uint32_t)K) st |= OFDM_STATUS_FEW_PEAKS;
       if (a.mode == OFDM_DETECT_THRESHOLD && cnt > (uint32_t)K) st |= OFDM_STATUS_OVERFLOW;

@@ -237,4 +237,55 @@ __device__ __forceinline__ void group_fft(float2* v, float2* sm, const float2* _
   run_passes<N, T, DIR>(v, sm, tw, t, group, std::make_integer_sequence<int, num_passes(N, N / T)>{});
 }
 
+// ---------------------------------------------------------------- double-float
+// Unevaluated pairs hi + lo of floats (about 48-bit significands) built from
+// the error-free transformations TwoSum (Knuth) and TwoProd (via FMA), after
+// Dekker, "A floating-point technique for extending the available precision"
+// (1971).  Used only to recompute the rare ill-conditioned precoded cells.
+struct dfl { float hi, lo; };
+struct cdf { dfl re, im; };
+
+__device__ __forceinline__ dfl df_quick(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dfl df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+  dfl s = df_two_sum(a.hi, b.hi);
+  return df_quick(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ dfl df_neg(dfl a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return df_quick(p, e);
+}
+__device__ __forceinline__ dfl df_mulf(dfl a, float b) {
+  const float p = __fmul_rn(a.hi, b);
+  const float e = __fmaf_rn(a.lo, b, __fmaf_rn(a.hi, b, -p));
+  return df_quick(p, e);
+}
+__device__ __forceinline__ cdf cdf_mul(cdf a, cdf b) {
+  return {df_add(df_mul(a.re, b.re), df_neg(df_mul(a.im, b.im))),
+          df_add(df_mul(a.re, b.im), df_mul(a.im, b.re))};
+}
+__device__ __forceinline__ cdf cdf_mulf(cdf a, float2 b) {
+  return {df_add(df_mulf(a.re, b.x), df_neg(df_mulf(a.im, b.y))),
+          df_add(df_mulf(a.re, b.y), df_mulf(a.im, b.x))};
+}
+__device__ __forceinline__ cdf cdf_add(cdf a, cdf b) { return {df_add(a.re, b.re), df_add(a.im, b.im)}; }
+__device__ __forceinline__ cdf cdf_ld(const float4* p) {
+  const float4 v = __ldg(p);
+  return {{v.x, v.y}, {v.z, v.w}};
+}
+__device__ __forceinline__ dfl df_shfl_xor(dfl a, int m) {
+  return {__shfl_xor_sync(0xffffffffu, a.hi, m), __shfl_xor_sync(0xffffffffu, a.lo, m)};
+}
+
 }  // namespace ofdm

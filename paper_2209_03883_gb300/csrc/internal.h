@@ -19,6 +19,11 @@ struct ColumnArgs {
   const float2* pre;       // [N] pre-chirp exp(i pi r'(k^2 + 2q'k)/N^2)
   const float2* post_conj; // [N] conj of the post factor (-1)^{r'i} exp(i 2 pi r'q' i/N)
   const float2* tw;        // N-point pass twiddles (DIR = +1)
+  int post_sign;           // 1: q' = 0, the post factor is (-1)^i (r' odd) and no table is read
+  int rprime;              // r'
+  float refine_tau;        // recompute precoded cells with |X_p|^2 < tau * mean in double-float; 0 = off
+  const float4* pre_df;    // [N] pre-chirp as double-float (re.hi, re.lo, im.hi, im.lo)
+  const float4* w_df;      // [N] exp(+2 pi i m / N) as double-float
 };
 
 struct ZctArgs {

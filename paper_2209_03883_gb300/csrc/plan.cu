@@ -24,6 +24,7 @@ struct ofdm_radar_plan {
   float c0, c1;
   float2* d_tables = nullptr;  // one allocation: pre, post, pre_conj, post_conj, twN, twM
   float2 *pre, *post, *pre_conj, *post_conj, *twN, *twM;
+  float4* d_df = nullptr;      // double-float pre-chirp [N] and roots of unity [N]
   float* d_wl = nullptr;
   float2* d_strip = nullptr;   // [max_frames][rows][M]
   float* d_pow = nullptr;      // [max_frames][rows][M']
@@ -46,6 +47,11 @@ struct ofdm_radar_plan {
 };
 
 namespace {
+// Precoded cells with |X_p|^2 below this fraction of the symbol's mean power
+// are recomputed in double-float (about 1e-4 of the cells for a ZC-precoded
+// QAM grid), which keeps the FP32 chain's error near FP32 rounding even when
+// the LS division meets a near-zero precoded cell.
+constexpr float kRefineTau = 1e-4f;
 constexpr int kMaxTimed = 4096;
 constexpr int kKinds = 5;  // column, zero_rows, doppler, detect, zct
 enum { K_COLUMN = 0, K_ZERO = 1, K_DOPPLER = 2, K_DETECT = 3, K_ZCT = 4 };
@@ -147,6 +153,7 @@ const char* ofdm_radar_strerror(int code) {
 void ofdm_radar_plan_destroy(ofdm_radar_plan* plan) {
   if (!plan) return;
   cudaFree(plan->d_tables);
+  cudaFree(plan->d_df);
   cudaFree(plan->d_wl);
   cudaFree(plan->d_strip);
   cudaFree(plan->d_pow);
@@ -217,10 +224,21 @@ int ofdm_radar_plan_create(const ofdm_radar_params* pin, ofdm_radar_plan** out) 
   const int r = p.zc_root ? p.zc_root : 1;
   const long long rr = mod_ll(r, two), qq = mod_ll(p.zc_q, two);
   std::vector<float2> pre(N), post(N), prec(N), postc(N);
+  std::vector<float4> df(2 * (size_t)N);  // [0, N): pre-chirp, [N, 2N): exp(+2 pi i m / N)
+  auto split = [](double v) {
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
+  };
+  auto df_phase = [&](double a) {
+    const float2 re = split(cos(a)), im = split(sin(a));
+    return make_float4(re.x, re.y, im.x, im.y);
+  };
+  for (int m = 0; m < N; ++m) df[(size_t)N + m] = df_phase(2.0 * M_PI * (double)m / (double)N);
   for (int j = 0; j < N; ++j) {
     const long long base = mod_ll((long long)j * j + 2 * qq % two * j % two, two);
     const long long m = (rr * base) % two;
     pre[j] = unit_phase(m, NN);
+    df[j] = df_phase(M_PI * (double)m / (double)NN);
     prec[j] = make_float2(pre[j].x, -pre[j].y);
   }
   for (int i = 0; i < N; ++i) {
@@ -255,6 +273,7 @@ int ofdm_radar_plan_create(const ofdm_radar_params* pin, ofdm_radar_plan** out) 
 
   const size_t ntab = 4 * (size_t)N + twN.size() + twM.size();
   cudaError_t e = dalloc(&pl->d_tables, ntab);
+  if (e == cudaSuccess) e = dalloc(&pl->d_df, 2 * (size_t)N);
   if (e == cudaSuccess) e = dalloc(&pl->d_wl, (size_t)M);
   if (e == cudaSuccess) e = dalloc(&pl->d_strip, (size_t)p.max_frames * pl->rows * M);
   if (e == cudaSuccess) e = dalloc(&pl->d_pow, (size_t)p.max_frames * pl->rows * Mp);
@@ -279,6 +298,7 @@ int ofdm_radar_plan_create(const ofdm_radar_params* pin, ofdm_radar_plan** out) 
   memcpy(host.data() + 4 * N + twN.size(), twM.data(), twM.size() * sizeof(float2));
   e = cudaMemcpy(pl->d_tables, host.data(), ntab * sizeof(float2), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(pl->d_wl, wl.data(), M * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(pl->d_df, df.data(), df.size() * sizeof(float4), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(pl->d_wstatus, 0, (size_t)p.max_frames * sizeof(uint32_t));
   if (e != cudaSuccess) {
     ofdm_radar_plan_destroy(pl);
@@ -354,6 +374,11 @@ ColumnArgs column_args(const ofdm_radar_plan* pl, int frames) {
   a.pre = pl->pre;
   a.post_conj = pl->post_conj;
   a.tw = pl->twN;
+  a.post_sign = (mod_ll(pl->p.zc_q, pl->p.N) == 0) ? 1 : 0;
+  a.rprime = pl->p.zc_root > 0 ? pl->p.zc_root : 1;
+  a.refine_tau = kRefineTau;
+  a.pre_df = pl->d_df;
+  a.w_df = pl->d_df + pl->p.N;
   return a;
 }
 
