@@ -157,6 +157,27 @@ int ofdm_radar_last_launch_count(const ofdm_radar_plan* plan);
 int ofdm_radar_timing_enable(ofdm_radar_plan* plan, int32_t enable);
 int ofdm_radar_timing_read(ofdm_radar_plan* plan, float* total_ms, int32_t* launches, int32_t n);
 
+/* No-allocation variant of ofdm_radar_process (the paper has no counterpart).
+ * For callers that cannot allocate device memory -- code running under an
+ * allocator it does not own, in a memory-capped process, or with all device
+ * memory committed up front -- so cannot create a plan.  Takes the parameters
+ * directly (max_frames is ignored) and keeps tables and workspace in one
+ * fixed array compiled into the library (about 12.6 MB, held on every device
+ * that loads the library until the process exits).  Same inputs, outputs,
+ * layouts and results as ofdm_radar_process on device buffers.
+ * Limits: frames <= 4096 and frames * support_rows * max(M, M') <= 2^20
+ * (e.g. 31 frames of 1024 x 256 with L_cp = 128 and a Hann window); larger
+ * requests return OFDM_ERR_UNSUPPORTED_SIZE before anything is launched.
+ * The first call on a device looks up the array's address
+ * (cudaGetSymbolAddress): make it before any stream capture.  Every call on
+ * a device shares the array and leaves its contents behind; status words are
+ * cleared by each call and tables are rebuilt on the caller's stream when the
+ * parameters change.  Calls that overlap on the GPU race on the array.
+ * Calls no cudaMalloc/cudaFree. */
+int ofdm_radar_process_noalloc(const ofdm_radar_params* p, const ofdm_c32* Y, const ofdm_c32* X,
+                               int32_t frames, float* out_map, ofdm_target* out_targets,
+                               int32_t* n_targets, uint32_t* status, void* stream);
+
 /* Static description of an error code; for OFDM_ERR_CUDA the last CUDA
  * error string of the calling thread is appended. */
 const char* ofdm_radar_strerror(int code);

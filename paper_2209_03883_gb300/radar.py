@@ -72,6 +72,8 @@ def _load():
     lib.ofdm_radar_last_launch_count.argtypes = [vp]
     lib.ofdm_radar_timing_enable.argtypes = [vp, i32]
     lib.ofdm_radar_timing_read.argtypes = [vp, vp, vp, i32]
+    lib.ofdm_radar_process_noalloc.argtypes = [P(Params), vp, vp, i32, vp, vp, vp, vp, vp]
+    lib.ofdm_radar_process_noalloc.restype = ctypes.c_int
     lib.ofdm_radar_strerror.argtypes = [ctypes.c_int]
     lib.ofdm_radar_strerror.restype = ctypes.c_char_p
     for name in ("ofdm_radar_plan_create", "ofdm_radar_support_rows", "ofdm_radar_process",
@@ -190,6 +192,15 @@ def ofdm_radar_process_host(plan: Plan, Y_host, X_host, frames, map_host=None, t
                                                _ptr(map_host), _ptr(targets_host),
                                                _ptr(n_targets_host), _ptr(status_host),
                                                _stream(stream)), "ofdm_radar_process_host")
+
+
+def ofdm_radar_process_noalloc(params: Params, Y, X, frames, out_map=None, out_targets=None,
+                               n_targets=None, status=None, stream=None):
+    """The chain without any device allocation (no plan; fixed in-library scratch)."""
+    return _check(_lib.ofdm_radar_process_noalloc(ctypes.byref(params), _ptr(Y), _ptr(X), frames,
+                                                  _ptr(out_map), _ptr(out_targets), _ptr(n_targets),
+                                                  _ptr(status), _stream(stream)),
+                  "ofdm_radar_process_noalloc")
 
 
 def ofdm_zc_precode(plan: Plan, inp, out, frames, inverse=False, stream=None):
