@@ -29,17 +29,18 @@ struct ColCfg {
 };
 
 // Pipelined configuration for N <= 1024 (one warp per symbol): each warp
-// owns two stages of [A row (+ FFT exchange padding) | Y row] in shared
-// memory; the next symbol's stage streams in with cp.async while the
-// current one is computed.
+// owns a ring of three padded row buffers in shared memory.  At any time one
+// holds the current symbol's A row (then serves as the FFT exchange buffer),
+// one its Y row, and one receives the next symbol's A row by cp.async; the
+// next Y row is issued as soon as the current one has been consumed.
 template <int N>
 struct PipeCfg {
   static constexpr int E = N / 32;
-  static constexpr int STAGE = smem_elems(N) + N;  // float2 per stage
-  static constexpr int FIT = (int)((227u * 1024u) / (2u * STAGE * sizeof(float2)));
-  static constexpr int WARPS = FIT < 8 ? FIT : 8;
+  static constexpr int BUF = smem_elems(N);  // float2 per row buffer
+  static constexpr int FIT = (int)((227u * 1024u) / (3u * BUF * sizeof(float2)));
+  static constexpr int WARPS = FIT < 10 ? FIT : 10;
   static constexpr int THREADS = 32 * WARPS;
-  static constexpr size_t SMEM = (size_t)WARPS * 2 * STAGE * sizeof(float2);
+  static constexpr size_t SMEM = (size_t)WARPS * 3 * BUF * sizeof(float2);
 };
 
 __device__ __forceinline__ uint64_t evict_first_policy() {
@@ -181,65 +182,122 @@ __device__ __forceinline__ uint32_t stencil_write(const float2* v, float2* sm, f
 
 // ---------------------------------------------------------------- N <= 1024: pipelined, one warp per symbol
 template <int N>
-__global__ void __launch_bounds__(PipeCfg<N>::THREADS)
+__global__ void __launch_bounds__(PipeCfg<N>::THREADS, 1)
 column_pipe_kernel(const float2* __restrict__ Y, const float2* __restrict__ X, float2* __restrict__ strip,
                    uint32_t* __restrict__ wstatus, ColumnArgs a) {
   using C = PipeCfg<N>;
   constexpr int E = C::E;
   extern __shared__ float2 smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float2* base = smem + (size_t)warp * 2 * C::STAGE;
+  float2* ring = smem + (size_t)warp * 3 * C::BUF;
   const long total = (long)a.frames * a.M;
-  const long stride = (long)gridDim.x * C::WARPS;
   const uint64_t pol = evict_first_policy();
 
-  auto issue = [&](long sym, float2* st) {
-    const char* ga = reinterpret_cast<const char*>(X + sym * N);
-    const char* gy = reinterpret_cast<const char*>(Y + sym * N);
-    char* sa = reinterpret_cast<char*>(st);
-    char* sy = reinterpret_cast<char*>(st + smem_elems(N));
+  auto issue_row = [&](const float2* g, float2* dst) {
+    const char* gs = reinterpret_cast<const char*>(g);
+    char* ds = reinterpret_cast<char*>(dst);
 #pragma unroll
-    for (int c = lane; c < N / 2; c += 32) {
-      cp_async16(sa + 16 * c, ga + 16 * c, pol);
-      cp_async16(sy + 16 * c, gy + 16 * c, pol);
-    }
+    for (int c = lane; c < N / 2; c += 32) cp_async16(ds + 16 * c, gs + 16 * c, pol);
   };
 
-  long sym = (long)blockIdx.x * C::WARPS + warp;
-  if (sym < total) issue(sym, base);
+  // Dynamic scheduling: each warp draws symbol tickets from a monotonic
+  // counter and stops after its first ticket past the end, so one launch
+  // advances the counter by exactly (symbols + warps).  The next ticket is
+  // drawn one symbol ahead so that its rows can be prefetched.
+  auto ticket = [&]() -> long {
+    unsigned long long v = 0;
+    if (lane == 0) v = atomicAdd(a.work_ctr, 1ull);
+    v = __shfl_sync(0xffffffffu, v, 0);
+    return (long)(v - a.work_base);
+  };
+  int ia = 0, iy = 1, ifree = 2;
+  long sym = ticket();
+  if (sym < total) issue_row(X + sym * N, ring + ia * C::BUF);
   cp_async_commit();
-  for (int it = 0; sym < total; ++it, sym += stride) {
-    float2* cur = base + (it & 1) * C::STAGE;
-    const long nxt = sym + stride;
-    if (nxt < total) issue(nxt, base + ((it + 1) & 1) * C::STAGE);
+  if (sym < total) issue_row(Y + sym * N, ring + iy * C::BUF);
+  cp_async_commit();
+  long nxt = sym < total ? ticket() : total;
+  for (; sym < total; sym = nxt, nxt = (nxt < total ? ticket() : total)) {
+    if (nxt < total) issue_row(X + nxt * N, ring + ifree * C::BUF);
     cp_async_commit();
-    cp_async_wait<1>();
-    __syncwarp();
     const int f = (int)(sym / a.M);
     const int l = (int)(sym % a.M);
-    float2* sa = cur;                    // A row, then the FFT exchange buffer
-    const float2* sy = cur + smem_elems(N);
+    float2* sa = ring + ia * C::BUF;        // A row, then the FFT exchange buffer
+    const float2* sy = ring + iy * C::BUF;  // Y row
     float2 v[E];
     uint32_t flags = 0;
+    int pass0 = 0;
     if (a.zc) {
+      cp_async_wait<2>();                   // A(sym) has landed
+      __syncwarp();
 #pragma unroll
       for (int q = 0; q < E; ++q) {
         const int k = lane + 32 * q;
         const int s = (a.rinv == 1) ? k : (int)(((unsigned)a.rinv * (unsigned)k) & (N - 1));
         v[q] = cmul(sa[s], __ldg(a.pre + s));
       }
-      group_fft<N, 32, +1>(v, sa, a.tw, lane, 0);
-      if (a.refine_tau > 0.f) refine_small_cells<N, 32, E>(v, X + sym * N, a, lane, lane);
-      flags |= divide_precoded<32, E>(v, sy, true, a, lane);
     } else {
+      cp_async_wait<1>();                   // A(sym) and Y(sym)
+      __syncwarp();
       flags |= divide_plain<32, E>(v, sa, sy, true, lane);
       __syncwarp();
+      if (nxt < total) issue_row(Y + nxt * N, ring + iy * C::BUF);
+      cp_async_commit();
+      pass0 = 1;
     }
-    group_fft<N, 32, +1>(v, sa, a.tw, lane, 0);   // N h[n] = sum_i F_i e^{+2 pi i n i / N} (Eq. (20))
+    // Both N-point DFTs run through one copy of the FFT code: pass 0 is the ZC
+    // transform, pass 1 the DFT-CE IDFT, N h[n] = sum_i F_i e^{+2 pi i n i / N} (Eq. (20)).
+    if constexpr (N == 1024) {
+      // Four radix-32 Stockham half-passes through ONE register DFT body
+      // (instruction-cache footprint): even h reads the registers and writes
+      // the transposed exchange, odd h reads it back and applies the
+      // exp(+2 pi i lane r / 1024) twiddles (pass-1 table, u = lane).
+#pragma unroll 1
+      for (int h = 2 * pass0; h < 4; ++h) {
+        if (h & 1) {
+#pragma unroll
+          for (int r = 0; r < 32; ++r) v[r] = sa[pad32(lane + 32 * r)];
+#pragma unroll
+          for (int r = 1; r < 32; ++r) v[r] = cmul(v[r], __ldg(a.tw + r * 32 + lane));
+        }
+        dft_reg<32, +1>(v);
+        if (!(h & 1)) {
+          __syncwarp();
+#pragma unroll
+          for (int r = 0; r < 32; ++r) sa[pad32(32 * lane + r)] = v[r];
+          __syncwarp();
+        } else if (h == 1) {
+          if (a.refine_tau > 0.f) refine_small_cells<N, 32, E>(v, X + sym * N, a, lane, lane);
+          cp_async_wait<1>();               // Y(sym)
+          __syncwarp();
+          flags |= divide_precoded<32, E>(v, sy, true, a, lane);
+          __syncwarp();
+          if (nxt < total) issue_row(Y + nxt * N, ring + iy * C::BUF);
+          cp_async_commit();
+        }
+      }
+    } else {
+#pragma unroll 1
+      for (int pass = pass0; pass < 2; ++pass) {
+        group_fft<N, 32, +1>(v, sa, a.tw, lane, 0);
+        if (pass == 0) {
+          if (a.refine_tau > 0.f) refine_small_cells<N, 32, E>(v, X + sym * N, a, lane, lane);
+          cp_async_wait<1>();               // Y(sym)
+          __syncwarp();
+          flags |= divide_precoded<32, E>(v, sy, true, a, lane);
+          __syncwarp();
+          if (nxt < total) issue_row(Y + nxt * N, ring + iy * C::BUF);
+          cp_async_commit();
+        }
+      }
+    }
     flags |= stencil_write<N, 32, E>(v, sa, strip, a, f, l, lane, 0);
     flags = __reduce_or_sync(0xffffffffu, flags);
     if (lane == 0 && flags) atomicOr(wstatus + f, flags);
-    __syncwarp();  // every lane is done with this stage before it is refilled
+    __syncwarp();  // every lane is done with sa before it is refilled
+    const int t = ia;
+    ia = ifree;
+    ifree = t;
   }
   cp_async_wait<0>();
 }
@@ -321,7 +379,8 @@ zct_kernel(const float2* __restrict__ in, float2* __restrict__ out, ZctArgs a) {
 
 template <int N>
 static cudaError_t launch_column_n(const float2* Y, const float2* X, float2* strip, uint32_t* wstatus,
-                                   const ColumnArgs& a, cudaStream_t s) {
+                                   const ColumnArgs& a, cudaStream_t s, unsigned long long* tickets) {
+  *tickets = 0;
   const long total = (long)a.frames * a.M;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -338,6 +397,7 @@ static cudaError_t launch_column_n(const float2* Y, const float2* X, float2* str
     const long need = (total + C::WARPS - 1) / C::WARPS;
     if (blocks > need) blocks = need;
     column_pipe_kernel<N><<<(unsigned)blocks, C::THREADS, C::SMEM, s>>>(Y, X, strip, wstatus, a);
+    *tickets = (unsigned long long)total + (unsigned long long)blocks * C::WARPS;
   } else {
     using C = ColCfg<N>;
     cudaError_t e = cudaFuncSetAttribute(column_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -362,16 +422,16 @@ static cudaError_t launch_zct_n(const float2* in, float2* out, const ZctArgs& a,
 }
 
 cudaError_t launch_column(int N, const float2* Y, const float2* X, float2* strip, uint32_t* wstatus,
-                          const ColumnArgs& a, cudaStream_t s, int* launches) {
+                          const ColumnArgs& a, cudaStream_t s, int* launches, unsigned long long* tk) {
   ++*launches;
   switch (N) {
-    case 64: return launch_column_n<64>(Y, X, strip, wstatus, a, s);
-    case 128: return launch_column_n<128>(Y, X, strip, wstatus, a, s);
-    case 256: return launch_column_n<256>(Y, X, strip, wstatus, a, s);
-    case 512: return launch_column_n<512>(Y, X, strip, wstatus, a, s);
-    case 1024: return launch_column_n<1024>(Y, X, strip, wstatus, a, s);
-    case 2048: return launch_column_n<2048>(Y, X, strip, wstatus, a, s);
-    case 4096: return launch_column_n<4096>(Y, X, strip, wstatus, a, s);
+    case 64: return launch_column_n<64>(Y, X, strip, wstatus, a, s, tk);
+    case 128: return launch_column_n<128>(Y, X, strip, wstatus, a, s, tk);
+    case 256: return launch_column_n<256>(Y, X, strip, wstatus, a, s, tk);
+    case 512: return launch_column_n<512>(Y, X, strip, wstatus, a, s, tk);
+    case 1024: return launch_column_n<1024>(Y, X, strip, wstatus, a, s, tk);
+    case 2048: return launch_column_n<2048>(Y, X, strip, wstatus, a, s, tk);
+    case 4096: return launch_column_n<4096>(Y, X, strip, wstatus, a, s, tk);
     default: --*launches; return cudaErrorInvalidValue;
   }
 }

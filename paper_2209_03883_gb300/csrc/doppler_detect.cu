@@ -86,19 +86,21 @@ __global__ void zero_rows_kernel(float* __restrict__ map, int frames, long frame
 }
 
 // ---------------------------------------------------------------- detection
-constexpr int kDetThreads = 1024;
-constexpr int kCandCap = 4096;   // shared-memory candidate keys (32 KB)
+constexpr int kDetThreads = 512;
+constexpr int kCandCap = 2048;          // candidate keys kept in shared memory
+constexpr int kBitWords = 16384;        // candidate bit-mask words (64 KB): frames up to 2^19 cells
+constexpr int kTileFloats = 24576;      // row tile incl. halo rows (96 KB)
 
 __device__ __forceinline__ float det_value(const float* base, const DetectArgs& a, int ri, int c) {
-  const int row = a.compact ? ri : (a.row0 + ri) % a.Np;
-  return base[(long)row * a.Mp + c];
+  const int row = a.compact ? ri : ((a.row0 + ri) & (a.Np - 1));
+  return base[((long)row << a.logMp) + c];
 }
 
-// Block-wide bitonic sort of buf[0..kCandCap) in DESCENDING key order.
-__device__ void bitonic_desc(uint64_t* buf) {
-  for (int k = 2; k <= kCandCap; k <<= 1) {
+// Block-wide bitonic sort of buf[0..n) (n a power of two <= kCandCap), keys descending.
+__device__ void bitonic_desc(uint64_t* buf, int n) {
+  for (int k = 2; k <= n; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = threadIdx.x; i < kCandCap; i += kDetThreads) {
+      for (int i = threadIdx.x; i < n; i += kDetThreads) {
         const int p = i ^ j;
         if (p > i) {
           const uint64_t a = buf[i], b = buf[p];
@@ -111,20 +113,69 @@ __device__ void bitonic_desc(uint64_t* buf) {
   }
 }
 
-// Keys: (float bits of P) << 32 | ~(flat map index): descending key order is
-// power descending, then index ascending; 0 marks an empty slot.
+// Key of a detection candidate, else 0.  The cell sits at tile row i
+// (1 <= i <= tile rows; rows 0 and tr + 1 are the halo) and column c of a
+// shared-memory tile whose first interior row is scanned row t0.  A
+// candidate is an 8-neighbour local maximum (circular in r and s) with
+// P > 0 and, in threshold mode, P >= eta.  Key = (float bits of P) << 32 |
+// ~(flat map index): descending key order is power descending, then map
+// index ascending.
+__device__ __forceinline__ uint64_t tile_key(const float* tile, const DetectArgs& a, int t0, int i, int c,
+                                             float eta) {
+  const float p = tile[(i << a.logMp) + c];
+  if (!(p > 0.f) || (a.mode == OFDM_DETECT_THRESHOLD && !(p >= eta))) return 0;
+  const int r = (a.row0 + t0 + i - 1) & (a.Np - 1);
+  const uint32_t idx = ((uint32_t)r << a.logMp) + c;
+  bool ok = true;
+#pragma unroll
+  for (int dr = -1; dr <= 1; ++dr) {
+    const int rn = (r + dr) & (a.Np - 1);
+#pragma unroll
+    for (int dc = -1; dc <= 1; ++dc) {
+      if (dr == 0 && dc == 0) continue;
+      const int cn = (c + dc) & (a.Mp - 1);
+      const uint32_t in_idx = ((uint32_t)rn << a.logMp) + cn;
+      const float pn = tile[((i + dr) << a.logMp) + cn];
+      ok &= (in_idx == idx) | (p > pn) | ((p == pn) & (idx < in_idx));
+    }
+  }
+  return ok ? ((uint64_t)__float_as_uint(p) << 32) | (uint64_t)(~idx) : 0;
+}
+
+// Stage scanned rows t0 - 1 .. t0 + tr (one halo row each side) into the
+// tile.  Rows outside a partial support are zero; a full support wraps.
+__device__ __forceinline__ void load_tile(float* tile, const float* base, const DetectArgs& a, int t0, int tr) {
+  const int n4 = ((tr + 2) << a.logMp) >> 2;
+  for (int v = threadIdx.x; v < n4; v += kDetThreads) {
+    const int idx = v << 2;
+    const int i = idx >> a.logMp, c = idx & (a.Mp - 1);
+    int rj = t0 - 1 + i;
+    float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (a.full) rj &= (a.rows - 1);
+    if (rj >= 0 && rj < a.rows) {
+      const int row = a.compact ? rj : ((a.row0 + rj) & (a.Np - 1));
+      val = *reinterpret_cast<const float4*>(base + ((long)row << a.logMp) + c);
+    }
+    *reinterpret_cast<float4*>(tile + idx) = val;
+  }
+}
+
 __global__ void __launch_bounds__(kDetThreads)
 detect_kernel(const float* __restrict__ src, ofdm_target* __restrict__ out, int32_t* __restrict__ n_out,
               uint32_t* __restrict__ status, uint32_t* __restrict__ wstatus, DetectArgs a) {
   __shared__ uint64_t buf[kCandCap];
+  extern __shared__ __align__(16) float dyn[];   // row tile, then the candidate bit mask
+  float* tile = dyn;
+  uint32_t* bits = reinterpret_cast<uint32_t*>(dyn + ((a.tile_rows + 2) << a.logMp));
   __shared__ uint32_t hist[256];
   __shared__ uint32_t s_prefix, s_rank, s_n, s_total;
   __shared__ uint64_t s_floor;
   const int f = blockIdx.x;
-  const int tid = threadIdx.x, lane = tid & 31;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const float* base = src + (long)f * a.frame_stride;
-  const int n = a.rows * a.Mp;
+  const int n = a.rows << a.logMp;
   const int K = a.K;
+  const bool use_bits = a.bit_words > 0;
 
   float eta = 0.f;
   if (a.mode == OFDM_DETECT_THRESHOLD) {
@@ -140,7 +191,7 @@ detect_kernel(const float* __restrict__ src, ofdm_target* __restrict__ out, int3
         __syncthreads();
         const uint32_t prefix = s_prefix;
         for (int e = tid; e < n; e += kDetThreads) {
-          const uint32_t u = __float_as_uint(det_value(base, a, e / a.Mp, e % a.Mp));
+          const uint32_t u = __float_as_uint(det_value(base, a, e >> a.logMp, e & (a.Mp - 1)));
           if ((u & mask) == prefix) atomicAdd(&hist[(u >> shift) & 255u], 1u);
         }
         __syncthreads();
@@ -160,61 +211,78 @@ detect_kernel(const float* __restrict__ src, ofdm_target* __restrict__ out, int3
     }
   }
 
-  for (int i = tid; i < kCandCap; i += kDetThreads) buf[i] = 0;
-  if (tid == 0) { s_n = 0; s_total = 0; s_floor = 0; }
-  __syncthreads();
-
-  for (int base_e = 0; base_e < n; base_e += kDetThreads) {
-    const int e = base_e + tid;
-    uint64_t key = 0;
-    if (e < n) {
-      const int ri = e / a.Mp, c = e % a.Mp;
-      const float p = det_value(base, a, ri, c);
-      bool ok = p > 0.f && (a.mode != OFDM_DETECT_THRESHOLD || p >= eta);
-      if (ok) {
-        const int r = (a.row0 + ri) % a.Np;
-        const uint32_t idx = (uint32_t)r * a.Mp + c;
-#pragma unroll
-        for (int dr = -1; dr <= 1; ++dr) {
-          int rj = ri + dr;
-          bool inside = true;
-          if (a.full) rj = (rj + a.rows) % a.rows;
-          else inside = rj >= 0 && rj < a.rows;
-          const int rn = (r + dr + a.Np) % a.Np;
-#pragma unroll
-          for (int dc = -1; dc <= 1; ++dc) {
-            if (dr == 0 && dc == 0) continue;
-            const int cn = (c + dc + a.Mp) % a.Mp;
-            const uint32_t in_idx = (uint32_t)rn * a.Mp + cn;
-            if (in_idx == idx) continue;
-            const float pn = inside ? det_value(base, a, rj, cn) : 0.f;
-            ok = ok && (p > pn || (p == pn && idx < in_idx));
-          }
-        }
-        if (ok) key = ((uint64_t)__float_as_uint(p) << 32) | (uint64_t)(~idx);
-      }
-    }
-    // count every candidate, keep only those above the current floor
-    const unsigned cand = __ballot_sync(0xffffffffu, key != 0);
-    if (lane == 0 && cand) atomicAdd(&s_total, (uint32_t)__popc(cand));
-    const bool keep = key != 0 && key > s_floor;
-    const unsigned km = __ballot_sync(0xffffffffu, keep);
-    uint32_t wbase = 0;
-    if (lane == 0 && km) wbase = atomicAdd(&s_n, (uint32_t)__popc(km));
-    wbase = __shfl_sync(0xffffffffu, wbase, 0);
-    if (keep) buf[wbase + __popc(km & ((1u << lane) - 1u))] = key;
+  // Scan 1 over row tiles: candidate bits, candidate count and each
+  // thread's best key.
+  uint64_t best = 0;
+  uint32_t cnt = 0;
+  for (int t0 = 0; t0 < a.rows; t0 += a.tile_rows) {
+    const int tr = min(a.tile_rows, a.rows - t0);
     __syncthreads();
-    const uint32_t nn = s_n;  // every thread takes the same decision below
+    load_tile(tile, base, a, t0, tr);
     __syncthreads();
-    // room for the next chunk of kDetThreads keys: compact to the best K
-    if (nn > (uint32_t)(kCandCap - kDetThreads)) {
-      bitonic_desc(buf);
-      for (int i = K + tid; i < kCandCap; i += kDetThreads) buf[i] = 0;
-      if (tid == 0) { s_n = K; s_floor = buf[K - 1]; }
-      __syncthreads();
+    const int nt = tr << a.logMp;
+    for (int e0 = 0; e0 < nt; e0 += kDetThreads) {
+      const int e = e0 + tid;
+      const uint64_t key = e < nt ? tile_key(tile, a, t0, 1 + (e >> a.logMp), e & (a.Mp - 1), eta) : 0;
+      const unsigned m = __ballot_sync(0xffffffffu, key != 0);
+      const int word = (((t0 << a.logMp) + e0) >> 5) + warp;
+      if (use_bits && lane == 0 && word < a.bit_words) bits[word] = m;
+      cnt += key ? 1u : 0u;
+      best = key > best ? key : best;
     }
   }
-  bitonic_desc(buf);
+  buf[tid] = best;
+  for (int i = kDetThreads + tid; i < kCandCap; i += kDetThreads) buf[i] = 0;
+  cnt = __reduce_add_sync(0xffffffffu, cnt);
+  if (tid == 0) { s_total = 0; s_n = 0; }
+  __syncthreads();
+  if (lane == 0) atomicAdd(&s_total, cnt);
+  // Floor: the K-th best of the per-thread best keys (each a distinct
+  // candidate), so at least K candidates lie at or above it.
+  bitonic_desc(buf, kDetThreads);
+  if (tid == 0) s_floor = buf[K - 1];
+  __syncthreads();
+  const uint64_t floor_key = s_floor;
+  for (int i = tid; i < kCandCap; i += kDetThreads) buf[i] = 0;
+  __syncthreads();
+
+  // Scan 2: keys >= floor into the buffer (compacted to the best K if full).
+  for (int t0 = 0; t0 < a.rows; t0 += a.tile_rows) {
+    const int tr = min(a.tile_rows, a.rows - t0);
+    __syncthreads();
+    load_tile(tile, base, a, t0, tr);
+    __syncthreads();
+    const int nt = tr << a.logMp;
+    for (int e0 = 0; e0 < nt; e0 += kDetThreads) {
+      const int e = e0 + tid;
+      uint64_t key = 0;
+      if (e < nt) {
+        const int ge = (t0 << a.logMp) + e;
+        const bool cand = use_bits ? ((bits[ge >> 5] >> (ge & 31)) & 1u) : true;
+        if (cand) key = tile_key(tile, a, t0, 1 + (e >> a.logMp), e & (a.Mp - 1), eta);
+      }
+      const bool keep = key != 0 && key >= floor_key;
+      const unsigned km = __ballot_sync(0xffffffffu, keep);
+      if (km) {
+        uint32_t wbase = 0;
+        if (lane == 0) wbase = atomicAdd(&s_n, (uint32_t)__popc(km));
+        wbase = __shfl_sync(0xffffffffu, wbase, 0);
+        if (keep) buf[wbase + __popc(km & ((1u << lane) - 1u))] = key;
+      }
+      __syncthreads();
+      const uint32_t nn = s_n;  // every thread takes the same decision below
+      __syncthreads();
+      if (nn > (uint32_t)(kCandCap - kDetThreads)) {
+        bitonic_desc(buf, kCandCap);
+        for (int i = K + tid; i < kCandCap; i += kDetThreads) buf[i] = 0;
+        if (tid == 0) s_n = K;
+        __syncthreads();
+      }
+    }
+  }
+  int sort_n = 32;
+  while (sort_n < (int)s_n) sort_n <<= 1;
+  bitonic_desc(buf, sort_n);
 
   if (tid < 32) {
     const uint64_t key = lane < K ? buf[lane] : 0;
@@ -223,18 +291,18 @@ detect_kernel(const float* __restrict__ src, ofdm_target* __restrict__ out, int3
     if (valid && out) {
       const uint32_t idx = ~(uint32_t)(key & 0xffffffffu);
       ofdm_target tg;
-      tg.r = (int32_t)(idx / (uint32_t)a.Mp);
-      tg.s = (int32_t)(idx % (uint32_t)a.Mp) - a.Mp / 2;
+      tg.r = (int32_t)(idx >> a.logMp);
+      tg.s = (int32_t)(idx & (uint32_t)(a.Mp - 1)) - a.Mp / 2;
       tg.power = __uint_as_float((uint32_t)(key >> 32));
       tg.range_m = (float)tg.r * a.dd;
       tg.vel_mps = (float)tg.s * a.dv;
       out[(long)f * K + lane] = tg;
     }
     if (lane == 0) {
-      const uint32_t cnt = s_total;
+      const uint32_t total = s_total;
       uint32_t st = wstatus ? wstatus[f] : 0u;
-      if (a.mode == OFDM_DETECT_TOPK && cnt < (uint32_t)K) st |= OFDM_STATUS_FEW_PEAKS;
-      if (a.mode == OFDM_DETECT_THRESHOLD && cnt > (uint32_t)K) st |= OFDM_STATUS_OVERFLOW;
+      if (a.mode == OFDM_DETECT_TOPK && total < (uint32_t)K) st |= OFDM_STATUS_FEW_PEAKS;
+      if (a.mode == OFDM_DETECT_THRESHOLD && total > (uint32_t)K) st |= OFDM_STATUS_OVERFLOW;
       if (status) status[f] = st;
       if (n_out) n_out[f] = nv;
       if (wstatus) wstatus[f] = 0u;  // ready for the next call
@@ -286,9 +354,23 @@ cudaError_t launch_zero_rows(float* map, int frames, int Np, int Mp, int z0, int
 }
 
 cudaError_t launch_detect(const float* pow, ofdm_target* out, int32_t* n_out, uint32_t* status,
-                          uint32_t* wstatus, const DetectArgs& a, cudaStream_t s, int* launches) {
+                          uint32_t* wstatus, const DetectArgs& a_in, cudaStream_t s, int* launches) {
   ++*launches;
-  detect_kernel<<<a.frames, kDetThreads, 0, s>>>(pow, out, n_out, status, wstatus, a);
+  DetectArgs a = a_in;
+  const long n = (long)a.rows * a.Mp;
+  const long words = (n + 31) / 32;
+  a.bit_words = words <= kBitWords ? (int)words : 0;  // too large: scan 2 re-tests every cell
+  // Row tiles of at most kTileFloats floats including the two halo rows; the
+  // tile rows times M' stay a multiple of 32 so that ballot words align.
+  int tr = kTileFloats / a.Mp - 2;
+  if (a.Mp < 32) tr &= ~1;
+  if (tr > a.rows) tr = a.rows;
+  a.tile_rows = tr;
+  const size_t smem = (size_t)(tr + 2) * a.Mp * sizeof(float) + (size_t)a.bit_words * sizeof(uint32_t);
+  cudaError_t e = cudaFuncSetAttribute(detect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(kTileFloats * sizeof(float) + kBitWords * sizeof(uint32_t)));
+  if (e != cudaSuccess) return e;
+  detect_kernel<<<a.frames, kDetThreads, smem, s>>>(pow, out, n_out, status, wstatus, a);
   return cudaGetLastError();
 }
 

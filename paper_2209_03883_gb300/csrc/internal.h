@@ -24,6 +24,8 @@ struct ColumnArgs {
   float refine_tau;        // recompute precoded cells with |X_p|^2 < tau * mean in double-float; 0 = off
   const float4* pre_df;    // [N] pre-chirp as double-float (re.hi, re.lo, im.hi, im.lo)
   const float4* w_df;      // [N] exp(+2 pi i m / N) as double-float
+  unsigned long long* work_ctr;  // monotonic symbol ticket counter (pipelined kernel)
+  unsigned long long work_base;  // counter value at the start of this launch
 };
 
 struct ZctArgs {
@@ -43,6 +45,9 @@ struct DopplerArgs {
 
 struct DetectArgs {
   int Np, Mp, rows, row0, full;   // rows scanned, starting at range bin row0 (circular)
+  int logMp;                      // log2(M'); N' and M' are powers of two
+  int bit_words;                  // set by the launcher: candidate bit-mask words in shared memory
+  int tile_rows;                  // set by the launcher: scanned rows per shared-memory tile
   long frame_stride;              // floats between frames of the input
   int compact;                    // 1: input rows are the support strip; 0: full map rows
   int frames;
@@ -52,8 +57,11 @@ struct DetectArgs {
   float dd, dv;                   // metres / (m/s) per bin, Eq. (19)
 };
 
+// *tickets receives how far the launch advances a.work_ctr (symbols + warps
+// for the pipelined kernel, 0 otherwise); the caller adds it to work_base.
 cudaError_t launch_column(int N, const float2* Y, const float2* X, float2* strip, uint32_t* wstatus,
-                          const ColumnArgs& a, cudaStream_t s, int* launches);
+                          const ColumnArgs& a, cudaStream_t s, int* launches,
+                          unsigned long long* tickets);
 cudaError_t launch_zct(int N, const float2* in, float2* out, const ZctArgs& a, cudaStream_t s,
                        int* launches);
 cudaError_t launch_doppler(int Mp, const float2* strip, float* map, float* pow, const DopplerArgs& a,

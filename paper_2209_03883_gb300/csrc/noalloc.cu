@@ -40,7 +40,8 @@ constexpr size_t kOffWl = align256(kOffTwM + 2 * kMaxM * sizeof(float2));   // f
 constexpr size_t kOffStatus = align256(kOffWl + kMaxM * sizeof(float));     // uint32[frames]
 constexpr size_t kOffStrip = align256(kOffStatus + kNoallocMaxFrames * sizeof(uint32_t));
 constexpr size_t kOffPow = align256(kOffStrip + (size_t)kNoallocMaxCells * sizeof(float2));
-constexpr size_t kScratchBytes = align256(kOffPow + (size_t)kNoallocMaxCells * sizeof(float));
+constexpr size_t kOffCtr = align256(kOffPow + (size_t)kNoallocMaxCells * sizeof(float));  // ticket counter
+constexpr size_t kScratchBytes = align256(kOffCtr + sizeof(unsigned long long));
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -149,6 +150,7 @@ struct DeviceState {
   bool ready = false;
   unsigned char* base = nullptr;  // device address of g_noalloc_scratch
   bool have_tables = false;
+  unsigned long long ctr_base = 0;  // the counter starts at zero: the array is zero-initialised
   ofdm_radar_params tables_for;   // parameters the tables in the array were built for
 };
 constexpr int kMaxDevices = 64;
@@ -236,6 +238,8 @@ extern "C" int ofdm_radar_process_noalloc(const ofdm_radar_params* pin, const of
   ca.refine_tau = kNoallocRefineTau;
   ca.pre_df = reinterpret_cast<float4*>(b + kOffDf);
   ca.w_df = ca.pre_df + N;
+  ca.work_ctr = reinterpret_cast<unsigned long long*>(b + kOffCtr);
+  ca.work_base = st.ctr_base;
 
   DopplerArgs da;
   da.N = N; da.Np = N; da.M = M; da.Mp = Mp; da.rows = rows; da.row0 = row0; da.frames = frames;
@@ -244,7 +248,9 @@ extern "C" int ofdm_radar_process_noalloc(const ofdm_radar_params* pin, const of
   da.tw = reinterpret_cast<float2*>(b + kOffTwM);
 
   DetectArgs ta;
-  ta.Np = N; ta.Mp = Mp; ta.rows = rows; ta.row0 = row0; ta.full = full; ta.compact = 1;
+  ta.Np = N; ta.Mp = Mp; ta.logMp = 0;
+  while ((1 << ta.logMp) < Mp) ++ta.logMp;
+  ta.rows = rows; ta.row0 = row0; ta.full = full; ta.compact = 1;
   ta.frame_stride = (long)rows * Mp; ta.frames = frames; ta.mode = p.detect_mode; ta.K = p.max_targets;
   ta.use_fixed_eta = p.noise_var > 0.f ? 1 : 0;
   ta.eta_fixed = p.noise_var * (float)(-log((double)p.pfa));
@@ -254,8 +260,10 @@ extern "C" int ofdm_radar_process_noalloc(const ofdm_radar_params* pin, const of
   ta.dd = (float)(3.0e8 / (2.0 * N * p.df_hz));
   ta.dv = (float)(3.0e8 / (2.0 * p.fc_hz * Mp * Ts));
 
+  unsigned long long tk = 0;
   e = launch_column(N, reinterpret_cast<const float2*>(Y), reinterpret_cast<const float2*>(X), strip, wstatus, ca,
-                    s, &launches);
+                    s, &launches, &tk);
+  st.ctr_base += tk;
   if (e == cudaSuccess && out_map)
     e = launch_zero_rows(out_map, frames, N, Mp, (row0 + rows) % N, N - rows, s, &launches);
   if (e == cudaSuccess) e = launch_doppler(Mp, strip, out_map, pow, da, s, &launches);

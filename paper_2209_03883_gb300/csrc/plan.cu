@@ -29,6 +29,12 @@ struct ofdm_radar_plan {
   float2* d_strip = nullptr;   // [max_frames][rows][M]
   float* d_pow = nullptr;      // [max_frames][rows][M']
   uint32_t* d_wstatus = nullptr;
+  // Ticket counters of the dynamically scheduled column kernel: slot 0 for
+  // calls on the caller's stream, slots 1-2 for the two streams of the host
+  // pipeline (launches that may run concurrently need separate counters).
+  unsigned long long* d_ctr = nullptr;
+  unsigned long long ctr_base[3] = {0, 0, 0};
+  int ctr_slot = 0;
   // host-buffer path (allocated on first use)
   float2* d_Y = nullptr;
   float2* d_X = nullptr;
@@ -158,6 +164,7 @@ void ofdm_radar_plan_destroy(ofdm_radar_plan* plan) {
   cudaFree(plan->d_strip);
   cudaFree(plan->d_pow);
   cudaFree(plan->d_wstatus);
+  cudaFree(plan->d_ctr);
   cudaFree(plan->d_Y);
   cudaFree(plan->d_X);
   cudaFree(plan->d_map);
@@ -278,6 +285,7 @@ int ofdm_radar_plan_create(const ofdm_radar_params* pin, ofdm_radar_plan** out) 
   if (e == cudaSuccess) e = dalloc(&pl->d_strip, (size_t)p.max_frames * pl->rows * M);
   if (e == cudaSuccess) e = dalloc(&pl->d_pow, (size_t)p.max_frames * pl->rows * Mp);
   if (e == cudaSuccess) e = dalloc(&pl->d_wstatus, (size_t)p.max_frames);
+  if (e == cudaSuccess) e = dalloc(&pl->d_ctr, 3);
   if (e != cudaSuccess) {
     ofdm_radar_plan_destroy(pl);
     cudaGetLastError();
@@ -300,6 +308,7 @@ int ofdm_radar_plan_create(const ofdm_radar_params* pin, ofdm_radar_plan** out) 
   if (e == cudaSuccess) e = cudaMemcpy(pl->d_wl, wl.data(), M * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(pl->d_df, df.data(), df.size() * sizeof(float4), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(pl->d_wstatus, 0, (size_t)p.max_frames * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemset(pl->d_ctr, 0, 3 * sizeof(unsigned long long));
   if (e != cudaSuccess) {
     ofdm_radar_plan_destroy(pl);
     return cuda_fail(e);
@@ -379,6 +388,8 @@ ColumnArgs column_args(const ofdm_radar_plan* pl, int frames) {
   a.refine_tau = kRefineTau;
   a.pre_df = pl->d_df;
   a.w_df = pl->d_df + pl->p.N;
+  a.work_ctr = pl->d_ctr + pl->ctr_slot;
+  a.work_base = pl->ctr_base[pl->ctr_slot];
   return a;
 }
 
@@ -402,6 +413,8 @@ DetectArgs detect_args(const ofdm_radar_plan* pl, int frames, int compact) {
   DetectArgs a;
   a.Np = pl->Np;
   a.Mp = pl->Mp;
+  a.logMp = 0;
+  while ((1 << a.logMp) < pl->Mp) ++a.logMp;
   a.rows = pl->rows;
   a.row0 = pl->row0;
   a.full = pl->full;
@@ -437,7 +450,9 @@ cudaError_t run_chain(ofdm_radar_plan* pl, const float2* Y, const float2* X, int
   cudaError_t e;
   {
     ScopedTimer tm(pl, s, K_COLUMN);
-    e = ofdm::launch_column(pl->p.N, Y, X, pl->d_strip, pl->d_wstatus, column_args(pl, frames), s, launches);
+    unsigned long long tk = 0;
+    e = ofdm::launch_column(pl->p.N, Y, X, pl->d_strip, pl->d_wstatus, column_args(pl, frames), s, launches, &tk);
+    pl->ctr_base[pl->ctr_slot] += tk;
   }
   if (e != cudaSuccess) return e;
   if (map && pl->nz > 0) {
@@ -494,8 +509,10 @@ int ofdm_radar_range_profile(ofdm_radar_plan* pl, const ofdm_c32* Y, const ofdm_
                              ofdm_c32* strip, void* stream) {
   if (!pl || !Y || !X || !strip || bad_frames(pl, frames)) return OFDM_ERR_INVALID_ARG;
   int launches = 0;
+  unsigned long long tk = 0;
   cudaError_t e = ofdm::launch_column(pl->p.N, (const float2*)Y, (const float2*)X, (float2*)strip,
-                                      pl->d_wstatus, column_args(pl, frames), (cudaStream_t)stream, &launches);
+                                      pl->d_wstatus, column_args(pl, frames), (cudaStream_t)stream, &launches, &tk);
+  pl->ctr_base[pl->ctr_slot] += tk;
   // the status words of this call are not reported; clear them
   if (e == cudaSuccess)
     e = cudaMemsetAsync(pl->d_wstatus, 0, (size_t)frames * sizeof(uint32_t), (cudaStream_t)stream);
@@ -560,11 +577,13 @@ int ofdm_radar_process_host(ofdm_radar_plan* pl, const ofdm_c32* Yh, const ofdm_
     if (e != cudaSuccess) break;
     // The chunk uses its own slice of the workspace (frame offset f0).
     ofdm_radar_plan view = *pl;
+    view.ctr_slot = 1 + (k & 1);
     view.d_strip = pl->d_strip + (size_t)f0 * pl->rows * p.M;
     view.d_pow = pl->d_pow + (size_t)f0 * pl->rows * pl->Mp;
     view.d_wstatus = pl->d_wstatus + f0;
     e = run_chain(&view, pl->d_Y + g0, pl->d_X + g0, nf, map_h ? pl->d_map + mapn * f0 : nullptr,
                   pl->d_tg + (size_t)p.max_targets * f0, pl->d_nt + f0, pl->d_st + f0, s, &launches);
+    pl->ctr_base[view.ctr_slot] = view.ctr_base[view.ctr_slot];
     if (e != cudaSuccess) break;
     if (map_h)
       e = cudaMemcpyAsync(map_h + mapn * f0, pl->d_map + mapn * f0, mapn * nf * sizeof(float),

@@ -310,3 +310,18 @@ def test_frames_out_of_range_rejected(env):
     Y = torch.zeros((3, 16, 64), dtype=torch.complex64, device=dev)
     with pytest.raises(radar.OfdmError):
         radar.process(plan, Y, Y, frames=3)
+
+
+def test_repeated_calls_on_one_plan(env):
+    """Calls of different sizes on one plan (dynamically scheduled column
+    kernel, ticket counter carried across calls) match a fresh plan each."""
+    radar, torch, dev = env
+    cfg, fr = make_frames(2, 8)
+    p = oracle_params(cfg)
+    plan = radar.Plan(**plan_kwargs(p, 8))
+    for n in (8, 3, 5, 8):
+        Ys, As = [f[2] for f in fr[:n]], [f[0].A for f in fr[:n]]
+        a = run_chain(env, p, Ys, As, plan=plan)
+        b = run_chain(env, p, Ys, As)
+        assert np.array_equal(a["map"][:n], b["map"][:n])
+        assert np.array_equal(a["n"][:n], b["n"][:n])
