@@ -367,3 +367,110 @@ def process(Y: np.ndarray, A: np.ndarray, p: Params) -> dict:
     d, v = estimates(det.r, det.s, p.Np, p.Mp, p.df_hz, p.fc_hz, Ts)
     return dict(Xp=Xp, F=F, h=h, Hd=Hd, P=P, det=det, eta=eta, d=d, v=v,
                 g=range_profile(Hd, w_k), rows=rows)
+
+
+# --------------------------------------------------------------------------
+# FPS-SFT (Sec. III-C) -- the sparse alternative to the 2D transform
+# --------------------------------------------------------------------------
+# The paper gives only the outline (I iterations, three or more Q-length
+# slices per iteration, Q = lcm(N, M), a Q-point DFT per slice, frequencies
+# recovered in one iteration removed from the next) and defers the details
+# to its FPS-SFT reference.  This is our restatement from the
+# projection-slice theorem, with the tolerances stated as parameters:
+#   slice  s_j[n] = x[(a0 n + t0_j) mod N, (a1 n + t1_j) mod M], n < Q;
+#   its Q-point DFT S_j[m] = (Q / (N M)) sum_f X[f] e^{+2pi i (f0 t0_j / N + f1 t1_j / M)}
+#   over the frequencies f on the line a0 f0 Q/N + a1 f1 Q/M = m (mod Q),
+#   X[f] = sum_{k,l} x[k,l] e^{-2pi i (f0 k / N + f1 l / M)} the 2D DFT.
+# A bin holding one frequency is decoded by the maximum-likelihood search
+# along its line (coherent sum over the T offsets), accepted when the
+# coherence |sum_j S_j e^{-i theta_j}| / sum_j |S_j| passes `coherence_min`.
+
+@dataclass
+class FpsParams:
+    iterations: int = 4
+    offsets: int = 8
+    max_recover: int = 32
+    bin_pfa: float = 1e-6
+    coherence_min: float = 0.95
+    dynamic_range: float = 1e-10   # bins below this fraction of the strongest are not tested
+
+
+def fps_line(m: int, a0: int, a1: int, N: int, M: int, Q: int):
+    """Frequencies (f0, f1) whose slice bin is m: a0 f0 Q/N + a1 f1 Q/M = m (mod Q)."""
+    out = []
+    qn, qm = Q // N, Q // M
+    for f0 in range(N):
+        rest = (m - a0 * f0 * qn) % Q
+        if rest % qm:
+            continue
+        # a1 f1 = rest / qm (mod M); a1 is odd, hence invertible mod M
+        f1 = (pow(a1, -1, M) * (rest // qm)) % M
+        out.append((f0, f1))
+    return out
+
+
+def fps_sft(x: np.ndarray, slice_params, fp: FpsParams):
+    """FPS-SFT on an N x M signal x (here the DFT-CE estimate H').
+
+    slice_params[i] = (a0, a1, [(t0_j, t1_j) for j < T]) for iteration i: the
+    directions (odd) and offsets drawn by the caller.  Returns a list of
+    (f0, f1, amplitude X[f]) in recovery order.
+    """
+    N, M = x.shape
+    Q = math.lcm(N, M)
+    rec = {}                      # (f0, f1) -> complex amplitude
+    e_peak = 0.0
+    for a0, a1, offs in slice_params:
+        T = len(offs)
+        n = np.arange(Q)
+        S = []
+        for t0, t1 in offs:
+            s = x[(a0 * n + t0) % N, (a1 * n + t1) % M]
+            S.append(dft_matrix(Q) @ s)                      # Q-point DFT of the slice
+        S = np.array(S)
+        # remove the frequencies already recovered (their bin in every slice)
+        for (f0, f1), amp in rec.items():
+            m = (a0 * f0 * (Q // N) + a1 * f1 * (Q // M)) % Q
+            for j, (t0, t1) in enumerate(offs):
+                ph = ((f0 * t0 * (Q // N) + f1 * t1 * (Q // M)) % Q) / Q
+                S[j, m] -= (Q / (N * M)) * amp * np.exp(2j * np.pi * ph)
+        E = np.mean(np.abs(S) ** 2, axis=0)                  # bin energy over the offsets
+        thr = np.sort(E)[(Q - 1) // 2] / math.log(2.0) * (-math.log(fp.bin_pfa))
+        e_peak = max(e_peak, float(E.max()))           # strongest bin of any iteration so far
+        thr = max(thr, fp.dynamic_range * e_peak)
+        found = []
+        live = np.flatnonzero(E > thr)
+        if live.size == 0:                 # nothing left above the noise: done
+            break
+        for m in live:
+            best, bf = -1.0, None
+            for f0, f1 in fps_line(int(m), a0, a1, N, M, Q):
+                acc = 0j
+                for j, (t0, t1) in enumerate(offs):
+                    ph = ((f0 * t0 * (Q // N) + f1 * t1 * (Q // M)) % Q) / Q
+                    acc += S[j, m] * np.exp(-2j * np.pi * ph)
+                if abs(acc) > best:
+                    best, bf = abs(acc), (f0, f1, acc)
+            if bf is None or best < fp.coherence_min * np.sum(np.abs(S[:, m])):
+                continue
+            f0, f1, acc = bf
+            found.append(((f0, f1), (N * M / Q) * acc / T))
+        for key, amp in found:
+            if key in rec:
+                rec[key] += amp
+            elif len(rec) < fp.max_recover:
+                rec[key] = amp
+    return [(f0, f1, a) for (f0, f1), a in rec.items()]
+
+
+def fps_targets(rec, N: int, M: int, K: int):
+    """Recovered frequencies as periodogram bins (Eq. (17) with a rect window):
+    r = -f0 mod N (the range sum is an IDFT), s = f1 centred, P = |X|^2/(N M);
+    ordered like detect(): power descending, then map index ascending."""
+    rows = []
+    for f0, f1, a in rec:
+        r = (-f0) % N
+        s = f1 - M if f1 >= M // 2 else f1
+        rows.append((abs(a) ** 2 / (N * M), r * M + (s + M // 2), r, s))
+    rows.sort(key=lambda t: (-t[0], t[1]))
+    return rows[:K]

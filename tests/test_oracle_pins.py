@@ -341,3 +341,80 @@ def test_support_rows_cover_nonzero_rows_once(N, L, w):
     assert len(set(rows.tolist())) == len(rows)
     nz = np.flatnonzero(np.abs(g).max(axis=1) > 1e-9 * np.abs(g).max())
     assert set(nz.tolist()) <= set(rows.tolist())
+
+
+# ---------------------------------------------------------------- FPS-SFT (Sec. III-C)
+def _sparse_case(seed, N, M, K, iters=6, T=8):
+    rng = np.random.default_rng(seed)
+    F = set()
+    while len(F) < K:
+        F.add((int(rng.integers(N)), int(rng.integers(M))))
+    X = np.zeros((N, M), complex)
+    for f in F:
+        X[f] = (rng.standard_normal() + 1j * rng.standard_normal()) * N * M
+    # time-domain signal by brute-force inverse 2D DFT (pure sums, no FFT)
+    k = np.arange(N)[:, None]
+    l = np.arange(M)[None, :]
+    x = np.zeros((N, M), complex)
+    for (f0, f1) in F:
+        x += X[f0, f1] * np.exp(2j * np.pi * (f0 * k / N + f1 * l / M)) / (N * M)
+    sp = []
+    for _ in range(iters):
+        a0 = int(rng.integers(0, N // 2)) * 2 + 1
+        a1 = int(rng.integers(0, M // 2)) * 2 + 1
+        sp.append((a0, a1, [(int(rng.integers(N)), int(rng.integers(M))) for _ in range(T)]))
+    return F, X, x, sp
+
+
+def check_fps_exact(seed=3, N=64, M=16, K=5):
+    F, X, x, sp = _sparse_case(seed, N, M, K)
+    rec = o.fps_sft(x, sp, o.FpsParams())
+    got = {(f0, f1): a for f0, f1, a in rec}
+    assert sorted(got) == sorted(F)
+    for f in F:
+        assert abs(got[f] - X[f]) < 1e-8 * abs(X[f])
+
+
+@pytest.mark.parametrize("seed,N,M,K", [(0, 64, 64, 1), (1, 64, 64, 8), (2, 64, 16, 7), (3, 64, 16, 5),
+                                        (4, 32, 32, 4), (5, 128, 32, 6)])
+def test_fps_sft_exact_recovery(seed, N, M, K):
+    check_fps_exact(seed, N, M, K)
+
+
+def test_fps_line_membership():
+    # every frequency on a bin's line maps back to that bin, and the lines of
+    # all bins partition the N x M grid
+    N, M, Q, a0, a1 = 16, 8, 16, 3, 5
+    seen = set()
+    for m in range(Q):
+        for f0, f1 in o.fps_line(m, a0, a1, N, M, Q):
+            assert (a0 * f0 * (Q // N) + a1 * f1 * (Q // M)) % Q == m
+            seen.add((f0, f1))
+    assert len(seen) == N * M
+
+
+def test_fps_sft_agrees_with_periodogram():
+    # small noisy frame with strong on-grid targets, rect window (K-sparse map)
+    cfg = syn.FrameConfig(N=64, M=16, L_cp=16, qam=16, zc_root=1, n_targets=3, on_grid=True,
+                          amp_db=(0.0, 0.0), snr_db=(10.0, 10.0), window=0)
+    fr = syn.draw_frame(cfg, 4242)
+    Xp = o.zc_precode(fr.A, 1)
+    p = o.Params(N=64, M=16, L_cp=16, zc_root=1, window=0, max_targets=3)
+    ref = o.process(syn.received(fr, Xp), fr.A, p)
+    rng = np.random.default_rng(9)
+    sp = [(int(rng.integers(0, 32)) * 2 + 1, int(rng.integers(0, 8)) * 2 + 1,
+           [(int(rng.integers(64)), int(rng.integers(16))) for _ in range(8)]) for _ in range(4)]
+    tg = o.fps_targets(o.fps_sft(ref["Hd"], sp, o.FpsParams()), 64, 16, 3)
+    assert sorted((r, s) for _, _, r, s in tg) == sorted(zip(ref["det"].r.tolist(), ref["det"].s.tolist()))
+
+
+def test_fps_pin_catches_wrong_peeling_sign(monkeypatch):
+    real = o.np.exp
+    calls = {"n": 0}
+
+    def bad_exp(z):
+        # conjugate the phase of the peeling step (first use inside each removal)
+        return real(np.conj(z)) if np.iscomplexobj(z) and np.ndim(z) == 0 else real(z)
+    monkeypatch.setattr(o.np, "exp", bad_exp)
+    with pytest.raises(AssertionError):
+        check_fps_exact(1, 64, 64, 8)
