@@ -144,6 +144,44 @@ int ofdm_radar_detect(ofdm_radar_plan* plan, const float* map, int32_t frames,
                       ofdm_target* out_targets, int32_t* n_targets, uint32_t* status,
                       void* stream);
 
+/* FPS-SFT (Sec. III-C): the sparse alternative to the periodogram.  The
+ * paper outlines it (iterations of three or more Q-length slices, Q =
+ * lcm(N, M), a Q-point DFT per slice, frequencies recovered in one iteration
+ * removed from the next) and defers its details to its FPS-SFT reference;
+ * this is a restatement from the projection-slice theorem:
+ *   - slice j of an iteration samples the DFT-CE estimate H' along
+ *     (a0 n + t0_j mod N, a1 n + t1_j mod M), n < Q, and is transformed;
+ *   - recovered frequencies are removed from every slice;
+ *   - bins whose energy (mean over the slices) exceeds the median bin energy
+ *     times -ln(bin_pfa)/ln 2, and dynamic_range times the strongest bin seen
+ *     so far, are decoded by a maximum-likelihood search along their
+ *     projection line, kept when the coherence |sum_j S_j e^{-i theta_j}| /
+ *     sum_j |S_j| reaches coherence_min (a 1-sparse bin);
+ *   - iterations stop early once no bin passes the energy test. */
+typedef struct {
+  int32_t iterations;     /* I, 1..16 (default 4) */
+  int32_t offsets;        /* T slices per iteration, 3..8 (default 8) */
+  int32_t max_recover;    /* recovered frequencies kept per frame, 1..64 (default 32) */
+  float bin_pfa;          /* default 1e-6 */
+  float coherence_min;    /* default 0.95 */
+  float dynamic_range;    /* default 1e-10 */
+} ofdm_fps_params;
+
+void ofdm_fps_default_params(ofdm_fps_params* fp);
+
+/* FPS-SFT on `frames` frames.  The random slice geometry is an input:
+ * slices is a DEVICE int32 array [frames][iterations][2 + 2 * offsets] holding
+ * a0, a1 (odd) and then (t0_j, t1_j) for every slice.  Uses the plan's
+ * ZC precoding, division and DFT-CE (any window setting: slices read the
+ * un-windowed H'); requires Q = max(N, M) <= 1024 and M' = M.  Writes the
+ * strongest min(recovered, max_targets) as targets with the periodogram's
+ * conventions: r = -f0 mod N, s centred, power |X[f]|^2 / (N M) (the rect-
+ * window periodogram value of that bin, Eq. (17)), ordered by power then
+ * map index. */
+int ofdm_fps_sft(ofdm_radar_plan* plan, const ofdm_c32* Y, const ofdm_c32* X, int32_t frames,
+                 const ofdm_fps_params* fp, const int32_t* slices, ofdm_target* out_targets,
+                 int32_t* n_targets, void* stream);
+
 /* Kernel launches made by the last successful call on this plan. */
 int ofdm_radar_last_launch_count(const ofdm_radar_plan* plan);
 

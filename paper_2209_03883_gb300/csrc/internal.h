@@ -59,6 +59,19 @@ struct DetectArgs {
 
 // *tickets receives how far the launch advances a.work_ctr (symbols + warps
 // for the pipelined kernel, 0 otherwise); the caller adds it to work_base.
+struct FpsArgs {
+  int N, M, T, rows, CB, iterations, frames, K, max_recover;
+  float invN, invNM, NMoverQ;       // 1/N, 1/(N M), N M / Q
+  float median_factor;             // bin threshold = median energy * (-ln pfa) / ln 2
+  float dynamic_range, coherence_min;
+  float dd, dv;                    // Eq. (19) bin widths
+  const float4* w_df;              // exp(+2 pi i m / N), double-float (hi parts used)
+  const float2* twQ;               // Q-point pass twiddles
+};
+
+cudaError_t launch_fps(int Q, const float2* strip, const int32_t* slices, ofdm_target* out, int32_t* n_out,
+                       uint32_t* wstatus, const FpsArgs& a, cudaStream_t s, int* launches);
+
 cudaError_t launch_column(int N, const float2* Y, const float2* X, float2* strip, uint32_t* wstatus,
                           const ColumnArgs& a, cudaStream_t s, int* launches,
                           unsigned long long* tickets);

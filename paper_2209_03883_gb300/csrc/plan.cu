@@ -605,3 +605,63 @@ int ofdm_radar_process_host(ofdm_radar_plan* pl, const ofdm_c32* Yh, const ofdm_
 }
 
 }  // extern "C"
+
+extern "C" {
+
+void ofdm_fps_default_params(ofdm_fps_params* fp) {
+  if (!fp) return;
+  fp->iterations = 4;
+  fp->offsets = 8;
+  fp->max_recover = 32;
+  fp->bin_pfa = 1e-6f;
+  fp->coherence_min = 0.95f;
+  fp->dynamic_range = 1e-10f;
+}
+
+int ofdm_fps_sft(ofdm_radar_plan* pl, const ofdm_c32* Y, const ofdm_c32* X, int32_t frames,
+                 const ofdm_fps_params* fp, const int32_t* slices, ofdm_target* out_targets,
+                 int32_t* n_targets, void* stream) {
+  if (!pl || !Y || !X || !fp || !slices || bad_frames(pl, frames)) return OFDM_ERR_INVALID_ARG;
+  const ofdm_radar_params& p = pl->p;
+  const int N = p.N, M = p.M, Q = N > M ? N : M;
+  if (Q > 1024 || pl->Mp != M) return OFDM_ERR_UNSUPPORTED_SIZE;
+  if (fp->iterations < 1 || fp->iterations > 16 || fp->offsets < 3 || fp->offsets > 8 ||
+      fp->max_recover < 1 || fp->max_recover > 64 || !(fp->bin_pfa > 0.f && fp->bin_pfa < 1.f) ||
+      !(fp->coherence_min >= 0.f && fp->coherence_min <= 1.f) || !(fp->dynamic_range >= 0.f))
+    return OFDM_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  // Column pass with a rect stencil: the strip then holds the kept taps N h[n].
+  ColumnArgs ca = column_args(pl, frames);
+  ca.rows = p.L_cp;
+  ca.row0 = 0;
+  ca.full = p.L_cp >= N ? 1 : 0;
+  ca.c0 = 1.f;
+  ca.c1 = 0.f;
+  int launches = 0;
+  unsigned long long tk = 0;
+  cudaError_t e = ofdm::launch_column(N, (const float2*)Y, (const float2*)X, pl->d_strip, pl->d_wstatus, ca, s,
+                                      &launches, &tk);
+  pl->ctr_base[pl->ctr_slot] += tk;
+  if (e != cudaSuccess) return finish(pl, launches, e);
+  ofdm::FpsArgs a;
+  a.N = N; a.M = M; a.T = fp->offsets; a.rows = p.L_cp; a.iterations = fp->iterations; a.frames = frames;
+  a.K = p.max_targets; a.max_recover = fp->max_recover;
+  a.CB = 4096 / p.L_cp;
+  if (a.CB < 1) a.CB = 1;
+  if (a.CB > 32) a.CB = 32;
+  a.invN = (float)(1.0 / N);
+  a.invNM = (float)(1.0 / ((double)N * M));
+  a.NMoverQ = (float)((double)N * M / Q);
+  a.median_factor = (float)(-log((double)fp->bin_pfa) / log(2.0));
+  a.dynamic_range = fp->dynamic_range;
+  a.coherence_min = fp->coherence_min;
+  const DetectArgs d = detect_args(pl, frames, 1);
+  a.dd = d.dd;
+  a.dv = d.dv;
+  a.w_df = pl->d_df + N;
+  a.twQ = (Q == N) ? pl->twN : pl->twM;
+  e = ofdm::launch_fps(Q, pl->d_strip, slices, out_targets, n_targets, pl->d_wstatus, a, s, &launches);
+  return finish(pl, launches, e);
+}
+
+}  // extern "C"

@@ -44,6 +44,12 @@ class Target(ctypes.Structure):
 TARGET_BYTES = ctypes.sizeof(Target)   # 20
 
 
+class FpsParams(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("offsets", ctypes.c_int32),
+                ("max_recover", ctypes.c_int32), ("bin_pfa", ctypes.c_float),
+                ("coherence_min", ctypes.c_float), ("dynamic_range", ctypes.c_float)]
+
+
 class OfdmError(RuntimeError):
     def __init__(self, code, where):
         self.code = code
@@ -74,6 +80,10 @@ def _load():
     lib.ofdm_radar_timing_read.argtypes = [vp, vp, vp, i32]
     lib.ofdm_radar_process_noalloc.argtypes = [P(Params), vp, vp, i32, vp, vp, vp, vp, vp]
     lib.ofdm_radar_process_noalloc.restype = ctypes.c_int
+    lib.ofdm_fps_default_params.argtypes = [P(FpsParams)]
+    lib.ofdm_fps_default_params.restype = None
+    lib.ofdm_fps_sft.argtypes = [vp, vp, vp, i32, P(FpsParams), vp, vp, vp, vp]
+    lib.ofdm_fps_sft.restype = ctypes.c_int
     lib.ofdm_radar_strerror.argtypes = [ctypes.c_int]
     lib.ofdm_radar_strerror.restype = ctypes.c_char_p
     for name in ("ofdm_radar_plan_create", "ofdm_radar_support_rows", "ofdm_radar_process",
@@ -256,3 +266,19 @@ def process(plan: Plan, Y, X, frames=None, with_map=True, stream=None):
     ofdm_radar_process(plan, Y, X, frames, out["map"], out["targets"], out["n_targets"],
                        out["status"], stream)
     return out
+
+
+def fps_default_params(**kw) -> FpsParams:
+    fp = FpsParams()
+    _lib.ofdm_fps_default_params(ctypes.byref(fp))
+    for k, v in kw.items():
+        setattr(fp, k, v)
+    return fp
+
+
+def ofdm_fps_sft(plan: Plan, Y, X, frames, fp: FpsParams, slices, out_targets=None, n_targets=None,
+                 stream=None):
+    """FPS-SFT; `slices` is a device int32 tensor [frames][iterations][2 + 2 * offsets]."""
+    return _check(_lib.ofdm_fps_sft(plan.handle, _ptr(Y), _ptr(X), frames, ctypes.byref(fp),
+                                    _ptr(slices), _ptr(out_targets), _ptr(n_targets),
+                                    _stream(stream)), "ofdm_fps_sft")

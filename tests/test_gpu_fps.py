@@ -1,0 +1,107 @@
+"""FPS-SFT on the GPU against the oracle's FPS-SFT (same seeded slice
+geometry, passed in as an input) and against the full periodogram."""
+import numpy as np
+import pytest
+
+import ofdm_synth as syn
+from oracle import ofdm_oracle as o
+from radar_cases import make_frames, oracle_params, plan_kwargs, stack_lk
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2209_03883_gb300 import radar
+    return radar, torch, torch.device("cuda:0")
+
+
+def draw_slices(seed, frames, iters, T, N, M):
+    rng = np.random.default_rng(seed)
+    arr = np.zeros((frames, iters, 2 + 2 * T), dtype=np.int32)
+    for f in range(frames):
+        for i in range(iters):
+            arr[f, i, 0] = int(rng.integers(0, N // 2)) * 2 + 1
+            arr[f, i, 1] = int(rng.integers(0, M // 2)) * 2 + 1
+            for j in range(T):
+                arr[f, i, 2 + 2 * j] = rng.integers(N)
+                arr[f, i, 3 + 2 * j] = rng.integers(M)
+    return arr
+
+
+def as_oracle_slices(arr_f, T):
+    return [(int(r[0]), int(r[1]), [(int(r[2 + 2 * j]), int(r[3 + 2 * j])) for j in range(T)]) for r in arr_f]
+
+
+def run_fps(env, p, Ys, As, slices, fp):
+    radar, torch, dev = env
+    frames = len(Ys)
+    plan = radar.Plan(**plan_kwargs(p, frames))
+    Y = torch.from_numpy(stack_lk(Ys)).to(dev)
+    X = torch.from_numpy(stack_lk(As)).to(dev)
+    sl = torch.from_numpy(slices).to(dev)
+    tg = torch.zeros((frames * p.max_targets * radar.TARGET_BYTES,), dtype=torch.uint8, device=dev)
+    nt = torch.zeros((frames,), dtype=torch.int32, device=dev)
+    radar.ofdm_fps_sft(plan, Y, X, frames, fp, sl, tg, nt)
+    torch.cuda.synchronize()
+    return radar.targets_view(tg, frames, p.max_targets), nt.cpu().numpy()
+
+
+@pytest.mark.parametrize("ci,frames", [(3, 2)])
+def test_fps_sparse_workload(env, ci, frames):
+    """1024 x 1024, K = 8 on-grid targets, 5 dB: the GPU recovers what the
+    oracle's FPS-SFT recovers, and that equals the periodogram's top-8."""
+    radar, torch, dev = env
+    cfg, fr = make_frames(ci, frames)
+    p = oracle_params(cfg)
+    T, I = 8, 4
+    slices = draw_slices(31, frames, I, T, cfg.N, cfg.M)
+    fp = radar.fps_default_params(iterations=I, offsets=T)
+    tv, nt = run_fps(env, p, [f[2] for f in fr], [f[0].A for f in fr], slices, fp)
+    ofp = o.FpsParams(iterations=I, offsets=T)
+    for i, (frm, Xp, Y) in enumerate(fr):
+        ref = o.process(Y, frm.A, p)
+        rec = o.fps_sft(ref["Hd"], as_oracle_slices(slices[i], T), ofp)
+        want = o.fps_targets(rec, cfg.N, cfg.M, p.max_targets)
+        n = int(nt[i])
+        got = [(int(t["r"]), int(t["s"])) for t in tv[i][:n]]
+        assert got == [(r, s) for _, _, r, s in want]
+        assert np.allclose(tv[i]["power"][:n], [w[0] for w in want], rtol=1e-3)
+        assert sorted(got) == sorted(zip(ref["det"].r.tolist(), ref["det"].s.tolist()))
+
+
+def test_fps_small_noiseless_exact(env):
+    """64 x 16, noiseless on-grid targets: exact recovery of every target."""
+    radar, torch, dev = env
+    cfg = syn.FrameConfig(N=64, M=16, L_cp=16, qam=4, zc_root=1, n_targets=4, on_grid=True,
+                          amp_db=(-6.0, 0.0), snr_db=(0.0, 0.0), window=0, detect_k=4)
+    frs = [syn.draw_frame(cfg, 5100 + f, noise=False) for f in range(3)]
+    Xps = [o.zc_precode(d.A, 1) for d in frs]
+    Ys = [syn.received(d, x) for d, x in zip(frs, Xps)]
+    p = o.Params(N=64, M=16, L_cp=16, zc_root=1, window=0, max_targets=4)
+    slices = draw_slices(5, 3, 6, 8, 64, 16)
+    fp = radar.fps_default_params(iterations=6, offsets=8)
+    tv, nt = run_fps(env, p, Ys, [d.A for d in frs], slices, fp)
+    for i, d in enumerate(frs):
+        truth = sorted((int(r), int(s)) for r, s in zip(d.rho, d.nu))
+        got = sorted((int(t["r"]), int(t["s"])) for t in tv[i][:int(nt[i])])
+        assert got == truth
+        # power of an on-grid noiseless target is N M |b|^2 (Eq. (17), rect window)
+        pw = {(int(t["r"]), int(t["s"])): float(t["power"]) for t in tv[i][:int(nt[i])]}
+        for r, s, b in zip(d.rho, d.nu, d.b):
+            assert abs(pw[(int(r), int(s))] - 64 * 16 * abs(b) ** 2) < 1e-3 * 64 * 16 * abs(b) ** 2
+
+
+def test_fps_rejects_bad_params(env):
+    radar, torch, dev = env
+    p = o.Params(N=64, M=16, L_cp=16)
+    plan = radar.Plan(**plan_kwargs(p, 1))
+    Y = torch.zeros((1, 16, 64), dtype=torch.complex64, device=dev)
+    sl = torch.zeros((1, 4, 18), dtype=torch.int32, device=dev)
+    with pytest.raises(radar.OfdmError):
+        radar.ofdm_fps_sft(plan, Y, Y, 1, radar.fps_default_params(offsets=9), sl)
