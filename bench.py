@@ -40,6 +40,26 @@ BYTES_PER_FRAME = 20 * CFG.N * CFG.M           # Y + X (8NM each) + map (4NM)
 COLUMN_BYTES_PER_FRAME = 16 * CFG.N * CFG.M    # the column kernel reads Y and X
 
 
+# DRAM traffic of the column kernel from one ncu capture (profiles/
+# column_pipe_kernel_1024x256_64frames.md), valid only while its sources are
+# byte-identical to the captured ones.
+TRAFFIC = {"bytes": 269.611776e6 + 7.131648e6,
+           "sources": {"paper_2209_03883_gb300/csrc/column.cu": "ab8c8510b449ec285377252d651db210e7d5bf42",
+                       "paper_2209_03883_gb300/csrc/fft.cuh": "34318dd4784cad2cecf15f849a8c0cfe4880d517"}}
+
+
+def captured_traffic():
+    import hashlib
+    for rel, sha in TRAFFIC["sources"].items():
+        try:
+            with open(os.path.join(ROOT, rel), "rb") as f:
+                if hashlib.sha1(f.read()).hexdigest() != sha:
+                    return None
+        except OSError:
+            return None
+    return TRAFFIC["bytes"]
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -302,7 +322,7 @@ def run_ours(args):
                    "l2": f"inputs {2 * FRAMES * CFG.N * CFG.M * 8 / 1e6:.0f} MB per step > 129 MB L2; no flush"},
         "roofline": {"bound": "hbm", "kernel": "column_kernel<1024>", "achieved": achieved, "peak": peak,
                      "peak_source": f"{peak_kind} hbm_gbs", "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None,
+                     "traffic": captured_traffic(),
                      "algorithmic_bytes_per_launch": COLUMN_BYTES_PER_FRAME * FRAMES,
                      "avg_launch_ms": col_avg_ms,
                      "step_frac": BYTES_PER_FRAME * FRAMES / (step_ms / 1e3) / 1e9 / peak},
