@@ -182,6 +182,54 @@ int ofdm_fps_sft(ofdm_radar_plan* plan, const ofdm_c32* Y, const ofdm_c32* X, in
                  const ofdm_fps_params* fp, const int32_t* slices, ofdm_target* out_targets,
                  int32_t* n_targets, void* stream);
 
+/* Batched frames of uneven shape (one launch of many frames).  Frames are
+ * described one by one; frames of equal (N, M, L_cp) form a group with its
+ * own plan (the base parameters give everything else; N_pad = M_pad = 0).
+ * Y and X are packed arrays in which frame f's M x N grid starts at
+ * desc[f].yx_offset complex elements; its N x M map starts at
+ * desc[f].map_offset floats of out_map (a multiple of 4).  Targets, target
+ * counts and status words are indexed by the frame's position in desc
+ * (targets: [nframes][base->max_targets]). */
+typedef struct {
+  int32_t N, M, L_cp;
+  int32_t reserved;
+  int64_t yx_offset;
+  int64_t map_offset;
+} ofdm_frame_desc;
+
+typedef struct ofdm_radar_batch ofdm_radar_batch;
+
+enum { OFDM_BATCH_NO_GRAPH = 1u, OFDM_BATCH_NO_TUNE = 2u };
+
+/* Group the frames, create one plan per group (allocates), upload the
+ * per-frame offset tables.  flags: OFDM_BATCH_NO_GRAPH launches on the
+ * stream instead of replaying a CUDA graph; OFDM_BATCH_NO_TUNE skips the
+ * launch-shape tuner. */
+int ofdm_radar_batch_create(const ofdm_radar_params* base, const ofdm_frame_desc* desc, int32_t nframes,
+                            uint32_t flags, ofdm_radar_batch** out);
+
+/* Whole chain on every frame of the batch.  Groups run concurrently (one
+ * stream each, joined back into `stream`).  The first call on a batch tunes
+ * the column kernel's launch shape of each group on these inputs (cached per
+ * (N, M, L_cp) for the process) and, unless OFDM_BATCH_NO_GRAPH, captures the
+ * launches into a CUDA graph that later calls with the same buffers replay
+ * (other buffers are captured anew).  A capture that cannot be made -- e.g.
+ * on the legacy NULL stream -- falls back to direct launches.  out_map may be
+ * NULL. */
+int ofdm_radar_batch_process(ofdm_radar_batch* b, const ofdm_c32* Y, const ofdm_c32* X, float* out_map,
+                             ofdm_target* out_targets, int32_t* n_targets, uint32_t* status, void* stream);
+
+/* Number of groups and, if shapes != NULL, [groups][5] = N, M, L_cp, frames,
+ * chosen column-kernel variant (0 = widest CTA, 4 = 4-warp CTAs, -1 = not
+ * tuned yet / not applicable).  Returns the group count. */
+int ofdm_radar_batch_groups(const ofdm_radar_batch* b, int32_t* shapes);
+
+/* 1 if the last ofdm_radar_batch_process replayed or captured a graph, 0 if
+ * it launched directly. */
+int ofdm_radar_batch_used_graph(const ofdm_radar_batch* b);
+
+void ofdm_radar_batch_destroy(ofdm_radar_batch* b);
+
 /* Kernel launches made by the last successful call on this plan. */
 int ofdm_radar_last_launch_count(const ofdm_radar_plan* plan);
 

@@ -33,12 +33,13 @@ struct ColCfg {
 // holds the current symbol's A row (then serves as the FFT exchange buffer),
 // one its Y row, and one receives the next symbol's A row by cp.async; the
 // next Y row is issued as soon as the current one has been consumed.
-template <int N>
+template <int N, int W = 0>
 struct PipeCfg {
   static constexpr int E = N / 32;
   static constexpr int BUF = smem_elems(N);  // float2 per row buffer
   static constexpr int FIT = (int)((227u * 1024u) / (3u * BUF * sizeof(float2)));
-  static constexpr int WARPS = FIT < 10 ? FIT : 10;
+  static constexpr int WMAX = FIT < 10 ? FIT : 10;
+  static constexpr int WARPS = W > 0 && W < WMAX ? W : WMAX;
   static constexpr int THREADS = 32 * WARPS;
   static constexpr size_t SMEM = (size_t)WARPS * 3 * BUF * sizeof(float2);
 };
@@ -181,11 +182,11 @@ __device__ __forceinline__ uint32_t stencil_write(const float2* v, float2* sm, f
 }
 
 // ---------------------------------------------------------------- N <= 1024: pipelined, one warp per symbol
-template <int N>
-__global__ void __launch_bounds__(PipeCfg<N>::THREADS, 1)
+template <int N, int W>
+__global__ void __launch_bounds__(PipeCfg<N, W>::THREADS, 1)
 column_pipe_kernel(const float2* __restrict__ Y, const float2* __restrict__ X, float2* __restrict__ strip,
                    uint32_t* __restrict__ wstatus, ColumnArgs a) {
-  using C = PipeCfg<N>;
+  using C = PipeCfg<N, W>;
   constexpr int E = C::E;
   extern __shared__ float2 smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -210,15 +211,20 @@ column_pipe_kernel(const float2* __restrict__ Y, const float2* __restrict__ X, f
     v = __shfl_sync(0xffffffffu, v, 0);
     return (long)(v - a.work_base);
   };
+  // Offset of symbol `sm`'s row in Y and X (frames may be scattered).
+  auto row_off = [&](long sm) -> long {
+    if (!a.frame_off) return sm * N;
+    return (long)a.frame_off[sm / a.M] + (sm % a.M) * N;
+  };
   int ia = 0, iy = 1, ifree = 2;
   long sym = ticket();
-  if (sym < total) issue_row(X + sym * N, ring + ia * C::BUF);
+  if (sym < total) issue_row(X + row_off(sym), ring + ia * C::BUF);
   cp_async_commit();
-  if (sym < total) issue_row(Y + sym * N, ring + iy * C::BUF);
+  if (sym < total) issue_row(Y + row_off(sym), ring + iy * C::BUF);
   cp_async_commit();
   long nxt = sym < total ? ticket() : total;
   for (; sym < total; sym = nxt, nxt = (nxt < total ? ticket() : total)) {
-    if (nxt < total) issue_row(X + nxt * N, ring + ifree * C::BUF);
+    if (nxt < total) issue_row(X + row_off(nxt), ring + ifree * C::BUF);
     cp_async_commit();
     const int f = (int)(sym / a.M);
     const int l = (int)(sym % a.M);
@@ -241,7 +247,7 @@ column_pipe_kernel(const float2* __restrict__ Y, const float2* __restrict__ X, f
       __syncwarp();
       flags |= divide_plain<32, E>(v, sa, sy, true, lane);
       __syncwarp();
-      if (nxt < total) issue_row(Y + nxt * N, ring + iy * C::BUF);
+      if (nxt < total) issue_row(Y + row_off(nxt), ring + iy * C::BUF);
       cp_async_commit();
       pass0 = 1;
     }
@@ -267,12 +273,12 @@ column_pipe_kernel(const float2* __restrict__ Y, const float2* __restrict__ X, f
           for (int r = 0; r < 32; ++r) sa[pad32(32 * lane + r)] = v[r];
           __syncwarp();
         } else if (h == 1) {
-          if (a.refine_tau > 0.f) refine_small_cells<N, 32, E>(v, X + sym * N, a, lane, lane);
+          if (a.refine_tau > 0.f) refine_small_cells<N, 32, E>(v, X + row_off(sym), a, lane, lane);
           cp_async_wait<1>();               // Y(sym)
           __syncwarp();
           flags |= divide_precoded<32, E>(v, sy, true, a, lane);
           __syncwarp();
-          if (nxt < total) issue_row(Y + nxt * N, ring + iy * C::BUF);
+          if (nxt < total) issue_row(Y + row_off(nxt), ring + iy * C::BUF);
           cp_async_commit();
         }
       }
@@ -281,12 +287,12 @@ column_pipe_kernel(const float2* __restrict__ Y, const float2* __restrict__ X, f
       for (int pass = pass0; pass < 2; ++pass) {
         group_fft<N, 32, +1>(v, sa, a.tw, lane, 0);
         if (pass == 0) {
-          if (a.refine_tau > 0.f) refine_small_cells<N, 32, E>(v, X + sym * N, a, lane, lane);
+          if (a.refine_tau > 0.f) refine_small_cells<N, 32, E>(v, X + row_off(sym), a, lane, lane);
           cp_async_wait<1>();               // Y(sym)
           __syncwarp();
           flags |= divide_precoded<32, E>(v, sy, true, a, lane);
           __syncwarp();
-          if (nxt < total) issue_row(Y + nxt * N, ring + iy * C::BUF);
+          if (nxt < total) issue_row(Y + row_off(nxt), ring + iy * C::BUF);
           cp_async_commit();
         }
       }
@@ -319,8 +325,9 @@ column_kernel(const float2* __restrict__ Y, const float2* __restrict__ X, float2
   for (long sym = (long)blockIdx.x * C::GROUPS + group; sym < total; sym += (long)gridDim.x * C::GROUPS) {
     const int f = (int)(sym / a.M);
     const int l = (int)(sym % a.M);
-    const float2* x = X + sym * N;
-    const float2* y = Y + sym * N;
+    const long ro = a.frame_off ? (long)a.frame_off[f] + (long)l * N : sym * N;
+    const float2* x = X + ro;
+    const float2* y = Y + ro;
     float2 v[E];
     uint32_t flags = 0;
     if (a.zc) {
@@ -377,6 +384,25 @@ zct_kernel(const float2* __restrict__ in, float2* __restrict__ out, ZctArgs a) {
   }
 }
 
+template <int N, int W>
+static cudaError_t launch_pipe(const float2* Y, const float2* X, float2* strip, uint32_t* wstatus,
+                               const ColumnArgs& a, cudaStream_t s, unsigned long long* tickets, int sms,
+                               long total) {
+  using C = PipeCfg<N, W>;
+  cudaError_t e = cudaFuncSetAttribute(column_pipe_kernel<N, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)C::SMEM);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, column_pipe_kernel<N, W>, C::THREADS, C::SMEM);
+  if (e != cudaSuccess) return e;
+  long blocks = (long)sms * (per_sm > 0 ? per_sm : 1);
+  const long need = (total + C::WARPS - 1) / C::WARPS;
+  if (blocks > need) blocks = need;
+  column_pipe_kernel<N, W><<<(unsigned)blocks, C::THREADS, C::SMEM, s>>>(Y, X, strip, wstatus, a);
+  *tickets = (unsigned long long)total + (unsigned long long)blocks * C::WARPS;
+  return cudaGetLastError();
+}
+
 template <int N>
 static cudaError_t launch_column_n(const float2* Y, const float2* X, float2* strip, uint32_t* wstatus,
                                    const ColumnArgs& a, cudaStream_t s, unsigned long long* tickets) {
@@ -386,18 +412,8 @@ static cudaError_t launch_column_n(const float2* Y, const float2* X, float2* str
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if constexpr (N <= 1024) {
-    using C = PipeCfg<N>;
-    cudaError_t e = cudaFuncSetAttribute(column_pipe_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)C::SMEM);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, column_pipe_kernel<N>, C::THREADS, C::SMEM);
-    if (e != cudaSuccess) return e;
-    long blocks = (long)sms * (per_sm > 0 ? per_sm : 1);
-    const long need = (total + C::WARPS - 1) / C::WARPS;
-    if (blocks > need) blocks = need;
-    column_pipe_kernel<N><<<(unsigned)blocks, C::THREADS, C::SMEM, s>>>(Y, X, strip, wstatus, a);
-    *tickets = (unsigned long long)total + (unsigned long long)blocks * C::WARPS;
+    if (a.pipe_warps == 4) return launch_pipe<N, 4>(Y, X, strip, wstatus, a, s, tickets, sms, total);
+    return launch_pipe<N, 0>(Y, X, strip, wstatus, a, s, tickets, sms, total);
   } else {
     using C = ColCfg<N>;
     cudaError_t e = cudaFuncSetAttribute(column_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -30,7 +30,7 @@ doppler_kernel(const float2* __restrict__ strip, float* __restrict__ map, float*
   const int r = (a.row0 + ri) % a.Np;
   const float2* g = strip + task * a.M;
   float* prow = pow + task * MP;
-  float* mrow = map ? map + ((long)f * a.Np + r) * MP : nullptr;
+  float* mrow = map ? map + (a.map_off ? (long)a.map_off[f] : (long)f * a.Np * MP) + (long)r * MP : nullptr;
 
   if constexpr (MP <= 32) {
     // Direct DFT: lane s computes one bin; g[l] is broadcast by shuffles.
@@ -74,14 +74,15 @@ doppler_kernel(const float2* __restrict__ strip, float* __restrict__ map, float*
 }
 
 __global__ void zero_rows_kernel(float* __restrict__ map, int frames, long frame_floats, long z_off,
-                                 long z_floats) {
-  // z_off and z_floats are multiples of 4 floats (M' >= 16).
+                                 long z_floats, const long long* __restrict__ map_off) {
+  // z_off, z_floats and the frame offsets are multiples of 4 floats (M' >= 16).
   const long per = z_floats / 4;
   const long total = per * frames;
   const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
     const long f = i / per, j = i % per;
-    __stcs(reinterpret_cast<float4*>(map + f * frame_floats + z_off) + j, z);
+    const long base = map_off ? (long)map_off[f] : f * frame_floats;
+    __stcs(reinterpret_cast<float4*>(map + base + z_off) + j, z);
   }
 }
 
@@ -288,6 +289,7 @@ detect_kernel(const float* __restrict__ src, ofdm_target* __restrict__ out, int3
     const uint64_t key = lane < K ? buf[lane] : 0;
     const bool valid = key != 0;
     const int nv = __popc(__ballot_sync(0xffffffffu, valid));
+    const long g = a.out_idx ? (long)a.out_idx[f] : (long)f;  // index into the caller's outputs
     if (valid && out) {
       const uint32_t idx = ~(uint32_t)(key & 0xffffffffu);
       ofdm_target tg;
@@ -296,15 +298,15 @@ detect_kernel(const float* __restrict__ src, ofdm_target* __restrict__ out, int3
       tg.power = __uint_as_float((uint32_t)(key >> 32));
       tg.range_m = (float)tg.r * a.dd;
       tg.vel_mps = (float)tg.s * a.dv;
-      out[(long)f * K + lane] = tg;
+      out[g * K + lane] = tg;
     }
     if (lane == 0) {
       const uint32_t total = s_total;
       uint32_t st = wstatus ? wstatus[f] : 0u;
       if (a.mode == OFDM_DETECT_TOPK && total < (uint32_t)K) st |= OFDM_STATUS_FEW_PEAKS;
       if (a.mode == OFDM_DETECT_THRESHOLD && total > (uint32_t)K) st |= OFDM_STATUS_OVERFLOW;
-      if (status) status[f] = st;
-      if (n_out) n_out[f] = nv;
+      if (status) status[g] = st;
+      if (n_out) n_out[g] = nv;
       if (wstatus) wstatus[f] = 0u;  // ready for the next call
     }
   }
@@ -342,14 +344,14 @@ cudaError_t launch_doppler(int Mp, const float2* strip, float* map, float* pow, 
 }
 
 cudaError_t launch_zero_rows(float* map, int frames, int Np, int Mp, int z0, int nz, cudaStream_t s,
-                             int* launches) {
+                             int* launches, const long long* map_off) {
   if (nz <= 0) return cudaSuccess;
   ++*launches;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const long frame_floats = (long)Np * Mp;
-  zero_rows_kernel<<<sms * 4, 256, 0, s>>>(map, frames, frame_floats, (long)z0 * Mp, (long)nz * Mp);
+  zero_rows_kernel<<<sms * 4, 256, 0, s>>>(map, frames, frame_floats, (long)z0 * Mp, (long)nz * Mp, map_off);
   return cudaGetLastError();
 }
 

@@ -26,6 +26,8 @@ struct ColumnArgs {
   const float4* w_df;      // [N] exp(+2 pi i m / N) as double-float
   unsigned long long* work_ctr;  // monotonic symbol ticket counter (pipelined kernel)
   unsigned long long work_base;  // counter value at the start of this launch
+  const long long* frame_off;    // per-frame complex offset of the Y / X rows, or null (f * M * N)
+  int pipe_warps;                // pipelined kernel variant: 0 = most warps that fit, 4 = 4 warps per CTA
 };
 
 struct ZctArgs {
@@ -40,6 +42,7 @@ struct DopplerArgs {
   int N, Np, M, Mp, rows, row0, frames;
   float inv_nm;           // 1 / (N M)
   const float* wl;        // [M] window over l
+  const long long* map_off;  // per-frame float offset of the map, or null (f * N' * M')
   const float2* tw;       // Mp-point pass twiddles (DIR = +1), or the Mp roots for Mp <= 32
 };
 
@@ -48,6 +51,7 @@ struct DetectArgs {
   int logMp;                      // log2(M'); N' and M' are powers of two
   int bit_words;                  // set by the launcher: candidate bit-mask words in shared memory
   int tile_rows;                  // set by the launcher: scanned rows per shared-memory tile
+  const int* out_idx;             // per-frame index into out / n_out / status, or null (f)
   long frame_stride;              // floats between frames of the input
   int compact;                    // 1: input rows are the support strip; 0: full map rows
   int frames;
@@ -80,7 +84,7 @@ cudaError_t launch_zct(int N, const float2* in, float2* out, const ZctArgs& a, c
 cudaError_t launch_doppler(int Mp, const float2* strip, float* map, float* pow, const DopplerArgs& a,
                            cudaStream_t s, int* launches);
 cudaError_t launch_zero_rows(float* map, int frames, int Np, int Mp, int z0, int nz, cudaStream_t s,
-                             int* launches);
+                             int* launches, const long long* map_off = nullptr);
 cudaError_t launch_detect(const float* pow, ofdm_target* out, int32_t* n_out, uint32_t* status,
                           uint32_t* wstatus, const DetectArgs& a, cudaStream_t s, int* launches);
 

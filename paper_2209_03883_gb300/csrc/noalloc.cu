@@ -240,17 +240,21 @@ extern "C" int ofdm_radar_process_noalloc(const ofdm_radar_params* pin, const of
   ca.w_df = ca.pre_df + N;
   ca.work_ctr = reinterpret_cast<unsigned long long*>(b + kOffCtr);
   ca.work_base = st.ctr_base;
+  ca.frame_off = nullptr;
+  ca.pipe_warps = 0;
 
   DopplerArgs da;
   da.N = N; da.Np = N; da.M = M; da.Mp = Mp; da.rows = rows; da.row0 = row0; da.frames = frames;
   da.inv_nm = (float)(1.0 / ((double)N * (double)M));
   da.wl = reinterpret_cast<float*>(b + kOffWl);
   da.tw = reinterpret_cast<float2*>(b + kOffTwM);
+  da.map_off = nullptr;
 
   DetectArgs ta;
   ta.Np = N; ta.Mp = Mp; ta.logMp = 0;
   while ((1 << ta.logMp) < Mp) ++ta.logMp;
   ta.rows = rows; ta.row0 = row0; ta.full = full; ta.compact = 1;
+  ta.out_idx = nullptr;
   ta.frame_stride = (long)rows * Mp; ta.frames = frames; ta.mode = p.detect_mode; ta.K = p.max_targets;
   ta.use_fixed_eta = p.noise_var > 0.f ? 1 : 0;
   ta.eta_fixed = p.noise_var * (float)(-log((double)p.pfa));

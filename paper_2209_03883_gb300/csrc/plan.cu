@@ -390,6 +390,8 @@ ColumnArgs column_args(const ofdm_radar_plan* pl, int frames) {
   a.w_df = pl->d_df + pl->p.N;
   a.work_ctr = pl->d_ctr + pl->ctr_slot;
   a.work_base = pl->ctr_base[pl->ctr_slot];
+  a.frame_off = nullptr;
+  a.pipe_warps = 0;
   return a;
 }
 
@@ -405,6 +407,7 @@ DopplerArgs doppler_args(const ofdm_radar_plan* pl, int frames) {
   a.inv_nm = (float)(1.0 / ((double)pl->p.N * (double)pl->p.M));
   a.wl = pl->d_wl;
   a.tw = pl->twM;
+  a.map_off = nullptr;
   return a;
 }
 
@@ -419,6 +422,7 @@ DetectArgs detect_args(const ofdm_radar_plan* pl, int frames, int compact) {
   a.row0 = pl->row0;
   a.full = pl->full;
   a.compact = compact;
+  a.out_idx = nullptr;
   a.frame_stride = compact ? (long)pl->rows * pl->Mp : (long)pl->Np * pl->Mp;
   a.frames = frames;
   a.mode = p.detect_mode;
@@ -662,6 +666,282 @@ int ofdm_fps_sft(ofdm_radar_plan* pl, const ofdm_c32* Y, const ofdm_c32* X, int3
   a.twQ = (Q == N) ? pl->twN : pl->twM;
   e = ofdm::launch_fps(Q, pl->d_strip, slices, out_targets, n_targets, pl->d_wstatus, a, s, &launches);
   return finish(pl, launches, e);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- batches of uneven frames
+#include <map>
+#include <mutex>
+#include <tuple>
+
+namespace {
+
+struct BatchGroup {
+  ofdm_radar_plan* plan = nullptr;
+  int N = 0, M = 0, L_cp = 0, n = 0;
+  long long* d_frame_off = nullptr;  // Y / X offsets of the group's frames
+  long long* d_map_off = nullptr;    // map offsets
+  int* d_idx = nullptr;              // position of each frame in the caller's desc array
+  int pipe_warps = -1;               // tuned column-kernel variant (-1: not tuned)
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+};
+
+// Process-wide tuning results: (N, M, L_cp) -> column-kernel variant.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, int> g_tune;
+
+}  // namespace
+
+struct ofdm_radar_batch {
+  ofdm_radar_params base;
+  int nframes = 0;
+  uint32_t flags = 0;
+  std::vector<BatchGroup> groups;
+  cudaEvent_t fork = nullptr;
+  bool tuned = false;
+  bool have_graph = false;
+  bool used_graph = false;
+  cudaGraphExec_t exec = nullptr;
+  const void* key[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+};
+
+namespace {
+
+// One group's chain on `s`.  Inside a graph the ticket counter is reset by a
+// memset node (a replay reuses the captured kernel arguments).
+cudaError_t run_group(BatchGroup& g, const float2* Y, const float2* X, float* map, ofdm_target* tg, int32_t* nt,
+                      uint32_t* st, cudaStream_t s, int pipe_warps, int* launches) {
+  ofdm_radar_plan* pl = g.plan;
+  cudaError_t e = cudaMemsetAsync(pl->d_ctr, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  ColumnArgs ca = column_args(pl, g.n);
+  ca.work_base = 0;
+  ca.frame_off = g.d_frame_off;
+  ca.pipe_warps = pipe_warps < 0 ? 0 : pipe_warps;
+  unsigned long long tk = 0;
+  e = ofdm::launch_column(g.N, Y, X, pl->d_strip, pl->d_wstatus, ca, s, launches, &tk);
+  if (e != cudaSuccess) return e;
+  if (map) {
+    e = ofdm::launch_zero_rows(map, g.n, pl->Np, pl->Mp, pl->z0, pl->nz, s, launches, g.d_map_off);
+    if (e != cudaSuccess) return e;
+  }
+  DopplerArgs da = doppler_args(pl, g.n);
+  da.map_off = g.d_map_off;
+  e = ofdm::launch_doppler(pl->Mp, pl->d_strip, map, pl->d_pow, da, s, launches);
+  if (e != cudaSuccess) return e;
+  DetectArgs ta = detect_args(pl, g.n, 1);
+  ta.out_idx = g.d_idx;
+  return ofdm::launch_detect(pl->d_pow, tg, nt, st, pl->d_wstatus, ta, s, launches);
+}
+
+// Time the column kernel variants of one group on the caller's inputs.
+cudaError_t tune_group(BatchGroup& g, const float2* Y, const float2* X, cudaStream_t s) {
+  const auto key = std::make_tuple(g.N, g.M, g.L_cp);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) { g.pipe_warps = it->second; return cudaSuccess; }
+  }
+  if (g.N > 1024) { g.pipe_warps = -1; return cudaSuccess; }
+  const int variants[2] = {0, 4};
+  float best = 1e30f;
+  int pick = 0;
+  cudaEvent_t e0, e1;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
+    float ms = 0.f;
+    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+      int launches = 0;
+      unsigned long long tk = 0;
+      ColumnArgs ca = column_args(g.plan, g.n);
+      ca.frame_off = g.d_frame_off;
+      ca.pipe_warps = variants[v];
+      e = cudaEventRecord(e0, s);
+      if (e == cudaSuccess) e = ofdm::launch_column(g.N, Y, X, g.plan->d_strip, g.plan->d_wstatus, ca, s, &launches, &tk);
+      g.plan->ctr_base[0] += tk;
+      if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess && rep > 0) {  // the first run warms up
+        float t = 0.f;
+        e = cudaEventElapsedTime(&t, e0, e1);
+        ms += t;
+      }
+    }
+    if (e == cudaSuccess && ms < best) { best = ms; pick = variants[v]; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // the tuning runs' status words are not reported
+  if (e == cudaSuccess) e = cudaMemsetAsync(g.plan->d_wstatus, 0, (size_t)g.n * sizeof(uint32_t), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e;
+  g.pipe_warps = pick;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = pick;
+  return cudaSuccess;
+}
+
+bool valid_shape(int N, int M, int L) {
+  return is_pow2(N) && N >= 64 && N <= 4096 && is_pow2(M) && M >= 16 && M <= 1024 && L >= 1 && L <= N;
+}
+
+}  // namespace
+
+extern "C" {
+
+void ofdm_radar_batch_destroy(ofdm_radar_batch* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (auto& g : b->groups) {
+    ofdm_radar_plan_destroy(g.plan);
+    cudaFree(g.d_frame_off);
+    cudaFree(g.d_map_off);
+    cudaFree(g.d_idx);
+    if (g.stream) cudaStreamDestroy(g.stream);
+    if (g.done) cudaEventDestroy(g.done);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
+  delete b;
+}
+
+int ofdm_radar_batch_create(const ofdm_radar_params* base, const ofdm_frame_desc* desc, int32_t nframes,
+                            uint32_t flags, ofdm_radar_batch** out) {
+  if (!base || !desc || !out || nframes < 1) return OFDM_ERR_INVALID_ARG;
+  *out = nullptr;
+  for (int f = 0; f < nframes; ++f) {
+    if (!valid_shape(desc[f].N, desc[f].M, desc[f].L_cp)) return OFDM_ERR_UNSUPPORTED_SIZE;
+    if (desc[f].yx_offset < 0 || desc[f].map_offset < 0 || (desc[f].map_offset & 3)) return OFDM_ERR_INVALID_ARG;
+  }
+  ofdm_radar_batch* b = new ofdm_radar_batch();
+  b->base = *base;
+  b->nframes = nframes;
+  b->flags = flags;
+  std::vector<std::vector<int>> members;
+  for (int f = 0; f < nframes; ++f) {
+    size_t gi = 0;
+    while (gi < b->groups.size() && !(b->groups[gi].N == desc[f].N && b->groups[gi].M == desc[f].M &&
+                                      b->groups[gi].L_cp == desc[f].L_cp))
+      ++gi;
+    if (gi == b->groups.size()) {
+      BatchGroup g;
+      g.N = desc[f].N; g.M = desc[f].M; g.L_cp = desc[f].L_cp;
+      b->groups.push_back(g);
+      members.emplace_back();
+    }
+    members[gi].push_back(f);
+  }
+  int rc = OFDM_OK;
+  cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  for (size_t gi = 0; gi < b->groups.size() && rc == OFDM_OK && e == cudaSuccess; ++gi) {
+    BatchGroup& g = b->groups[gi];
+    g.n = (int)members[gi].size();
+    ofdm_radar_params p = *base;
+    p.N = g.N; p.M = g.M; p.L_cp = g.L_cp; p.N_pad = 0; p.M_pad = 0; p.max_frames = g.n;
+    rc = ofdm_radar_plan_create(&p, &g.plan);
+    if (rc != OFDM_OK) break;
+    std::vector<long long> fo(g.n), mo(g.n);
+    std::vector<int> idx(g.n);
+    for (int i = 0; i < g.n; ++i) {
+      const ofdm_frame_desc& d = desc[members[gi][i]];
+      fo[i] = d.yx_offset;
+      mo[i] = d.map_offset;
+      idx[i] = members[gi][i];
+    }
+    e = dalloc(&g.d_frame_off, (size_t)g.n);
+    if (e == cudaSuccess) e = dalloc(&g.d_map_off, (size_t)g.n);
+    if (e == cudaSuccess) e = dalloc(&g.d_idx, (size_t)g.n);
+    if (e == cudaSuccess) e = cudaMemcpy(g.d_frame_off, fo.data(), g.n * sizeof(long long), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g.d_map_off, mo.data(), g.n * sizeof(long long), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g.d_idx, idx.data(), g.n * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming);
+  }
+  if (rc == OFDM_OK && e != cudaSuccess) rc = e == cudaErrorMemoryAllocation ? OFDM_ERR_NO_MEMORY : cuda_fail(e);
+  if (rc != OFDM_OK) {
+    ofdm_radar_batch_destroy(b);
+    cudaGetLastError();
+    return rc;
+  }
+  *out = b;
+  return OFDM_OK;
+}
+
+int ofdm_radar_batch_groups(const ofdm_radar_batch* b, int32_t* shapes) {
+  if (!b) return OFDM_ERR_INVALID_ARG;
+  if (shapes)
+    for (size_t i = 0; i < b->groups.size(); ++i) {
+      const BatchGroup& g = b->groups[i];
+      const int32_t row[5] = {g.N, g.M, g.L_cp, g.n, g.pipe_warps};
+      for (int k = 0; k < 5; ++k) shapes[5 * i + k] = row[k];
+    }
+  return (int)b->groups.size();
+}
+
+int ofdm_radar_batch_used_graph(const ofdm_radar_batch* b) { return b ? (b->used_graph ? 1 : 0) : OFDM_ERR_INVALID_ARG; }
+
+int ofdm_radar_batch_process(ofdm_radar_batch* b, const ofdm_c32* Yc, const ofdm_c32* Xc, float* map,
+                             ofdm_target* tg, int32_t* nt, uint32_t* st, void* stream) {
+  if (!b || !Yc || !Xc) return OFDM_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const float2* Y = (const float2*)Yc;
+  const float2* X = (const float2*)Xc;
+  cudaError_t e = cudaSuccess;
+  if (!b->tuned) {
+    for (auto& g : b->groups) {
+      if (b->flags & OFDM_BATCH_NO_TUNE) { g.pipe_warps = -1; continue; }
+      e = tune_group(g, Y, X, s);
+      if (e != cudaSuccess) return cuda_fail(e);
+    }
+    b->tuned = true;
+  }
+  int launches = 0;
+  auto launch_all = [&](cudaStream_t main) -> cudaError_t {
+    cudaError_t r = cudaEventRecord(b->fork, main);
+    for (auto& g : b->groups) {
+      if (r == cudaSuccess) r = cudaStreamWaitEvent(g.stream, b->fork, 0);
+      if (r == cudaSuccess) r = run_group(g, Y, X, map, tg, nt, st, g.stream, g.pipe_warps, &launches);
+      if (r == cudaSuccess) r = cudaEventRecord(g.done, g.stream);
+      if (r == cudaSuccess) r = cudaStreamWaitEvent(main, g.done, 0);
+    }
+    return r;
+  };
+  const void* key[7] = {Y, X, map, tg, nt, st, stream};
+  const bool graph_ok = !(b->flags & OFDM_BATCH_NO_GRAPH) && s != nullptr;
+  if (graph_ok && b->have_graph && memcmp(key, b->key, sizeof key) == 0) {
+    e = cudaGraphLaunch(b->exec, s);
+    b->used_graph = true;
+    return e == cudaSuccess ? OFDM_OK : cuda_fail(e);
+  }
+  if (graph_ok) {
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t r = launch_all(s);
+      e = cudaStreamEndCapture(s, &graph);
+      if (r != cudaSuccess) e = r;
+    }
+    if (e == cudaSuccess) {
+      if (b->exec) cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+      e = cudaGraphInstantiate(&b->exec, graph, 0);
+    }
+    if (graph) cudaGraphDestroy(graph);
+    if (e == cudaSuccess) {
+      memcpy(b->key, key, sizeof key);
+      b->have_graph = true;
+      e = cudaGraphLaunch(b->exec, s);
+      b->used_graph = true;
+      return e == cudaSuccess ? OFDM_OK : cuda_fail(e);
+    }
+    cudaGetLastError();  // capture failed: launch directly below
+    b->have_graph = false;
+  }
+  b->used_graph = false;
+  e = launch_all(s);
+  return e == cudaSuccess ? OFDM_OK : cuda_fail(e);
 }
 
 }  // extern "C"

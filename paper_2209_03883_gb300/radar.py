@@ -44,6 +44,14 @@ class Target(ctypes.Structure):
 TARGET_BYTES = ctypes.sizeof(Target)   # 20
 
 
+class FrameDesc(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int32), ("M", ctypes.c_int32), ("L_cp", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("yx_offset", ctypes.c_int64), ("map_offset", ctypes.c_int64)]
+
+
+BATCH_NO_GRAPH, BATCH_NO_TUNE = 1, 2
+
+
 class FpsParams(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("offsets", ctypes.c_int32),
                 ("max_recover", ctypes.c_int32), ("bin_pfa", ctypes.c_float),
@@ -84,6 +92,16 @@ def _load():
     lib.ofdm_fps_default_params.restype = None
     lib.ofdm_fps_sft.argtypes = [vp, vp, vp, i32, P(FpsParams), vp, vp, vp, vp]
     lib.ofdm_fps_sft.restype = ctypes.c_int
+    lib.ofdm_radar_batch_create.argtypes = [P(Params), vp, i32, ctypes.c_uint32, P(vp)]
+    lib.ofdm_radar_batch_create.restype = ctypes.c_int
+    lib.ofdm_radar_batch_process.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.ofdm_radar_batch_process.restype = ctypes.c_int
+    lib.ofdm_radar_batch_groups.argtypes = [vp, vp]
+    lib.ofdm_radar_batch_groups.restype = ctypes.c_int
+    lib.ofdm_radar_batch_used_graph.argtypes = [vp]
+    lib.ofdm_radar_batch_used_graph.restype = ctypes.c_int
+    lib.ofdm_radar_batch_destroy.argtypes = [vp]
+    lib.ofdm_radar_batch_destroy.restype = None
     lib.ofdm_radar_strerror.argtypes = [ctypes.c_int]
     lib.ofdm_radar_strerror.restype = ctypes.c_char_p
     for name in ("ofdm_radar_plan_create", "ofdm_radar_support_rows", "ofdm_radar_process",
@@ -282,3 +300,43 @@ def ofdm_fps_sft(plan: Plan, Y, X, frames, fp: FpsParams, slices, out_targets=No
     return _check(_lib.ofdm_fps_sft(plan.handle, _ptr(Y), _ptr(X), frames, ctypes.byref(fp),
                                     _ptr(slices), _ptr(out_targets), _ptr(n_targets),
                                     _stream(stream)), "ofdm_fps_sft")
+
+
+class Batch:
+    """Frames of uneven shape processed together (ofdm_radar_batch_*)."""
+
+    def __init__(self, params: Params, descs, flags=0):
+        arr = (FrameDesc * len(descs))()
+        for i, d in enumerate(descs):
+            arr[i] = FrameDesc(*d[:3], 0, d[3], d[4])
+        self.nframes = len(descs)
+        self.max_targets = params.max_targets
+        h = ctypes.c_void_p()
+        _check(_lib.ofdm_radar_batch_create(ctypes.byref(params), ctypes.cast(arr, ctypes.c_void_p),
+                                            len(descs), flags, ctypes.byref(h)), "ofdm_radar_batch_create")
+        self._h = h
+
+    def groups(self):
+        n = _check(_lib.ofdm_radar_batch_groups(self._h, None), "ofdm_radar_batch_groups")
+        arr = (ctypes.c_int32 * (5 * n))()
+        _lib.ofdm_radar_batch_groups(self._h, ctypes.cast(arr, ctypes.c_void_p))
+        return [tuple(arr[5 * i:5 * i + 5]) for i in range(n)]
+
+    def used_graph(self):
+        return bool(_lib.ofdm_radar_batch_used_graph(self._h))
+
+    def process(self, Y, X, out_map, targets, n_targets, status, stream=None):
+        return _check(_lib.ofdm_radar_batch_process(self._h, _ptr(Y), _ptr(X), _ptr(out_map), _ptr(targets),
+                                                    _ptr(n_targets), _ptr(status), _stream(stream)),
+                      "ofdm_radar_batch_process")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.ofdm_radar_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
