@@ -219,6 +219,123 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _gpu_precode_groups(radar, torch, dev, shapes, As):
+    """Transmitted grids via the library's own ZC transform, one plan per shape."""
+    out = [None] * len(As)
+    by = {}
+    for i, sh in enumerate(shapes):
+        by.setdefault(sh, []).append(i)
+    for (N, M, L), idx in by.items():
+        plan = radar.Plan(N=N, M=M, L_cp=L, max_frames=len(idx))
+        Ad = torch.from_numpy(np.stack([syn.to_lk(As[i]) for i in idx])).to(dev)
+        Xd = torch.empty_like(Ad)
+        radar.ofdm_zc_precode(plan, Ad, Xd, len(idx))
+        Xn = Xd.cpu().numpy()
+        for j, i in enumerate(idx):
+            out[i] = syn.from_lk(Xn[j]).astype(np.complex128)
+        plan.close()
+    return out
+
+
+def extra_batched(radar, torch, dev, stream, steps, n_frames=512):
+    """The uneven workload: 512 frames, N in {256..2048}, M in {64, 128, 256},
+    L_cp = N/8, 1-16 targets, SNR U[-15, 5] dB, QPSK/16-QAM; one graph replay
+    per step."""
+    rng = np.random.default_rng(4 * 1000)
+    shapes5 = syn.mixed_batch_shapes(rng, n_frames)
+    frames = []
+    for f, (N, M, L, K, q) in enumerate(shapes5):
+        cfg = syn.FrameConfig(N=N, M=M, L_cp=L, qam=q, zc_root=1, n_targets=K, on_grid=False,
+                              amp_db=(-20.0, 0.0), snr_db=(-15.0, 5.0), window=1, detect_k=16)
+        frames.append(syn.draw_frame(cfg, syn.seed_for(4, f)))
+    shapes = [(N, M, L) for N, M, L, _, _ in shapes5]
+    Xps = _gpu_precode_groups(radar, torch, dev, shapes, [d.A for d in frames])
+    Ys, Xs, descs, yx = [], [], [], 0
+    for (N, M, L), d, Xp in zip(shapes, frames, Xps):
+        Ys.append(syn.to_lk(syn.received(d, Xp)).ravel())
+        Xs.append(syn.to_lk(d.A).ravel())
+        descs.append((N, M, L, yx, yx))
+        yx += N * M
+    Y = torch.from_numpy(np.concatenate(Ys)).to(dev)
+    X = torch.from_numpy(np.concatenate(Xs)).to(dev)
+    K = 16
+    b = radar.Batch(radar.default_params(max_targets=K, window=1, zc_root=1), descs)
+    mp = torch.empty((yx,), dtype=torch.float32, device=dev)
+    tg = torch.zeros((n_frames * K * radar.TARGET_BYTES,), dtype=torch.uint8, device=dev)
+    nt = torch.zeros((n_frames,), dtype=torch.int32, device=dev)
+    st = torch.zeros((n_frames,), dtype=torch.int32, device=dev)
+    for _ in range(3):
+        b.process(Y, X, mp, tg, nt, st, stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        b.process(Y, X, mp, tg, nt, st, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    peak, _ = load_peaks()
+    byts = 20.0 * yx
+    out = {"workload": "512 uneven frames (N 256-2048, M 64-256, L_cp N/8), one CUDA graph per step",
+           "value": n_frames / (ms / 1e3), "unit": "frames/s", "ms_per_step": ms,
+           "hbm_frac": byts / (ms / 1e3) / 1e9 / peak, "graph": b.used_graph(),
+           "groups": [list(g) for g in b.groups()]}
+    b.close()
+    return out
+
+
+def extra_fps(radar, torch, dev, stream, steps, n_frames=32):
+    """The sparse workload (1024 x 1024, K = 8 on-grid, 5 dB, rect window):
+    FPS-SFT (4 iterations x 8 slices) against the full periodogram, same frames."""
+    cfg = syn.CONFIGS[3]
+    frames = [syn.draw_frame(cfg, syn.seed_for(3, f)) for f in range(n_frames)]
+    plan = radar.Plan(N=cfg.N, M=cfg.M, L_cp=cfg.L_cp, zc_root=1, window=0, max_targets=8,
+                      max_frames=n_frames)
+    Ad = torch.from_numpy(np.stack([syn.to_lk(d.A) for d in frames])).to(dev)
+    Xd = torch.empty_like(Ad)
+    radar.ofdm_zc_precode(plan, Ad, Xd, n_frames)
+    Xn = Xd.cpu().numpy()
+    Y = torch.from_numpy(np.stack([syn.to_lk(syn.received(d, syn.from_lk(Xn[i]).astype(np.complex128)))
+                                   for i, d in enumerate(frames)])).to(dev)
+    rng = np.random.default_rng(3 * 1000 + 999)
+    T, I = 8, 4
+    sl = np.zeros((n_frames, I, 2 + 2 * T), dtype=np.int32)
+    sl[:, :, 0:2] = rng.integers(0, 512, size=(n_frames, I, 2)) * 2 + 1
+    sl[:, :, 2::2] = rng.integers(0, cfg.N, size=(n_frames, I, T))
+    sl[:, :, 3::2] = rng.integers(0, cfg.M, size=(n_frames, I, T))
+    sld = torch.from_numpy(sl).to(dev)
+    fp = radar.fps_default_params(iterations=I, offsets=T)
+    out = radar.alloc_outputs(plan, n_frames, dev)
+    tg2 = torch.zeros_like(out["targets"])
+    nt2 = torch.zeros_like(out["n_targets"])
+
+    def t_of(fn):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    ms_p = t_of(lambda: radar.ofdm_radar_process(plan, Y, Ad, n_frames, out["map"], out["targets"],
+                                                   out["n_targets"], out["status"], stream))
+    ms_f = t_of(lambda: radar.ofdm_fps_sft(plan, Y, Ad, n_frames, fp, sld, tg2, nt2, stream))
+    a = radar.targets_view(out["targets"], n_frames, 8)
+    b = radar.targets_view(tg2, n_frames, 8)
+    agree = sum(sorted((int(t["r"]), int(t["s"])) for t in a[f][:int(out["n_targets"][f])]) ==
+                sorted((int(t["r"]), int(t["s"])) for t in b[f][:int(nt2[f])]) for f in range(n_frames))
+    plan.close()
+    return {"workload": "32 frames 1024x1024, K=8 on-grid, 5 dB, rect window",
+            "periodogram": {"value": n_frames / (ms_p / 1e3), "unit": "frames/s", "ms_per_step": ms_p},
+            "fps_sft": {"value": n_frames / (ms_f / 1e3), "unit": "frames/s", "ms_per_step": ms_f,
+                        "iterations": I, "slices": T},
+            "bins_agree_frames": f"{agree}/{n_frames}"}
+
+
 def run_ours(args):
     import torch
     rank, world, local, dist = dist_setup(args.gpus)
@@ -333,6 +450,17 @@ def run_ours(args):
         "clocks": clocks,
         "detection_hits": f"{hits}/{5 * FRAMES} targets within one bin",
     }
+    if not args.no_extra:
+        extra = {}
+        try:
+            extra["batched_uneven"] = extra_batched(radar, torch, dev, stream, max(3, min(args.steps, 10)))
+        except Exception as exc:  # report, never hide, a failing secondary measurement
+            extra["batched_uneven"] = {"error": str(exc)}
+        try:
+            extra["sparse_fps_vs_periodogram"] = extra_fps(radar, torch, dev, stream, max(3, min(args.steps, 10)))
+        except Exception as exc:
+            extra["sparse_fps_vs_periodogram"] = {"error": str(exc)}
+        line["extra"] = extra
     if rank == 0 and args.gpus == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -349,6 +477,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batched and FPS-SFT measurements")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -230,6 +230,62 @@ int ofdm_radar_batch_used_graph(const ofdm_radar_batch* b);
 
 void ofdm_radar_batch_destroy(ofdm_radar_batch* b);
 
+/* ---- Learned proposal (the paper has no counterpart: its conclusion names
+ * machine learning as future work).  A coarse range-Doppler map -- an M/4-
+ * point Doppler DFT of the first M/4 symbols of the DFT-CE range profile,
+ * max-pooled 4x over range rows, x = log(1 + C / mean C) -- feeds a 3-layer
+ * CNN (3x3 convolutions 1->16->16->1 with ReLU, BF16 weights, FP32
+ * accumulation).  Coarse cells whose logit exceeds a threshold are refined
+ * exactly: the periodogram value of Eq. (17) on the 8 x 8 fine cells around
+ * each, local maxima of the inner 6 x 6, strongest max_targets reported.
+ * Frames with more candidates than the cap fall back to the full
+ * periodogram and detection (status bit OFDM_STATUS_FALLBACK).
+ * Requirements: M in {256, 512, 1024}, M' = M, L_cp + 2 < N (Hann/Hamming) or
+ * L_cp < N (rect). */
+enum { OFDM_STATUS_FALLBACK = 16u };
+
+/* Allocate the learned path's workspace for max_frames (coarse maps, CNN
+ * activations, logits).  Must precede the two calls below. */
+int ofdm_radar_learned_prepare(ofdm_radar_plan* plan);
+
+/* Coarse-map height and width for this plan. */
+int ofdm_radar_coarse_shape(const ofdm_radar_plan* plan, int32_t* height, int32_t* width);
+
+/* Steps a1-a5 and the coarse map: x_out [frames][height][width] float32
+ * (the CNN input).  x_out may be NULL (kept in the workspace). */
+int ofdm_radar_coarse_map(ofdm_radar_plan* plan, const ofdm_c32* Y, const ofdm_c32* X, int32_t frames,
+                          float* x_out, void* stream);
+
+/* The chain with the learned proposal in place of the full Doppler stage and
+ * detection.  theta: DEVICE float32 network parameters in the order
+ * w1[16][1][3][3], b1[16], w2[16][16][3][3], b2[16], w3[1][16][3][3], b3[1]
+ * (ofdm_cnn_param_count() floats; weights rounded to BF16 when used, biases
+ * FP32).  A coarse cell
+ * is a candidate when its logit exceeds logit_threshold; more than
+ * max_candidates (1..256) candidates send the frame to the fallback. */
+int ofdm_radar_process_learned(ofdm_radar_plan* plan, const float* theta, const ofdm_c32* Y, const ofdm_c32* X,
+                               int32_t frames, float logit_threshold, int32_t max_candidates,
+                               ofdm_target* out_targets, int32_t* n_targets, uint32_t* status, void* stream);
+
+/* The CNN's own kernels, on device buffers [B][C][H][W] (no plan needed).
+ * bf16 != 0 rounds the weights (not the biases) to BF16 as they are used
+ * (inference and training alike); accumulation is FP32. */
+int ofdm_cnn_param_count(void);
+int ofdm_cnn_forward(const float* theta, int32_t bf16, const float* x, int32_t B, int32_t H, int32_t W,
+                     float* a1, float* a2, float* logits, void* stream);
+/* Gradient of the loss w.r.t. theta (written to gtheta) given d loss / d logits;
+ * ga1, ga2: [B][16][H][W] workspace. */
+int ofdm_cnn_backward(const float* theta, int32_t bf16, const float* x, const float* a1, const float* a2,
+                      const float* glogits, int32_t B, int32_t H, int32_t W, float* ga1, float* ga2,
+                      float* gtheta, void* stream);
+/* Mean binary cross-entropy with logits (positives weighted by pos_weight):
+ * *loss (device float) and d loss / d logits. */
+int ofdm_cnn_bce(const float* logits, const float* labels, int32_t n, float pos_weight, float* loss,
+                 float* glogits, void* stream);
+/* One Adam step (bias-corrected, step >= 1) on theta in place. */
+int ofdm_cnn_adam(float* theta, const float* grad, float* m, float* v, int32_t n, int32_t step, float lr,
+                  float beta1, float beta2, float eps, void* stream);
+
 /* Kernel launches made by the last successful call on this plan. */
 int ofdm_radar_last_launch_count(const ofdm_radar_plan* plan);
 

@@ -175,3 +175,39 @@ def mixed_batch_shapes(rng: np.random.Generator, n_frames: int):
     K = rng.integers(1, 17, size=n_frames)
     Q = rng.choice([4, 16], size=n_frames)
     return [(int(n), int(m), int(n) // 8, int(k), int(q)) for n, m, k, q in zip(Ns, Ms, K, Q)]
+
+
+def draw_frames_torch(cfg: FrameConfig, seeds, device, precode):
+    """A batch of frames generated on the device (for training and large
+    benchmarks).  Same recipe as draw_frame -- QAM data, targets inside the CP
+    support, H = sum_p b_p e^{-j2pi k rho/N} e^{+j2pi l nu/M}, AWGN -- with the
+    per-frame randomness from PCG64 (targets, SNR) and torch's Philox
+    generator seeded from the first seed (symbols, noise).  `precode` maps a
+    [B][M][N] complex64 tensor of QAM grids to the transmitted grids.
+    Returns Y, A (both [B][M][N] complex64 on the device) and the targets."""
+    import torch
+    B, N, M = len(seeds), cfg.N, cfg.M
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seeds[0]))
+    m = int(round(np.sqrt(cfg.qam)))
+    levels = (2.0 * torch.arange(m, device=device) - (m - 1)) / np.sqrt(2.0 * (m * m - 1) / 3.0)
+    iq = torch.randint(0, m, (2, B, M, N), generator=g, device=device)
+    A = torch.complex(levels[iq[0]], levels[iq[1]]).to(torch.complex64)
+    Xp = precode(A)
+    k = torch.arange(N, device=device, dtype=torch.float64)
+    l = torch.arange(M, device=device, dtype=torch.float64)
+    Y = torch.empty_like(A)
+    truth = []
+    for i, sd in enumerate(seeds):
+        rng = np.random.Generator(np.random.PCG64(int(sd)))
+        rho, nu, b = draw_targets(rng, cfg.n_targets, N, M, cfg.L_cp, cfg.on_grid, cfg.amp_db)
+        snr = float(rng.uniform(*cfg.snr_db)) if cfg.snr_db[1] > cfg.snr_db[0] else cfg.snr_db[0]
+        H = torch.zeros((M, N), dtype=torch.complex128, device=device)
+        for r, v, a in zip(rho, nu, b):
+            H += complex(a) * torch.outer(torch.exp(2j * np.pi * l * v / M), torch.exp(-2j * np.pi * k * r / N))
+        s2 = 10.0 ** (-snr / 10.0)
+        Z = np.sqrt(s2 / 2.0) * torch.complex(torch.randn((M, N), generator=g, device=device, dtype=torch.float32),
+                                              torch.randn((M, N), generator=g, device=device, dtype=torch.float32))
+        Y[i] = (Xp[i].to(torch.complex128) * H).to(torch.complex64) + Z
+        truth.append((rho, nu, b, snr))
+    return Y, A, truth

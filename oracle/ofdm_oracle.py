@@ -474,3 +474,106 @@ def fps_targets(rec, N: int, M: int, K: int):
         rows.append((abs(a) ** 2 / (N * M), r * M + (s + M // 2), r, s))
     rows.sort(key=lambda t: (-t[0], t[1]))
     return rows[:K]
+
+
+# --------------------------------------------------------------------------
+# Learned proposal (not in the paper; its conclusion names machine learning
+# as future work).  FP64 definition of the coarse map, the 3-layer CNN, its
+# gradients and the training loss, for checking the GPU kernels.
+# --------------------------------------------------------------------------
+CNN_SHAPES = (("w1", (16, 1, 3, 3)), ("b1", (16,)), ("w2", (16, 16, 3, 3)), ("b2", (16,)),
+              ("w3", (1, 16, 3, 3)), ("b3", (1,)))
+
+
+def cnn_unflatten(theta: np.ndarray) -> dict:
+    out, o = {}, 0
+    for name, shp in CNN_SHAPES:
+        n = int(np.prod(shp))
+        out[name] = np.asarray(theta[o:o + n], dtype=np.float64).reshape(shp)
+        o += n
+    return out
+
+
+def cnn_n_params() -> int:
+    return sum(int(np.prod(s)) for _, s in CNN_SHAPES)
+
+
+def conv3x3(x: np.ndarray, w: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Same-size 3x3 convolution with zero padding: x [B, Ci, H, W], w [Co, Ci, 3, 3]."""
+    B, Ci, H, W = x.shape
+    xp = np.zeros((B, Ci, H + 2, W + 2))
+    xp[:, :, 1:-1, 1:-1] = x
+    y = np.zeros((B, w.shape[0], H, W))
+    for dy in range(3):
+        for dx in range(3):
+            y += np.einsum("oc,bchw->bohw", w[:, :, dy, dx], xp[:, :, dy:dy + H, dx:dx + W])
+    return y + b[None, :, None, None]
+
+
+def cnn_forward(x: np.ndarray, theta: np.ndarray):
+    """conv(1->16)-ReLU-conv(16->16)-ReLU-conv(16->1): logits and saved activations."""
+    p = cnn_unflatten(theta)
+    z1 = conv3x3(x, p["w1"], p["b1"])
+    a1 = np.maximum(z1, 0)
+    z2 = conv3x3(a1, p["w2"], p["b2"])
+    a2 = np.maximum(z2, 0)
+    z3 = conv3x3(a2, p["w3"], p["b3"])
+    return z3, (x, z1, a1, z2, a2)
+
+
+def bce_logits(z: np.ndarray, y: np.ndarray, pos_weight: float):
+    """Mean over cells of -[pw y log s(z) + (1 - y) log(1 - s(z))] and its gradient."""
+    ls = -np.logaddexp(0.0, -z)            # log sigmoid(z)
+    l1s = -np.logaddexp(0.0, z)            # log(1 - sigmoid(z))
+    n = z.size
+    loss = -np.sum(pos_weight * y * ls + (1 - y) * l1s) / n
+    s = 1.0 / (1.0 + np.exp(-z))
+    g = (pos_weight * y * (s - 1) + (1 - y) * s) / n
+    return loss, g
+
+
+def conv3x3_backward(x, w, gy):
+    """Gradients of conv3x3 w.r.t. its input, weights and bias."""
+    B, Ci, H, W = x.shape
+    xp = np.zeros((B, Ci, H + 2, W + 2))
+    xp[:, :, 1:-1, 1:-1] = x
+    gw = np.zeros_like(w)
+    gxp = np.zeros_like(xp)
+    for dy in range(3):
+        for dx in range(3):
+            gw[:, :, dy, dx] = np.einsum("bohw,bchw->oc", gy, xp[:, :, dy:dy + H, dx:dx + W])
+            gxp[:, :, dy:dy + H, dx:dx + W] += np.einsum("oc,bohw->bchw", w[:, :, dy, dx], gy)
+    return gxp[:, :, 1:-1, 1:-1], gw, gy.sum(axis=(0, 2, 3))
+
+
+def cnn_backward(saved, theta, gz3):
+    """Gradient of a loss w.r.t. the flat parameters, given dL/dlogits."""
+    x, z1, a1, z2, a2 = saved
+    p = cnn_unflatten(theta)
+    ga2, gw3, gb3 = conv3x3_backward(a2, p["w3"], gz3)
+    gz2 = ga2 * (z2 > 0)
+    ga1, gw2, gb2 = conv3x3_backward(a1, p["w2"], gz2)
+    gz1 = ga1 * (z1 > 0)
+    _, gw1, gb1 = conv3x3_backward(x, p["w1"], gz1)
+    g = {"w1": gw1, "b1": gb1, "w2": gw2, "b2": gb2, "w3": gw3, "b3": gb3}
+    return np.concatenate([g[n].ravel() for n, _ in CNN_SHAPES])
+
+
+def coarse_map(g_rows: np.ndarray, window_kind: int) -> np.ndarray:
+    """The learned proposal's input from the support rows of the range profile
+    g_rows [rows][M] (workspace order): an M/4-point Doppler DFT of the first M/4
+    symbols with the window over those symbols, |.|^2, the maximum over each
+    group of 4 rows, columns centred like the map, x = log(1 + C / mean C)."""
+    rows, M = g_rows.shape
+    Mc = M // 4
+    w4 = window(Mc, window_kind)
+    D = (g_rows[:, :Mc] * w4[None, :]) @ dft_matrix(Mc).T
+    P = np.abs(D) ** 2
+    Hc = (rows + 3) // 4
+    C = np.zeros((Hc, Mc))
+    for rc in range(Hc):
+        C[rc] = P[4 * rc:4 * rc + 4].max(axis=0)
+    Cs = np.empty_like(C)
+    for c in range(Mc):
+        Cs[:, c] = C[:, (c - Mc // 2) % Mc]
+    return np.log1p(Cs / Cs.mean())

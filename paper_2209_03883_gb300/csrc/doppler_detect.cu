@@ -26,6 +26,7 @@ doppler_kernel(const float2* __restrict__ strip, float* __restrict__ map, float*
   const long task = (long)blockIdx.x * kDopWarps + warp;
   if (task >= (long)a.frames * a.rows) return;
   const int f = (int)(task / a.rows);
+  if (a.frame_mask && !a.frame_mask[f]) return;
   const int ri = (int)(task % a.rows);
   const int r = (a.row0 + ri) % a.Np;
   const float2* g = strip + task * a.M;
@@ -172,6 +173,7 @@ detect_kernel(const float* __restrict__ src, ofdm_target* __restrict__ out, int3
   __shared__ uint32_t s_prefix, s_rank, s_n, s_total;
   __shared__ uint64_t s_floor;
   const int f = blockIdx.x;
+  if (a.frame_mask && !a.frame_mask[f]) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const float* base = src + (long)f * a.frame_stride;
   const int n = a.rows << a.logMp;

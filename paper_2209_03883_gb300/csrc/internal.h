@@ -43,6 +43,7 @@ struct DopplerArgs {
   float inv_nm;           // 1 / (N M)
   const float* wl;        // [M] window over l
   const long long* map_off;  // per-frame float offset of the map, or null (f * N' * M')
+  const int* frame_mask;     // process only frames with mask != 0, or null (all)
   const float2* tw;       // Mp-point pass twiddles (DIR = +1), or the Mp roots for Mp <= 32
 };
 
@@ -52,6 +53,7 @@ struct DetectArgs {
   int bit_words;                  // set by the launcher: candidate bit-mask words in shared memory
   int tile_rows;                  // set by the launcher: scanned rows per shared-memory tile
   const int* out_idx;             // per-frame index into out / n_out / status, or null (f)
+  const int* frame_mask;          // process only frames with mask != 0, or null (all)
   long frame_stride;              // floats between frames of the input
   int compact;                    // 1: input rows are the support strip; 0: full map rows
   int frames;
@@ -72,6 +74,21 @@ struct FpsArgs {
   const float4* w_df;              // exp(+2 pi i m / N), double-float (hi parts used)
   const float2* twQ;               // Q-point pass twiddles
 };
+
+struct RefineArgs {
+  int N, M, rows, row0, Hc, Mc, frames, K, cap;
+  float zthr, inv_nm, dd, dv;
+  const float* wl;
+};
+
+cudaError_t launch_coarse(const float2* strip, unsigned* cpow, float* x, int rows, int M, int frames,
+                          const float* w4, const float2* tw, cudaStream_t s, int* launches);
+cudaError_t launch_refine(const float2* strip, const float* logits, ofdm_target* out, int32_t* n_out,
+                          uint32_t* status, uint32_t* wstatus, int* mask, const RefineArgs& a, cudaStream_t s,
+                          int* launches);
+
+cudaError_t cnn_forward(const float* th, int bf16, const float* x, int B, int H, int W, float* a1, float* a2,
+                        float* z, cudaStream_t s);
 
 cudaError_t launch_fps(int Q, const float2* strip, const int32_t* slices, ofdm_target* out, int32_t* n_out,
                        uint32_t* wstatus, const FpsArgs& a, cudaStream_t s, int* launches);

@@ -249,12 +249,14 @@ extern "C" int ofdm_radar_process_noalloc(const ofdm_radar_params* pin, const of
   da.wl = reinterpret_cast<float*>(b + kOffWl);
   da.tw = reinterpret_cast<float2*>(b + kOffTwM);
   da.map_off = nullptr;
+  da.frame_mask = nullptr;
 
   DetectArgs ta;
   ta.Np = N; ta.Mp = Mp; ta.logMp = 0;
   while ((1 << ta.logMp) < Mp) ++ta.logMp;
   ta.rows = rows; ta.row0 = row0; ta.full = full; ta.compact = 1;
   ta.out_idx = nullptr;
+  ta.frame_mask = nullptr;
   ta.frame_stride = (long)rows * Mp; ta.frames = frames; ta.mode = p.detect_mode; ta.K = p.max_targets;
   ta.use_fixed_eta = p.noise_var > 0.f ? 1 : 0;
   ta.eta_fixed = p.noise_var * (float)(-log((double)p.pfa));

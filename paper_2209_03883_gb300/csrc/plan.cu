@@ -45,6 +45,12 @@ struct ofdm_radar_plan {
   cudaStream_t hs[2] = {nullptr, nullptr};
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   int last_launches = 0;
+  // learned proposal workspace (ofdm_radar_learned_prepare)
+  int Hc = 0, Mc = 0;
+  unsigned* d_cpow = nullptr;
+  float *d_cx = nullptr, *d_a1 = nullptr, *d_a2 = nullptr, *d_logit = nullptr, *d_w4 = nullptr;
+  float2* d_twMc = nullptr;
+  int* d_mask = nullptr;
   // per-kernel timing (ofdm_radar_timing_enable)
   int timing = 0;
   int nrec = 0;
@@ -81,6 +87,17 @@ struct ScopedTimer {
 }  // namespace
 
 namespace {
+
+__global__ void mark_fallback_kernel(const int* mask, uint32_t* status, int frames) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f < frames && mask[f] && status) status[f] |= OFDM_STATUS_FALLBACK;
+}
+
+cudaError_t mark_fallback(const int* mask, uint32_t* status, int frames, cudaStream_t s) {
+  if (!status) return cudaSuccess;
+  mark_fallback_kernel<<<(frames + 255) / 256, 256, 0, s>>>(mask, status, frames);
+  return cudaGetLastError();
+}
 
 thread_local char g_errbuf[512];
 
@@ -165,6 +182,14 @@ void ofdm_radar_plan_destroy(ofdm_radar_plan* plan) {
   cudaFree(plan->d_pow);
   cudaFree(plan->d_wstatus);
   cudaFree(plan->d_ctr);
+  cudaFree(plan->d_cpow);
+  cudaFree(plan->d_cx);
+  cudaFree(plan->d_a1);
+  cudaFree(plan->d_a2);
+  cudaFree(plan->d_logit);
+  cudaFree(plan->d_w4);
+  cudaFree(plan->d_twMc);
+  cudaFree(plan->d_mask);
   cudaFree(plan->d_Y);
   cudaFree(plan->d_X);
   cudaFree(plan->d_map);
@@ -408,6 +433,7 @@ DopplerArgs doppler_args(const ofdm_radar_plan* pl, int frames) {
   a.wl = pl->d_wl;
   a.tw = pl->twM;
   a.map_off = nullptr;
+  a.frame_mask = nullptr;
   return a;
 }
 
@@ -423,6 +449,7 @@ DetectArgs detect_args(const ofdm_radar_plan* pl, int frames, int compact) {
   a.full = pl->full;
   a.compact = compact;
   a.out_idx = nullptr;
+  a.frame_mask = nullptr;
   a.frame_stride = compact ? (long)pl->rows * pl->Mp : (long)pl->Np * pl->Mp;
   a.frames = frames;
   a.mode = p.detect_mode;
@@ -942,6 +969,109 @@ int ofdm_radar_batch_process(ofdm_radar_batch* b, const ofdm_c32* Yc, const ofdm
   b->used_graph = false;
   e = launch_all(s);
   return e == cudaSuccess ? OFDM_OK : cuda_fail(e);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- learned proposal
+extern "C" {
+
+int ofdm_radar_learned_prepare(ofdm_radar_plan* pl) {
+  if (!pl) return OFDM_ERR_INVALID_ARG;
+  const ofdm_radar_params& p = pl->p;
+  if (!(p.M == 256 || p.M == 512 || p.M == 1024) || pl->Mp != p.M || pl->full) return OFDM_ERR_UNSUPPORTED_SIZE;
+  if (pl->d_cpow) return OFDM_OK;
+  pl->Mc = p.M / 4;
+  pl->Hc = (pl->rows + 3) / 4;
+  const size_t cells = (size_t)p.max_frames * pl->Hc * pl->Mc;
+  std::vector<float2> tw;
+  build_twiddles(tw, pl->Mc, pl->Mc / 32);
+  std::vector<float> w4(pl->Mc);
+  for (int l = 0; l < pl->Mc; ++l) {
+    const double c = cos(2.0 * M_PI * l / pl->Mc);
+    w4[l] = p.window == OFDM_WINDOW_HANN ? (float)(0.5 - 0.5 * c)
+          : p.window == OFDM_WINDOW_HAMMING ? (float)(0.54 - 0.46 * c) : 1.f;
+  }
+  cudaError_t e = dalloc(&pl->d_cpow, cells);
+  if (e == cudaSuccess) e = dalloc(&pl->d_cx, cells);
+  if (e == cudaSuccess) e = dalloc(&pl->d_a1, 16 * cells);
+  if (e == cudaSuccess) e = dalloc(&pl->d_a2, 16 * cells);
+  if (e == cudaSuccess) e = dalloc(&pl->d_logit, cells);
+  if (e == cudaSuccess) e = dalloc(&pl->d_w4, (size_t)pl->Mc);
+  if (e == cudaSuccess) e = dalloc(&pl->d_twMc, tw.size());
+  if (e == cudaSuccess) e = dalloc(&pl->d_mask, (size_t)p.max_frames);
+  if (e == cudaSuccess) e = cudaMemcpy(pl->d_w4, w4.data(), w4.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(pl->d_twMc, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? OFDM_ERR_NO_MEMORY : cuda_fail(e);
+  }
+  return OFDM_OK;
+}
+
+int ofdm_radar_coarse_shape(const ofdm_radar_plan* pl, int32_t* h, int32_t* w) {
+  if (!pl || !pl->d_cpow) return OFDM_ERR_INVALID_ARG;
+  if (h) *h = pl->Hc;
+  if (w) *w = pl->Mc;
+  return OFDM_OK;
+}
+
+int ofdm_radar_coarse_map(ofdm_radar_plan* pl, const ofdm_c32* Y, const ofdm_c32* X, int32_t frames, float* x_out,
+                          void* stream) {
+  if (!pl || !Y || !X || !pl->d_cpow || bad_frames(pl, frames)) return OFDM_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int launches = 0;
+  unsigned long long tk = 0;
+  cudaError_t e = ofdm::launch_column(pl->p.N, (const float2*)Y, (const float2*)X, pl->d_strip, pl->d_wstatus,
+                                      column_args(pl, frames), s, &launches, &tk);
+  pl->ctr_base[pl->ctr_slot] += tk;
+  if (e == cudaSuccess)
+    e = ofdm::launch_coarse(pl->d_strip, pl->d_cpow, x_out ? x_out : pl->d_cx, pl->rows, pl->p.M, frames, pl->d_w4,
+                            pl->d_twMc, s, &launches);
+  // status words of this call are not reported
+  if (e == cudaSuccess) e = cudaMemsetAsync(pl->d_wstatus, 0, (size_t)frames * sizeof(uint32_t), s);
+  return finish(pl, launches, e);
+}
+
+int ofdm_radar_process_learned(ofdm_radar_plan* pl, const float* theta, const ofdm_c32* Y, const ofdm_c32* X,
+                               int32_t frames, float zthr, int32_t cap, ofdm_target* out, int32_t* nt,
+                               uint32_t* st, void* stream) {
+  if (!pl || !theta || !Y || !X || !pl->d_cpow || bad_frames(pl, frames) || cap < 1 || cap > 256)
+    return OFDM_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int launches = 0;
+  unsigned long long tk = 0;
+  cudaError_t e = ofdm::launch_column(pl->p.N, (const float2*)Y, (const float2*)X, pl->d_strip, pl->d_wstatus,
+                                      column_args(pl, frames), s, &launches, &tk);
+  pl->ctr_base[pl->ctr_slot] += tk;
+  if (e == cudaSuccess)
+    e = ofdm::launch_coarse(pl->d_strip, pl->d_cpow, pl->d_cx, pl->rows, pl->p.M, frames, pl->d_w4, pl->d_twMc, s,
+                            &launches);
+  if (e == cudaSuccess) {
+    e = ofdm::cnn_forward(theta, 1, pl->d_cx, frames, pl->Hc, pl->Mc, pl->d_a1, pl->d_a2, pl->d_logit, s);
+    launches += 3;
+  }
+  if (e != cudaSuccess) return finish(pl, launches, e);
+  ofdm::RefineArgs ra;
+  const DetectArgs da = detect_args(pl, frames, 1);
+  ra.N = pl->p.N; ra.M = pl->p.M; ra.rows = pl->rows; ra.row0 = pl->row0; ra.Hc = pl->Hc; ra.Mc = pl->Mc;
+  ra.frames = frames; ra.K = pl->p.max_targets; ra.cap = cap; ra.zthr = zthr;
+  ra.inv_nm = (float)(1.0 / ((double)pl->p.N * pl->p.M));
+  ra.dd = da.dd; ra.dv = da.dv; ra.wl = pl->d_wl;
+  e = ofdm::launch_refine(pl->d_strip, pl->d_logit, out, nt, st, pl->d_wstatus, pl->d_mask, ra, s, &launches);
+  // fallback: the full Doppler stage and detection on the flagged frames only
+  if (e == cudaSuccess) {
+    DopplerArgs dop = doppler_args(pl, frames);
+    dop.frame_mask = pl->d_mask;
+    e = ofdm::launch_doppler(pl->Mp, pl->d_strip, nullptr, pl->d_pow, dop, s, &launches);
+  }
+  if (e == cudaSuccess) {
+    DetectArgs det = detect_args(pl, frames, 1);
+    det.frame_mask = pl->d_mask;
+    e = ofdm::launch_detect(pl->d_pow, out, nt, st, pl->d_wstatus, det, s, &launches);
+  }
+  if (e == cudaSuccess) e = mark_fallback(pl->d_mask, st, frames, s);
+  return finish(pl, launches, e);
 }
 
 }  // extern "C"

@@ -102,6 +102,20 @@ def _load():
     lib.ofdm_radar_batch_used_graph.restype = ctypes.c_int
     lib.ofdm_radar_batch_destroy.argtypes = [vp]
     lib.ofdm_radar_batch_destroy.restype = None
+    f32 = ctypes.c_float
+    lib.ofdm_radar_learned_prepare.argtypes = [vp]
+    lib.ofdm_radar_coarse_shape.argtypes = [vp, vp, vp]
+    lib.ofdm_radar_coarse_map.argtypes = [vp, vp, vp, i32, vp, vp]
+    lib.ofdm_radar_process_learned.argtypes = [vp, vp, vp, vp, i32, f32, i32, vp, vp, vp, vp]
+    lib.ofdm_cnn_param_count.argtypes = []
+    lib.ofdm_cnn_forward.argtypes = [vp, i32, vp, i32, i32, i32, vp, vp, vp, vp]
+    lib.ofdm_cnn_backward.argtypes = [vp, i32, vp, vp, vp, vp, i32, i32, i32, vp, vp, vp, vp]
+    lib.ofdm_cnn_bce.argtypes = [vp, vp, i32, f32, vp, vp, vp]
+    lib.ofdm_cnn_adam.argtypes = [vp, vp, vp, vp, i32, i32, f32, f32, f32, f32, vp]
+    for name in ("ofdm_radar_learned_prepare", "ofdm_radar_coarse_shape", "ofdm_radar_coarse_map",
+                 "ofdm_radar_process_learned", "ofdm_cnn_param_count", "ofdm_cnn_forward",
+                 "ofdm_cnn_backward", "ofdm_cnn_bce", "ofdm_cnn_adam"):
+        getattr(lib, name).restype = ctypes.c_int
     lib.ofdm_radar_strerror.argtypes = [ctypes.c_int]
     lib.ofdm_radar_strerror.restype = ctypes.c_char_p
     for name in ("ofdm_radar_plan_create", "ofdm_radar_support_rows", "ofdm_radar_process",
@@ -340,3 +354,54 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------- learned proposal
+STATUS_FALLBACK = 16
+
+
+def ofdm_radar_learned_prepare(plan: Plan):
+    _check(_lib.ofdm_radar_learned_prepare(plan.handle), "ofdm_radar_learned_prepare")
+    h, w = ctypes.c_int32(), ctypes.c_int32()
+    _check(_lib.ofdm_radar_coarse_shape(plan.handle, ctypes.byref(h), ctypes.byref(w)),
+           "ofdm_radar_coarse_shape")
+    return h.value, w.value
+
+
+def ofdm_radar_coarse_map(plan: Plan, Y, X, frames, x_out=None, stream=None):
+    return _check(_lib.ofdm_radar_coarse_map(plan.handle, _ptr(Y), _ptr(X), frames, _ptr(x_out),
+                                             _stream(stream)), "ofdm_radar_coarse_map")
+
+
+def ofdm_radar_process_learned(plan: Plan, theta, Y, X, frames, logit_threshold, max_candidates,
+                               out_targets=None, n_targets=None, status=None, stream=None):
+    return _check(_lib.ofdm_radar_process_learned(plan.handle, _ptr(theta), _ptr(Y), _ptr(X), frames,
+                                                  float(logit_threshold), int(max_candidates),
+                                                  _ptr(out_targets), _ptr(n_targets), _ptr(status),
+                                                  _stream(stream)), "ofdm_radar_process_learned")
+
+
+def ofdm_cnn_param_count():
+    return _lib.ofdm_cnn_param_count()
+
+
+def ofdm_cnn_forward(theta, bf16, x, B, H, W, a1, a2, logits, stream=None):
+    return _check(_lib.ofdm_cnn_forward(_ptr(theta), int(bf16), _ptr(x), B, H, W, _ptr(a1), _ptr(a2),
+                                        _ptr(logits), _stream(stream)), "ofdm_cnn_forward")
+
+
+def ofdm_cnn_backward(theta, bf16, x, a1, a2, glogits, B, H, W, ga1, ga2, gtheta, stream=None):
+    return _check(_lib.ofdm_cnn_backward(_ptr(theta), int(bf16), _ptr(x), _ptr(a1), _ptr(a2), _ptr(glogits),
+                                         B, H, W, _ptr(ga1), _ptr(ga2), _ptr(gtheta), _stream(stream)),
+                  "ofdm_cnn_backward")
+
+
+def ofdm_cnn_bce(logits, labels, n, pos_weight, loss, glogits, stream=None):
+    return _check(_lib.ofdm_cnn_bce(_ptr(logits), _ptr(labels), n, float(pos_weight), _ptr(loss),
+                                    _ptr(glogits), _stream(stream)), "ofdm_cnn_bce")
+
+
+def ofdm_cnn_adam(theta, grad, m, v, n, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    return _check(_lib.ofdm_cnn_adam(_ptr(theta), _ptr(grad), _ptr(m), _ptr(v), n, step, float(lr),
+                                     float(beta1), float(beta2), float(eps), _stream(stream)),
+                  "ofdm_cnn_adam")

@@ -418,3 +418,53 @@ def test_fps_pin_catches_wrong_peeling_sign(monkeypatch):
     monkeypatch.setattr(o.np, "exp", bad_exp)
     with pytest.raises(AssertionError):
         check_fps_exact(1, 64, 64, 8)
+
+
+# ---------------------------------------------------------------- learned proposal: the CNN
+def _conv_loops(x, w, b):
+    B, Ci, H, W = x.shape
+    Co = w.shape[0]
+    y = np.zeros((B, Co, H, W))
+    for bb in range(B):
+        for o_ in range(Co):
+            for i in range(H):
+                for j in range(W):
+                    acc = b[o_]
+                    for c in range(Ci):
+                        for dy in range(3):
+                            for dx in range(3):
+                                ii, jj = i + dy - 1, j + dx - 1
+                                if 0 <= ii < H and 0 <= jj < W:
+                                    acc += w[o_, c, dy, dx] * x[bb, c, ii, jj]
+                    y[bb, o_, i, j] = acc
+    return y
+
+
+def test_conv3x3_matches_loops():
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal((2, 3, 5, 6))
+    w = rng.standard_normal((4, 3, 3, 3))
+    b = rng.standard_normal(4)
+    assert np.allclose(o.conv3x3(x, w, b), _conv_loops(x, w, b))
+
+
+def test_cnn_gradient_matches_finite_differences():
+    rng = np.random.default_rng(1)
+    theta = 0.3 * rng.standard_normal(o.cnn_n_params())
+    x = rng.standard_normal((2, 1, 6, 7))
+    y = (rng.random((2, 1, 6, 7)) < 0.2).astype(float)
+
+    def loss(t):
+        z, _ = o.cnn_forward(x, t)
+        return o.bce_logits(z, y, 4.0)[0]
+
+    z, saved = o.cnn_forward(x, theta)
+    _, gz = o.bce_logits(z, y, 4.0)
+    g = o.cnn_backward(saved, theta, gz)
+    idx = rng.choice(theta.size, 60, replace=False)
+    h = 1e-6
+    for i in idx:
+        e = np.zeros_like(theta)
+        e[i] = h
+        fd = (loss(theta + e) - loss(theta - e)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), i
