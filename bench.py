@@ -98,7 +98,7 @@ class Clocks:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -336,6 +336,88 @@ def extra_fps(radar, torch, dev, stream, steps, n_frames=32):
             "bins_agree_frames": f"{agree}/{n_frames}"}
 
 
+def _hits(tv, nt, truth, M):
+    h = 0
+    for f, (rho, nu, _b, _snr) in enumerate(truth):
+        got = [(int(t["r"]), int(t["s"])) for t in tv[f][:int(nt[f])]]
+        for a, b in zip(rho, nu):
+            h += any(abs(r - a) <= 1.0 and abs(((s - b) + M // 2) % M - M // 2) <= 1.0 for r, s in got)
+    return h
+
+
+def extra_learned(radar, torch, dev, stream, steps, train_steps=150, n_eval=16):
+    """The learned form on the largest workload (4096 x 1024, L_cp 512, 32
+    off-grid targets, SNR U[-15, 5] dB): the CNN is trained here on frames
+    generated on the device (the library's own forward/backward/Adam
+    kernels), its threshold set on separate validation frames, then the
+    learned chain and the plain chain (no map: the same outputs) are timed on
+    16 fresh frames and scored against the ground truth."""
+    from paper_2209_03883_gb300.learned import Trainer, coarse_labels
+    cfg = syn.CONFIGS[5]
+    N, M, L = cfg.N, cfg.M, cfg.L_cp
+    B = 4
+    tplan = radar.Plan(N=N, M=M, L_cp=L, max_frames=B, max_targets=cfg.detect_k)
+    tr = Trainer(tplan, torch, dev, seed=5)
+    rows = tplan.support_rows()
+
+    def precode_with(plan):
+        def f(A):
+            out = torch.empty_like(A)
+            radar.ofdm_zc_precode(plan, A, out, A.shape[0])
+            return out
+        return f
+
+    t0 = time.perf_counter()
+    for step in range(train_steps):
+        Y, A, truth = syn.draw_frames_torch(cfg, [5 * 1000 + 100 + B * step + i for i in range(B)], dev,
+                                            precode_with(tplan))
+        loss = tr.train_step(Y, A, coarse_labels(truth, N, M, len(rows), rows[0], tr.Hc, tr.Mc))
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    # threshold: the 64th largest logit per validation frame, averaged
+    Yv, Av, _ = syn.draw_frames_torch(cfg, [5 * 1000 + 50 + i for i in range(B)], dev, precode_with(tplan))
+    z = tr.logits(Yv, Av).reshape(B, -1)
+    thr = float(torch.topk(z, 64, dim=1).values[:, -1].mean())
+
+    plan = radar.Plan(N=N, M=M, L_cp=L, max_frames=n_eval, max_targets=cfg.detect_k)
+    radar.ofdm_radar_learned_prepare(plan)
+    Y, A, truth = syn.draw_frames_torch(cfg, [syn.seed_for(5, f) for f in range(n_eval)], dev, precode_with(plan))
+    po = radar.alloc_outputs(plan, n_eval, dev, with_map=False)
+    lo = radar.alloc_outputs(plan, n_eval, dev, with_map=False)
+
+    def t_of(fn):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    ms_p = t_of(lambda: radar.ofdm_radar_process(plan, Y, A, n_eval, None, po["targets"], po["n_targets"],
+                                                   po["status"], stream))
+    ms_l = t_of(lambda: radar.ofdm_radar_process_learned(plan, tr.theta, Y, A, n_eval, thr, 256, lo["targets"],
+                                                           lo["n_targets"], lo["status"], stream))
+    K = cfg.detect_k
+    hp = _hits(radar.targets_view(po["targets"], n_eval, K), po["n_targets"].cpu().numpy(), truth, M)
+    hl = _hits(radar.targets_view(lo["targets"], n_eval, K), lo["n_targets"].cpu().numpy(), truth, M)
+    fb = int(((lo["status"].cpu().numpy().view(np.uint32) & radar.STATUS_FALLBACK) != 0).sum())
+    out = {"workload": "16 frames 4096x1024, L_cp 512, 32 off-grid targets, SNR U[-15,5] dB",
+           "plain_no_map": {"value": n_eval / (ms_p / 1e3), "unit": "frames/s", "ms_per_step": ms_p,
+                            "target_hits": f"{hp}/{32 * n_eval}"},
+           "learned": {"value": n_eval / (ms_l / 1e3), "unit": "frames/s", "ms_per_step": ms_l,
+                       "target_hits": f"{hl}/{32 * n_eval}", "fallback_frames": fb, "logit_threshold": thr},
+           "gain": ms_p / ms_l,
+           "training": {"steps": train_steps, "frames_per_step": B, "seconds": train_s,
+                        "final_loss": float(loss)}}
+    plan.close()
+    tplan.close()
+    return out
+
+
 def run_ours(args):
     import torch
     rank, world, local, dist = dist_setup(args.gpus)
@@ -374,6 +456,13 @@ def run_ours(args):
     # ---- timed region: K steps, CUDA events on the launching stream
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with Clocks(local) as clk:
+        # about a second of the same steps first, so that the clock sampler
+        # sees the GPU under this load (the timed region itself is short)
+        t_soak = time.perf_counter()
+        while time.perf_counter() - t_soak < 1.0:
+            for _ in range(20):
+                step()
+            torch.cuda.synchronize()
         barrier_sync(dist, torch)
         e0.record(stream)
         for _ in range(args.steps):
@@ -453,13 +542,19 @@ def run_ours(args):
     if not args.no_extra:
         extra = {}
         try:
-            extra["batched_uneven"] = extra_batched(radar, torch, dev, stream, max(3, min(args.steps, 10)))
+            bs = torch.cuda.Stream(device=dev)  # a graph needs a capturable (non-legacy) stream
+            with torch.cuda.stream(bs):
+                extra["batched_uneven"] = extra_batched(radar, torch, dev, bs, max(3, min(args.steps, 10)))
         except Exception as exc:  # report, never hide, a failing secondary measurement
             extra["batched_uneven"] = {"error": str(exc)}
         try:
             extra["sparse_fps_vs_periodogram"] = extra_fps(radar, torch, dev, stream, max(3, min(args.steps, 10)))
         except Exception as exc:
             extra["sparse_fps_vs_periodogram"] = {"error": str(exc)}
+        try:
+            extra["learned_vs_plain"] = extra_learned(radar, torch, dev, stream, max(3, min(args.steps, 10)))
+        except Exception as exc:
+            extra["learned_vs_plain"] = {"error": str(exc)}
         line["extra"] = extra
     if rank == 0 and args.gpus == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline()

@@ -304,7 +304,7 @@ int ofdm_radar_timing_read(ofdm_radar_plan* plan, float* total_ms, int32_t* laun
  * allocator it does not own, in a memory-capped process, or with all device
  * memory committed up front -- so cannot create a plan.  Takes the parameters
  * directly (max_frames is ignored) and keeps tables and workspace in one
- * fixed array compiled into the library (about 12.6 MB, held on every device
+ * fixed array compiled into the library (about 14.1 MB, held on every device
  * that loads the library until the process exits).  Same inputs, outputs,
  * layouts and results as ofdm_radar_process on device buffers.
  * Limits: frames <= 4096 and frames * support_rows * max(M, M') <= 2^20

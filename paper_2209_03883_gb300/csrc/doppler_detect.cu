@@ -88,17 +88,25 @@ __global__ void zero_rows_kernel(float* __restrict__ map, int frames, long frame
 }
 
 // ---------------------------------------------------------------- detection
-constexpr int kDetThreads = 512;
-constexpr int kCandCap = 2048;          // candidate keys kept in shared memory
-constexpr int kBitWords = 16384;        // candidate bit-mask words (64 KB): frames up to 2^19 cells
-constexpr int kTileFloats = 24576;      // row tile incl. halo rows (96 KB)
+// detect_band_kernel: grid (bands, frames).  Each CTA stages its band of
+// scanned rows plus one halo row on each side in shared memory, finds the
+// 8-neighbour local maxima (circular in r and s; equal powers broken by the
+// smaller map index) and keeps its K strongest as keys
+//   (float bits of P) << 32 | ~(flat map index)
+// (descending key order = power descending, then index ascending).  The last
+// CTA of a frame (atomic ticket, no waiting) merges the bands' keys, writes
+// the targets and status, and resets the frame's ticket and counter.
+// median_kernel: threshold mode without a given noise level -- the lower
+// median of P over the scanned rows (radix select on the float bits).
+constexpr int kDetThreads = 256;
+constexpr int kBandCap = 1024;          // keys kept per band before compaction
 
 __device__ __forceinline__ float det_value(const float* base, const DetectArgs& a, int ri, int c) {
   const int row = a.compact ? ri : ((a.row0 + ri) & (a.Np - 1));
   return base[((long)row << a.logMp) + c];
 }
 
-// Block-wide bitonic sort of buf[0..n) (n a power of two <= kCandCap), keys descending.
+// Block-wide bitonic sort of buf[0..n) (n a power of two), keys descending.
 __device__ void bitonic_desc(uint64_t* buf, int n) {
   for (int k = 2; k <= n; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
@@ -115,40 +123,57 @@ __device__ void bitonic_desc(uint64_t* buf, int n) {
   }
 }
 
-// Key of a detection candidate, else 0.  The cell sits at tile row i
-// (1 <= i <= tile rows; rows 0 and tr + 1 are the halo) and column c of a
-// shared-memory tile whose first interior row is scanned row t0.  A
-// candidate is an 8-neighbour local maximum (circular in r and s) with
-// P > 0 and, in threshold mode, P >= eta.  Key = (float bits of P) << 32 |
-// ~(flat map index): descending key order is power descending, then map
-// index ascending.
-__device__ __forceinline__ uint64_t tile_key(const float* tile, const DetectArgs& a, int t0, int i, int c,
+// Key of the cell at tile row i (1..tr) and column c, or 0.  Fast path: float
+// comparisons with the eight neighbours; the map-index tie-break runs only
+// when a neighbour has exactly the same power.
+__device__ __forceinline__ uint64_t band_key(const float* tile, const DetectArgs& a, int t0, int i, int c,
                                              float eta) {
   const float p = tile[(i << a.logMp) + c];
   if (!(p > 0.f) || (a.mode == OFDM_DETECT_THRESHOLD && !(p >= eta))) return 0;
+  const int cm = (c - 1) & (a.Mp - 1), cp = (c + 1) & (a.Mp - 1);
+  const float* up = tile + ((i - 1) << a.logMp);
+  const float* mid = tile + (i << a.logMp);
+  const float* dn = tile + ((i + 1) << a.logMp);
+  const float n0 = up[cm], n1 = up[c], n2 = up[cp], n3 = mid[cm], n4 = mid[cp], n5 = dn[cm], n6 = dn[c],
+              n7 = dn[cp];
+  const bool larger = (n0 > p) | (n1 > p) | (n2 > p) | (n3 > p) | (n4 > p) | (n5 > p) | (n6 > p) | (n7 > p);
+  if (larger) return 0;
   const int r = (a.row0 + t0 + i - 1) & (a.Np - 1);
   const uint32_t idx = ((uint32_t)r << a.logMp) + c;
-  bool ok = true;
-#pragma unroll
-  for (int dr = -1; dr <= 1; ++dr) {
-    const int rn = (r + dr) & (a.Np - 1);
-#pragma unroll
-    for (int dc = -1; dc <= 1; ++dc) {
-      if (dr == 0 && dc == 0) continue;
-      const int cn = (c + dc) & (a.Mp - 1);
-      const uint32_t in_idx = ((uint32_t)rn << a.logMp) + cn;
-      const float pn = tile[((i + dr) << a.logMp) + cn];
-      ok &= (in_idx == idx) | (p > pn) | ((p == pn) & (idx < in_idx));
-    }
+  const bool equal = (n0 == p) | (n1 == p) | (n2 == p) | (n3 == p) | (n4 == p) | (n5 == p) | (n6 == p) | (n7 == p);
+  if (equal) {
+    const float nb[8] = {n0, n1, n2, n3, n4, n5, n6, n7};
+    const int dr[8] = {-1, -1, -1, 0, 0, 1, 1, 1}, dc[8] = {-1, 0, 1, -1, 1, -1, 0, 1};
+    for (int k = 0; k < 8; ++k)
+      if (nb[k] == p) {
+        const uint32_t in_idx = ((uint32_t)((r + dr[k]) & (a.Np - 1)) << a.logMp) + ((c + dc[k]) & (a.Mp - 1));
+        if (in_idx < idx) return 0;
+      }
   }
-  return ok ? ((uint64_t)__float_as_uint(p) << 32) | (uint64_t)(~idx) : 0;
+  return ((uint64_t)__float_as_uint(p) << 32) | (uint64_t)(~idx);
 }
 
-// Stage scanned rows t0 - 1 .. t0 + tr (one halo row each side) into the
-// tile.  Rows outside a partial support are zero; a full support wraps.
-__device__ __forceinline__ void load_tile(float* tile, const float* base, const DetectArgs& a, int t0, int tr) {
+__global__ void __launch_bounds__(kDetThreads)
+detect_band_kernel(const float* __restrict__ src, ofdm_target* __restrict__ out, int32_t* __restrict__ n_out,
+                   uint32_t* __restrict__ status, uint32_t* __restrict__ wstatus, DetectArgs a) {
+  extern __shared__ __align__(16) unsigned char det_smem[];
+  __shared__ uint64_t buf[kBandCap];
+  __shared__ uint32_t bits[8192 / 32 + 32];
+  __shared__ unsigned s_n, s_cnt;
+  __shared__ int s_last;
+  float* tile = reinterpret_cast<float*>(det_smem);
+  const int band = blockIdx.x, f = blockIdx.y;
+  if (a.frame_mask && !a.frame_mask[f]) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int K = a.K;
+  const int t0 = band * a.band_rows;
+  const int tr = min(a.band_rows, a.rows - t0);
+  const float* base = src + (long)f * a.frame_stride;
+  const float eta = a.mode == OFDM_DETECT_THRESHOLD ? (a.use_fixed_eta ? a.eta_fixed : a.eta[f]) : 0.f;
+
+  // stage rows t0 - 1 .. t0 + tr; rows outside a partial support are zero, a full support wraps
   const int n4 = ((tr + 2) << a.logMp) >> 2;
-  for (int v = threadIdx.x; v < n4; v += kDetThreads) {
+  for (int v = tid; v < n4; v += kDetThreads) {
     const int idx = v << 2;
     const int i = idx >> a.logMp, c = idx & (a.Mp - 1);
     int rj = t0 - 1 + i;
@@ -160,135 +185,73 @@ __device__ __forceinline__ void load_tile(float* tile, const float* base, const 
     }
     *reinterpret_cast<float4*>(tile + idx) = val;
   }
-}
+  if (tid == 0) { s_n = 0; s_cnt = 0; }
+  __syncthreads();
 
-__global__ void __launch_bounds__(kDetThreads)
-detect_kernel(const float* __restrict__ src, ofdm_target* __restrict__ out, int32_t* __restrict__ n_out,
-              uint32_t* __restrict__ status, uint32_t* __restrict__ wstatus, DetectArgs a) {
-  __shared__ uint64_t buf[kCandCap];
-  extern __shared__ __align__(16) float dyn[];   // row tile, then the candidate bit mask
-  float* tile = dyn;
-  uint32_t* bits = reinterpret_cast<uint32_t*>(dyn + ((a.tile_rows + 2) << a.logMp));
-  __shared__ uint32_t hist[256];
-  __shared__ uint32_t s_prefix, s_rank, s_n, s_total;
-  __shared__ uint64_t s_floor;
-  const int f = blockIdx.x;
-  if (a.frame_mask && !a.frame_mask[f]) return;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const float* base = src + (long)f * a.frame_stride;
-  const int n = a.rows << a.logMp;
-  const int K = a.K;
-  const bool use_bits = a.bit_words > 0;
-
-  float eta = 0.f;
-  if (a.mode == OFDM_DETECT_THRESHOLD) {
-    if (a.use_fixed_eta) {
-      eta = a.eta_fixed;
-    } else {
-      // Lower median (rank (n-1)/2) of P over the scanned rows: 8-bit
-      // MSB-first radix select on the float bits (P >= 0 sorts as uint).
-      if (tid == 0) { s_prefix = 0; s_rank = (uint32_t)(n - 1) / 2; }
-      uint32_t mask = 0;
-      for (int shift = 24; shift >= 0; shift -= 8) {
-        for (int i = tid; i < 256; i += kDetThreads) hist[i] = 0;
-        __syncthreads();
-        const uint32_t prefix = s_prefix;
-        for (int e = tid; e < n; e += kDetThreads) {
-          const uint32_t u = __float_as_uint(det_value(base, a, e >> a.logMp, e & (a.Mp - 1)));
-          if ((u & mask) == prefix) atomicAdd(&hist[(u >> shift) & 255u], 1u);
-        }
-        __syncthreads();
-        if (tid == 0) {
-          uint32_t rank = s_rank, d = 0;
-          for (; d < 255; ++d) {
-            if (hist[d] > rank) break;
-            rank -= hist[d];
-          }
-          s_rank = rank;
-          s_prefix = prefix | (d << shift);
-        }
-        mask |= 255u << shift;
-        __syncthreads();
-      }
-      eta = __fmul_rn(__uint_as_float(s_prefix), a.eta_factor);
-    }
-  }
-
-  // Scan 1 over row tiles: candidate bits, candidate count and each
-  // thread's best key.
+  // scan 1: candidate bits, count, each thread's best key
+  const int nt = tr << a.logMp;
   uint64_t best = 0;
-  uint32_t cnt = 0;
-  for (int t0 = 0; t0 < a.rows; t0 += a.tile_rows) {
-    const int tr = min(a.tile_rows, a.rows - t0);
-    __syncthreads();
-    load_tile(tile, base, a, t0, tr);
-    __syncthreads();
-    const int nt = tr << a.logMp;
-    for (int e0 = 0; e0 < nt; e0 += kDetThreads) {
-      const int e = e0 + tid;
-      const uint64_t key = e < nt ? tile_key(tile, a, t0, 1 + (e >> a.logMp), e & (a.Mp - 1), eta) : 0;
-      const unsigned m = __ballot_sync(0xffffffffu, key != 0);
-      const int word = (((t0 << a.logMp) + e0) >> 5) + warp;
-      if (use_bits && lane == 0 && word < a.bit_words) bits[word] = m;
-      cnt += key ? 1u : 0u;
-      best = key > best ? key : best;
-    }
+  unsigned cnt = 0;
+  for (int e0 = 0; e0 < nt; e0 += kDetThreads) {
+    const int e = e0 + tid;
+    const uint64_t key = e < nt ? band_key(tile, a, t0, 1 + (e >> a.logMp), e & (a.Mp - 1), eta) : 0;
+    const unsigned m = __ballot_sync(0xffffffffu, key != 0);
+    if (lane == 0) bits[(e0 >> 5) + warp] = m;
+    cnt += key ? 1u : 0u;
+    best = key > best ? key : best;
   }
-  buf[tid] = best;
-  for (int i = kDetThreads + tid; i < kCandCap; i += kDetThreads) buf[i] = 0;
   cnt = __reduce_add_sync(0xffffffffu, cnt);
-  if (tid == 0) { s_total = 0; s_n = 0; }
+  if (lane == 0) atomicAdd(&s_cnt, cnt);
+  buf[tid] = best;
   __syncthreads();
-  if (lane == 0) atomicAdd(&s_total, cnt);
-  // Floor: the K-th best of the per-thread best keys (each a distinct
-  // candidate), so at least K candidates lie at or above it.
-  bitonic_desc(buf, kDetThreads);
-  if (tid == 0) s_floor = buf[K - 1];
+  bitonic_desc(buf, kDetThreads);      // the K-th best per-thread key is a floor for the band's top K
+  const uint64_t floor_key = buf[K - 1];
   __syncthreads();
-  const uint64_t floor_key = s_floor;
-  for (int i = tid; i < kCandCap; i += kDetThreads) buf[i] = 0;
+  for (int i = tid; i < kBandCap; i += kDetThreads) buf[i] = 0;
   __syncthreads();
-
-  // Scan 2: keys >= floor into the buffer (compacted to the best K if full).
-  for (int t0 = 0; t0 < a.rows; t0 += a.tile_rows) {
-    const int tr = min(a.tile_rows, a.rows - t0);
-    __syncthreads();
-    load_tile(tile, base, a, t0, tr);
-    __syncthreads();
-    const int nt = tr << a.logMp;
-    for (int e0 = 0; e0 < nt; e0 += kDetThreads) {
-      const int e = e0 + tid;
-      uint64_t key = 0;
-      if (e < nt) {
-        const int ge = (t0 << a.logMp) + e;
-        const bool cand = use_bits ? ((bits[ge >> 5] >> (ge & 31)) & 1u) : true;
-        if (cand) key = tile_key(tile, a, t0, 1 + (e >> a.logMp), e & (a.Mp - 1), eta);
-      }
-      const bool keep = key != 0 && key >= floor_key;
-      const unsigned km = __ballot_sync(0xffffffffu, keep);
-      if (km) {
-        uint32_t wbase = 0;
-        if (lane == 0) wbase = atomicAdd(&s_n, (uint32_t)__popc(km));
-        wbase = __shfl_sync(0xffffffffu, wbase, 0);
-        if (keep) buf[wbase + __popc(km & ((1u << lane) - 1u))] = key;
-      }
-      __syncthreads();
-      const uint32_t nn = s_n;  // every thread takes the same decision below
-      __syncthreads();
-      if (nn > (uint32_t)(kCandCap - kDetThreads)) {
-        bitonic_desc(buf, kCandCap);
-        for (int i = K + tid; i < kCandCap; i += kDetThreads) buf[i] = 0;
-        if (tid == 0) s_n = K;
-        __syncthreads();
-      }
+  // scan 2: keys >= floor (only cells with their candidate bit set)
+  for (int e0 = 0; e0 < nt; e0 += kDetThreads) {
+    const int e = e0 + tid;
+    uint64_t key = 0;
+    if (e < nt && ((bits[e >> 5] >> (e & 31)) & 1u))
+      key = band_key(tile, a, t0, 1 + (e >> a.logMp), e & (a.Mp - 1), eta);
+    const bool keep = key != 0 && key >= floor_key;
+    const unsigned km = __ballot_sync(0xffffffffu, keep);
+    if (km) {
+      unsigned wb = 0;
+      if (lane == 0) wb = atomicAdd(&s_n, (unsigned)__popc(km));
+      wb = __shfl_sync(0xffffffffu, wb, 0);
+      const unsigned pos = wb + __popc(km & ((1u << lane) - 1u));
+      if (keep && pos < kBandCap) buf[pos] = key;
     }
   }
-  int sort_n = 32;
-  while (sort_n < (int)s_n) sort_n <<= 1;
+  __syncthreads();
+  // At most K threads have a best key at or above the floor and each scans at
+  // most 8192 / kDetThreads = 32 cells, so s_n <= 32 K <= kBandCap.
+  int sn = min((int)s_n, kBandCap), sort_n = 32;
+  while (sort_n < sn) sort_n <<= 1;
   bitonic_desc(buf, sort_n);
+  uint64_t* pk = a.part_keys + ((long)f * a.bands + band) * 32;
+  if (tid < 32) pk[tid] = tid < K ? buf[tid] : 0;
+  if (tid == 0) atomicAdd(a.counts + f, s_cnt);
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_last = atomicAdd(a.tickets + f, 1u) == (unsigned)(a.bands - 1);
+  __syncthreads();
+  if (!s_last) return;
 
+  // last CTA of the frame: merge the bands
+  __threadfence();
+  uint64_t* mbuf = reinterpret_cast<uint64_t*>(det_smem);
+  const int nk = a.bands * 32;
+  int mn = 32;
+  while (mn < nk) mn <<= 1;
+  const volatile uint64_t* all = a.part_keys + (long)f * a.bands * 32;
+  for (int i = tid; i < mn; i += kDetThreads) mbuf[i] = i < nk ? all[i] : 0;
+  __syncthreads();
+  bitonic_desc(mbuf, mn);
   if (tid < 32) {
-    const uint64_t key = lane < K ? buf[lane] : 0;
+    const uint64_t key = lane < K ? mbuf[lane] : 0;
     const bool valid = key != 0;
     const int nv = __popc(__ballot_sync(0xffffffffu, valid));
     const long g = a.out_idx ? (long)a.out_idx[f] : (long)f;  // index into the caller's outputs
@@ -303,15 +266,49 @@ detect_kernel(const float* __restrict__ src, ofdm_target* __restrict__ out, int3
       out[g * K + lane] = tg;
     }
     if (lane == 0) {
-      const uint32_t total = s_total;
+      const unsigned total = atomicExch(a.counts + f, 0u);
       uint32_t st = wstatus ? wstatus[f] : 0u;
-      if (a.mode == OFDM_DETECT_TOPK && total < (uint32_t)K) st |= OFDM_STATUS_FEW_PEAKS;
-      if (a.mode == OFDM_DETECT_THRESHOLD && total > (uint32_t)K) st |= OFDM_STATUS_OVERFLOW;
+      if (a.mode == OFDM_DETECT_TOPK && total < (unsigned)K) st |= OFDM_STATUS_FEW_PEAKS;
+      if (a.mode == OFDM_DETECT_THRESHOLD && total > (unsigned)K) st |= OFDM_STATUS_OVERFLOW;
       if (status) status[g] = st;
       if (n_out) n_out[g] = nv;
       if (wstatus) wstatus[f] = 0u;  // ready for the next call
+      a.tickets[f] = 0u;
     }
   }
+}
+
+__global__ void __launch_bounds__(1024) median_kernel(const float* __restrict__ src, DetectArgs a) {
+  __shared__ uint32_t hist[256];
+  __shared__ uint32_t s_prefix, s_rank;
+  const int f = blockIdx.x, tid = threadIdx.x;
+  if (a.frame_mask && !a.frame_mask[f]) return;
+  const float* base = src + (long)f * a.frame_stride;
+  const int n = a.rows << a.logMp;
+  if (tid == 0) { s_prefix = 0; s_rank = (uint32_t)(n - 1) / 2; }
+  uint32_t mask = 0;
+  for (int shift = 24; shift >= 0; shift -= 8) {
+    for (int i = tid; i < 256; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    const uint32_t prefix = s_prefix;
+    for (int e = tid; e < n; e += blockDim.x) {
+      const uint32_t u = __float_as_uint(det_value(base, a, e >> a.logMp, e & (a.Mp - 1)));
+      if ((u & mask) == prefix) atomicAdd(&hist[(u >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      uint32_t rank = s_rank, d = 0;
+      for (; d < 255; ++d) {
+        if (hist[d] > rank) break;
+        rank -= hist[d];
+      }
+      s_rank = rank;
+      s_prefix = prefix | (d << shift);
+    }
+    mask |= 255u << shift;
+    __syncthreads();
+  }
+  if (tid == 0) a.eta[f] = __fmul_rn(__uint_as_float(s_prefix), a.eta_factor);
 }
 
 // ---------------------------------------------------------------- launchers
@@ -359,22 +356,20 @@ cudaError_t launch_zero_rows(float* map, int frames, int Np, int Mp, int z0, int
 
 cudaError_t launch_detect(const float* pow, ofdm_target* out, int32_t* n_out, uint32_t* status,
                           uint32_t* wstatus, const DetectArgs& a_in, cudaStream_t s, int* launches) {
-  ++*launches;
   DetectArgs a = a_in;
-  const long n = (long)a.rows * a.Mp;
-  const long words = (n + 31) / 32;
-  a.bit_words = words <= kBitWords ? (int)words : 0;  // too large: scan 2 re-tests every cell
-  // Row tiles of at most kTileFloats floats including the two halo rows; the
-  // tile rows times M' stay a multiple of 32 so that ballot words align.
-  int tr = kTileFloats / a.Mp - 2;
-  if (a.Mp < 32) tr &= ~1;
-  if (tr > a.rows) tr = a.rows;
-  a.tile_rows = tr;
-  const size_t smem = (size_t)(tr + 2) * a.Mp * sizeof(float) + (size_t)a.bit_words * sizeof(uint32_t);
-  cudaError_t e = cudaFuncSetAttribute(detect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)(kTileFloats * sizeof(float) + kBitWords * sizeof(uint32_t)));
+  detect_bands(a.rows, a.Mp, &a.band_rows, &a.bands);
+  if (a.mode == OFDM_DETECT_THRESHOLD && !a.use_fixed_eta) {
+    ++*launches;
+    median_kernel<<<a.frames, 1024, 0, s>>>(pow, a);
+  }
+  const size_t tile = (size_t)(a.band_rows + 2) * a.Mp * sizeof(float);
+  int mn = 32;
+  while (mn < a.bands * 32) mn <<= 1;
+  const size_t smem = tile > (size_t)mn * sizeof(uint64_t) ? tile : (size_t)mn * sizeof(uint64_t);
+  cudaError_t e = cudaFuncSetAttribute(detect_band_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  detect_kernel<<<a.frames, kDetThreads, smem, s>>>(pow, out, n_out, status, wstatus, a);
+  ++*launches;
+  detect_band_kernel<<<dim3(a.bands, a.frames), kDetThreads, smem, s>>>(pow, out, n_out, status, wstatus, a);
   return cudaGetLastError();
 }
 

@@ -61,7 +61,22 @@ struct DetectArgs {
   int use_fixed_eta;
   float eta_fixed, eta_factor;
   float dd, dv;                   // metres / (m/s) per bin, Eq. (19)
+  // workspace (zero-initialised tickets / counts; the last CTA of a frame resets them)
+  uint64_t* part_keys;            // [frames][bands][32] best keys of each band
+  unsigned* tickets;              // [frames]
+  unsigned* counts;               // [frames] candidates found
+  float* eta;                     // [frames] threshold from the median pre-pass
+  int bands, band_rows;           // set by detect_bands()
 };
+
+// Row bands of the detection grid: about 8192 cells per CTA.
+inline void detect_bands(int rows, int Mp, int* band_rows, int* bands) {
+  int br = 8192 / Mp;
+  if (br < 1) br = 1;
+  if (br > rows) br = rows;
+  *band_rows = br;
+  *bands = (rows + br - 1) / br;
+}
 
 // *tickets receives how far the launch advances a.work_ctr (symbols + warps
 // for the pipelined kernel, 0 otherwise); the caller adds it to work_base.
@@ -79,13 +94,14 @@ struct RefineArgs {
   int N, M, rows, row0, Hc, Mc, frames, K, cap;
   float zthr, inv_nm, dd, dv;
   const float* wl;
+  const float2* rootsM;   // exp(-2 pi i m / M), m < M
 };
 
 cudaError_t launch_coarse(const float2* strip, unsigned* cpow, float* x, int rows, int M, int frames,
                           const float* w4, const float2* tw, cudaStream_t s, int* launches);
 cudaError_t launch_refine(const float2* strip, const float* logits, ofdm_target* out, int32_t* n_out,
-                          uint32_t* status, uint32_t* wstatus, int* mask, const RefineArgs& a, cudaStream_t s,
-                          int* launches);
+                          uint32_t* status, uint32_t* wstatus, int* mask, int* cand, int* ncand, uint64_t* keys,
+                          const RefineArgs& a, cudaStream_t s, int* launches);
 
 cudaError_t cnn_forward(const float* th, int bf16, const float* x, int B, int H, int W, float* a1, float* a2,
                         float* z, cudaStream_t s);

@@ -6,20 +6,19 @@
 //   symbols), |.|^2, max-pooled 4x over range rows with atomicMax on the
 //   float bits (P >= 0 orders like unsigned).
 // coarse_norm_kernel: x = log(1 + C / mean_frame(C)) -- the CNN input.
-// refine_kernel: one CTA per frame: coarse cells whose logit exceeds the
-//   threshold become candidates; for each, the exact periodogram value
-//   (Eq. (17): full M-term Doppler sum of the strip, |.|^2 / (N M)) is
-//   computed on the 8 x 8 fine block around it, local maxima of the inner
-//   6 x 6 are collected and the strongest K distinct ones are reported.  A
-//   frame with more candidates than the cap is flagged for the full
-//   periodogram (the fallback and judge).
+// refine_select_kernel: coarse cells whose logit exceeds the threshold
+//   become candidates (ascending cell order); a frame with more than the cap
+//   is flagged for the full periodogram (the fallback and judge).
+// refine_cand_kernel: one CTA per (frame, candidate): the exact periodogram
+//   value (Eq. (17): full M-term Doppler sum of the strip, |.|^2 / (N M)) on
+//   the 8 x 8 fine block around the candidate, local maxima of its inner 6 x 6.
+// refine_merge_kernel: per frame, the strongest K distinct local maxima.
 #include "fft.cuh"
 #include "internal.h"
 
 namespace ofdm {
 
 constexpr int kRefThreads = 512;
-constexpr int kRefKeys = 2048;
 
 struct CoarseArgs {
   int rows, M, frames, Hc;
@@ -69,112 +68,143 @@ __global__ void coarse_norm_kernel(const unsigned* __restrict__ cpow, float* __r
     x[(long)f * cells + i] = log1pf(__uint_as_float(c[i]) * inv_mean);
 }
 
+// Candidate selection (one CTA per frame): coarse cells above the logit
+// threshold, in a fixed order (ascending cell index) so that the result does
+// not depend on thread timing; more than `cap` sends the frame to the fallback.
 __global__ void __launch_bounds__(kRefThreads)
-refine_kernel(const float2* __restrict__ strip, const float* __restrict__ logits, ofdm_target* __restrict__ out,
-              int32_t* __restrict__ n_out, uint32_t* __restrict__ status, uint32_t* __restrict__ wstatus,
-              int* __restrict__ mask, RefineArgs a) {
-  extern __shared__ __align__(16) unsigned char ref_smem[];
-  float2* tw = reinterpret_cast<float2*>(ref_smem);            // exp(-2 pi i m / M)
-  float2* rows8 = tw + a.M;                                    // 8 windowed strip rows
-  uint64_t* keys = reinterpret_cast<uint64_t*>(rows8 + 8 * a.M);
-  float* blk = reinterpret_cast<float*>(keys + kRefKeys);      // 8 x 8 block of P
-  int* cand = reinterpret_cast<int*>(blk + 64);
-  __shared__ int s_nc, s_nk;
-  const int f = blockIdx.x, tid = threadIdx.x;
+refine_select_kernel(const float* __restrict__ logits, int* __restrict__ cand, int* __restrict__ ncand,
+                     int* __restrict__ mask, RefineArgs a) {
+  __shared__ int s_n;
+  const int f = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
   const int cells = a.Hc * a.Mc;
   const float* z = logits + (long)f * cells;
-  if (tid == 0) { s_nc = 0; s_nk = 0; }
-  for (int m = tid; m < a.M; m += kRefThreads) {
-    double sn, cs;
-    sincospi(2.0 * m / a.M, &sn, &cs);
-    tw[m] = make_float2((float)cs, -(float)sn);
-  }
-  for (int i = tid; i < kRefKeys; i += kRefThreads) keys[i] = 0;
+  if (tid == 0) s_n = 0;
   __syncthreads();
-  for (int i = tid; i < cells; i += kRefThreads)
-    if (z[i] > a.zthr) {
-      const int slot = atomicAdd(&s_nc, 1);
-      if (slot < a.cap) cand[slot] = i;
+  for (int c0 = 0; c0 < cells; c0 += kRefThreads) {
+    const int i = c0 + tid;
+    const bool hit = i < cells && z[i] > a.zthr;
+    const unsigned m = __ballot_sync(0xffffffffu, hit);
+    // warp-ordered compaction: warps append in warp order within the chunk
+    __shared__ int s_wcount[kRefThreads / 32];
+    if (lane == 0) s_wcount[tid >> 5] = __popc(m);
+    __syncthreads();
+    int base = s_n;
+    for (int w = 0; w < (tid >> 5); ++w) base += s_wcount[w];
+    const int pos = base + __popc(m & ((1u << lane) - 1u));
+    if (hit && pos < a.cap) cand[(long)f * a.cap + pos] = i;
+    __syncthreads();
+    if (tid == 0) {
+      int t = 0;
+      for (int w = 0; w < kRefThreads / 32; ++w) t += s_wcount[w];
+      s_n += t;
     }
-  __syncthreads();
-  const int nc = s_nc;
-  if (nc > a.cap) {  // unsure: the full periodogram decides this frame
-    if (tid == 0) mask[f] = 1;
+    __syncthreads();
+  }
+  if (tid == 0) {
+    ncand[f] = s_n;
+    mask[f] = s_n > a.cap ? 1 : 0;
+  }
+}
+
+// One CTA per (frame, candidate): exact P on the 8 x 8 fine block, keys of
+// the local maxima of its inner 6 x 6 (36 slots, 0 = none).
+__global__ void __launch_bounds__(kRefThreads)
+refine_cand_kernel(const float2* __restrict__ strip, const int* __restrict__ cand, const int* __restrict__ ncand,
+                   uint64_t* __restrict__ keys, RefineArgs a) {
+  extern __shared__ __align__(16) unsigned char ref_smem[];
+  float2* tw = reinterpret_cast<float2*>(ref_smem);            // exp(-2 pi i m / M), from the plan
+  float2* rows8 = tw + a.M;                                    // 8 windowed strip rows
+  float* blk = reinterpret_cast<float*>(rows8 + 8 * a.M);      // 8 x 8 block of P
+  const int f = blockIdx.y, ci = blockIdx.x, tid = threadIdx.x;
+  uint64_t* kout = keys + ((long)f * a.cap + ci) * 36;
+  const int nc = ncand[f];
+  if (nc > a.cap || ci >= nc) {  // fallback frame or unused slot
+    if (tid < 36) kout[tid] = 0;
     return;
   }
-  if (tid == 0) mask[f] = 0;
+  for (int m = tid; m < a.M; m += kRefThreads) tw[m] = __ldg(a.rootsM + m);
   const float2* g = strip + (long)f * a.rows * a.M;
-  for (int ci = 0; ci < nc; ++ci) {
-    const int cell = cand[ci];
-    const int rc = cell / a.Mc, col = cell % a.Mc;
-    const int r0 = 4 * rc - 2;                        // first fine support row of the block
-    const int s0 = 4 * (col - a.Mc / 2) - 4;          // first fine (centred) Doppler bin
-    __syncthreads();
-    for (int e = tid; e < 8 * a.M; e += kRefThreads) {
-      const int u = e / a.M, l = e % a.M, ri = r0 + u;
-      rows8[e] = (ri >= 0 && ri < a.rows) ? cscale(g[(long)ri * a.M + l], __ldg(a.wl + l)) : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    {  // 64 cells, 8 lanes each
-      const int cidx = tid >> 3, part = tid & 7;
-      const int u = cidx >> 3, vv = cidx & 7;
-      const int sb = (s0 + vv) & (a.M - 1);
-      float2 acc = make_float2(0.f, 0.f);
-      for (int l = part; l < a.M; l += 8) acc = cadd(acc, cmul(rows8[u * a.M + l], tw[(l * sb) & (a.M - 1)]));
-      const unsigned m8 = 0xffu << (threadIdx.x & 24);
-      for (int off = 4; off; off >>= 1) {
-        acc.x += __shfl_xor_sync(m8, acc.x, off);
-        acc.y += __shfl_xor_sync(m8, acc.y, off);
-      }
-      if (part == 0) blk[cidx] = (acc.x * acc.x + acc.y * acc.y) * a.inv_nm;
-    }
-    __syncthreads();
-    if (tid < 36) {  // inner 6 x 6: local maxima with the map's key order
-      const int u = 1 + tid / 6, vv = 1 + tid % 6, ri = r0 + u;
-      const float p = blk[u * 8 + vv];
-      if (ri >= 0 && ri < a.rows && p > 0.f) {
-        auto idx_of = [&](int uu, int w) -> uint32_t {
-          const int r = (a.row0 + r0 + uu) & (a.N - 1);
-          const int s = ((s0 + w + a.M / 2) & (a.M - 1));   // map column of the centred bin
-          return (uint32_t)r * a.M + (uint32_t)s;
-        };
-        const uint64_t key = ((uint64_t)__float_as_uint(p) << 32) | (uint64_t)(~idx_of(u, vv));
-        bool ok = true;
-        for (int du = -1; du <= 1; ++du)
-          for (int dv = -1; dv <= 1; ++dv) {
-            if (!du && !dv) continue;
-            const int rn = r0 + u + du;
-            const float pn = (rn >= 0 && rn < a.rows) ? blk[(u + du) * 8 + vv + dv] : 0.f;
-            const uint64_t kn = ((uint64_t)__float_as_uint(pn) << 32) | (uint64_t)(~idx_of(u + du, vv + dv));
-            ok &= key > kn;
-          }
-        if (ok) {
-          const int slot = atomicAdd(&s_nk, 1);
-          if (slot < kRefKeys) keys[slot] = key;
-        }
-      }
-    }
+  const int cell = cand[(long)f * a.cap + ci];
+  const int rc = cell / a.Mc, col = cell % a.Mc;
+  const int r0 = 4 * rc - 2;                        // first fine support row of the block
+  const int s0 = 4 * (col - a.Mc / 2) - 4;          // first fine (centred) Doppler bin
+  for (int e = tid; e < 8 * a.M; e += kRefThreads) {
+    const int u = e / a.M, l = e % a.M, ri = r0 + u;
+    rows8[e] = (ri >= 0 && ri < a.rows) ? cscale(g[(long)ri * a.M + l], __ldg(a.wl + l)) : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  int n = min(s_nk, kRefKeys), sort_n = 32;
+  {  // 64 cells, 8 lanes each: P = |sum_l w_l g[r, l] e^{-2 pi i l s / M}|^2 / (N M)  (Eq. (17))
+    const int cidx = tid >> 3, part = tid & 7;
+    const int u = cidx >> 3, vv = cidx & 7;
+    const int sb = (s0 + vv) & (a.M - 1);
+    float2 acc = make_float2(0.f, 0.f);
+    for (int l = part; l < a.M; l += 8) acc = cadd(acc, cmul(rows8[u * a.M + l], tw[(l * sb) & (a.M - 1)]));
+    const unsigned m8 = 0xffu << (threadIdx.x & 24);
+    for (int off = 4; off; off >>= 1) {
+      acc.x += __shfl_xor_sync(m8, acc.x, off);
+      acc.y += __shfl_xor_sync(m8, acc.y, off);
+    }
+    if (part == 0) blk[cidx] = (acc.x * acc.x + acc.y * acc.y) * a.inv_nm;
+  }
+  __syncthreads();
+  if (tid < 36) {  // inner 6 x 6: local maxima with the map's key order
+    const int u = 1 + tid / 6, vv = 1 + tid % 6, ri = r0 + u;
+    const float p = blk[u * 8 + vv];
+    uint64_t key = 0;
+    if (ri >= 0 && ri < a.rows && p > 0.f) {
+      auto idx_of = [&](int uu, int w) -> uint32_t {
+        const int r = (a.row0 + r0 + uu) & (a.N - 1);
+        const int s = ((s0 + w + a.M / 2) & (a.M - 1));   // map column of the centred bin
+        return (uint32_t)r * a.M + (uint32_t)s;
+      };
+      key = ((uint64_t)__float_as_uint(p) << 32) | (uint64_t)(~idx_of(u, vv));
+      bool ok = true;
+      for (int du = -1; du <= 1; ++du)
+        for (int dv = -1; dv <= 1; ++dv) {
+          if (!du && !dv) continue;
+          const int rn = r0 + u + du;
+          const float pn = (rn >= 0 && rn < a.rows) ? blk[(u + du) * 8 + vv + dv] : 0.f;
+          const uint64_t kn = ((uint64_t)__float_as_uint(pn) << 32) | (uint64_t)(~idx_of(u + du, vv + dv));
+          ok &= key > kn;
+        }
+      if (!ok) key = 0;
+    }
+    kout[tid] = key;
+  }
+}
+
+// One CTA per frame: sort the candidates' keys, drop repeats (overlapping
+// blocks), report the strongest K.
+__global__ void __launch_bounds__(kRefThreads)
+refine_merge_kernel(const uint64_t* __restrict__ keys, const int* __restrict__ ncand, ofdm_target* __restrict__ out,
+                    int32_t* __restrict__ n_out, uint32_t* __restrict__ status, uint32_t* __restrict__ wstatus,
+                    RefineArgs a) {
+  extern __shared__ uint64_t buf[];   // next power of two >= cap * 36 keys
+  const int f = blockIdx.x, tid = threadIdx.x;
+  const int nc = ncand[f];
+  if (nc > a.cap) return;  // fallback frame: the full path reports it
+  const int n = min(nc, a.cap) * 36;
+  int sort_n = 32;
   while (sort_n < n) sort_n <<= 1;
+  for (int i = tid; i < sort_n; i += kRefThreads) buf[i] = i < n ? keys[(long)f * a.cap * 36 + i] : 0;
+  __syncthreads();
   for (int k = 2; k <= sort_n; k <<= 1)
     for (int j = k >> 1; j > 0; j >>= 1) {
       for (int i = tid; i < sort_n; i += kRefThreads) {
         const int p = i ^ j;
         if (p > i) {
-          const uint64_t x = keys[i], y = keys[p];
+          const uint64_t x = buf[i], y = buf[p];
           const bool desc = (i & k) == 0;
-          if (desc ? (x < y) : (x > y)) { keys[i] = y; keys[p] = x; }
+          if (desc ? (x < y) : (x > y)) { buf[i] = y; buf[p] = x; }
         }
       }
       __syncthreads();
     }
-  if (tid == 0) {  // distinct keys (overlapping blocks repeat a cell), strongest first
+  if (tid == 0) {
     int nv = 0;
     uint64_t prev = 0;
     for (int i = 0; i < n && nv < a.K; ++i) {
-      const uint64_t k = keys[i];
+      const uint64_t k = buf[i];
       if (k == 0 || k == prev) continue;
       prev = k;
       const uint32_t idx = ~(uint32_t)(k & 0xffffffffu);
@@ -220,14 +250,20 @@ cudaError_t launch_coarse(const float2* strip, unsigned* cpow, float* x, int row
 }
 
 cudaError_t launch_refine(const float2* strip, const float* logits, ofdm_target* out, int32_t* n_out,
-                          uint32_t* status, uint32_t* wstatus, int* mask, const RefineArgs& a, cudaStream_t s,
-                          int* launches) {
-  const size_t smem = (size_t)a.M * sizeof(float2) * 9 + kRefKeys * sizeof(uint64_t) + 64 * sizeof(float) +
-                      (size_t)a.cap * sizeof(int);
-  cudaError_t e = cudaFuncSetAttribute(refine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                          uint32_t* status, uint32_t* wstatus, int* mask, int* cand, int* ncand, uint64_t* keys,
+                          const RefineArgs& a, cudaStream_t s, int* launches) {
+  *launches += 3;
+  refine_select_kernel<<<a.frames, kRefThreads, 0, s>>>(logits, cand, ncand, mask, a);
+  const size_t smem = (size_t)a.M * sizeof(float2) * 9 + 64 * sizeof(float);
+  cudaError_t e = cudaFuncSetAttribute(refine_cand_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  ++*launches;
-  refine_kernel<<<a.frames, kRefThreads, smem, s>>>(strip, logits, out, n_out, status, wstatus, mask, a);
+  refine_cand_kernel<<<dim3(a.cap, a.frames), kRefThreads, smem, s>>>(strip, cand, ncand, keys, a);
+  int pow2 = 32;
+  while (pow2 < a.cap * 36) pow2 <<= 1;
+  const size_t msmem = (size_t)pow2 * sizeof(uint64_t);
+  e = cudaFuncSetAttribute(refine_merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msmem);
+  if (e != cudaSuccess) return e;
+  refine_merge_kernel<<<a.frames, kRefThreads, msmem, s>>>(keys, ncand, out, n_out, status, wstatus, a);
   return cudaGetLastError();
 }
 

@@ -41,7 +41,12 @@ constexpr size_t kOffStatus = align256(kOffWl + kMaxM * sizeof(float));     // u
 constexpr size_t kOffStrip = align256(kOffStatus + kNoallocMaxFrames * sizeof(uint32_t));
 constexpr size_t kOffPow = align256(kOffStrip + (size_t)kNoallocMaxCells * sizeof(float2));
 constexpr size_t kOffCtr = align256(kOffPow + (size_t)kNoallocMaxCells * sizeof(float));  // ticket counter
-constexpr size_t kScratchBytes = align256(kOffCtr + sizeof(unsigned long long));
+// detection workspace: frames * bands <= 2^20 / 8192 + frames (see detect_bands)
+constexpr size_t kMaxBandSlots = (kNoallocMaxCells / 8192) + kNoallocMaxFrames;
+constexpr size_t kOffDetKeys = align256(kOffCtr + sizeof(unsigned long long));
+constexpr size_t kOffDetTick = align256(kOffDetKeys + kMaxBandSlots * 32 * sizeof(uint64_t));
+constexpr size_t kOffEta = align256(kOffDetTick + 2 * kNoallocMaxFrames * sizeof(unsigned));
+constexpr size_t kScratchBytes = align256(kOffEta + kNoallocMaxFrames * sizeof(float));
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -257,6 +262,10 @@ extern "C" int ofdm_radar_process_noalloc(const ofdm_radar_params* pin, const of
   ta.rows = rows; ta.row0 = row0; ta.full = full; ta.compact = 1;
   ta.out_idx = nullptr;
   ta.frame_mask = nullptr;
+  ta.part_keys = reinterpret_cast<uint64_t*>(b + kOffDetKeys);
+  ta.tickets = reinterpret_cast<unsigned*>(b + kOffDetTick);   // zero-initialised with the array,
+  ta.counts = ta.tickets + kNoallocMaxFrames;                   // reset by every frame's last CTA
+  ta.eta = reinterpret_cast<float*>(b + kOffEta);
   ta.frame_stride = (long)rows * Mp; ta.frames = frames; ta.mode = p.detect_mode; ta.K = p.max_targets;
   ta.use_fixed_eta = p.noise_var > 0.f ? 1 : 0;
   ta.eta_fixed = p.noise_var * (float)(-log((double)p.pfa));

@@ -29,6 +29,11 @@ struct ofdm_radar_plan {
   float2* d_strip = nullptr;   // [max_frames][rows][M]
   float* d_pow = nullptr;      // [max_frames][rows][M']
   uint32_t* d_wstatus = nullptr;
+  // detection workspace: per-band keys, per-frame tickets / counters / eta
+  uint64_t* d_detkeys = nullptr;
+  unsigned* d_dettick = nullptr;   // [2][max_frames]: tickets, counts
+  float* d_eta = nullptr;
+  int det_bands = 0;
   // Ticket counters of the dynamically scheduled column kernel: slot 0 for
   // calls on the caller's stream, slots 1-2 for the two streams of the host
   // pipeline (launches that may run concurrently need separate counters).
@@ -50,7 +55,11 @@ struct ofdm_radar_plan {
   unsigned* d_cpow = nullptr;
   float *d_cx = nullptr, *d_a1 = nullptr, *d_a2 = nullptr, *d_logit = nullptr, *d_w4 = nullptr;
   float2* d_twMc = nullptr;
+  float2* d_rootsM = nullptr;   // exp(-2 pi i m / M)
   int* d_mask = nullptr;
+  int* d_cand = nullptr;        // [max_frames][256] candidate cells
+  int* d_ncand = nullptr;       // [max_frames]
+  uint64_t* d_keys = nullptr;   // [max_frames][256][36] local-maximum keys
   // per-kernel timing (ofdm_radar_timing_enable)
   int timing = 0;
   int nrec = 0;
@@ -182,6 +191,9 @@ void ofdm_radar_plan_destroy(ofdm_radar_plan* plan) {
   cudaFree(plan->d_pow);
   cudaFree(plan->d_wstatus);
   cudaFree(plan->d_ctr);
+  cudaFree(plan->d_detkeys);
+  cudaFree(plan->d_dettick);
+  cudaFree(plan->d_eta);
   cudaFree(plan->d_cpow);
   cudaFree(plan->d_cx);
   cudaFree(plan->d_a1);
@@ -189,7 +201,11 @@ void ofdm_radar_plan_destroy(ofdm_radar_plan* plan) {
   cudaFree(plan->d_logit);
   cudaFree(plan->d_w4);
   cudaFree(plan->d_twMc);
+  cudaFree(plan->d_rootsM);
   cudaFree(plan->d_mask);
+  cudaFree(plan->d_cand);
+  cudaFree(plan->d_ncand);
+  cudaFree(plan->d_keys);
   cudaFree(plan->d_Y);
   cudaFree(plan->d_X);
   cudaFree(plan->d_map);
@@ -311,6 +327,13 @@ int ofdm_radar_plan_create(const ofdm_radar_params* pin, ofdm_radar_plan** out) 
   if (e == cudaSuccess) e = dalloc(&pl->d_pow, (size_t)p.max_frames * pl->rows * Mp);
   if (e == cudaSuccess) e = dalloc(&pl->d_wstatus, (size_t)p.max_frames);
   if (e == cudaSuccess) e = dalloc(&pl->d_ctr, 3);
+  {
+    int br = 0;
+    ofdm::detect_bands(pl->rows, Mp, &br, &pl->det_bands);
+  }
+  if (e == cudaSuccess) e = dalloc(&pl->d_detkeys, (size_t)p.max_frames * pl->det_bands * 32);
+  if (e == cudaSuccess) e = dalloc(&pl->d_dettick, 2 * (size_t)p.max_frames);
+  if (e == cudaSuccess) e = dalloc(&pl->d_eta, (size_t)p.max_frames);
   if (e != cudaSuccess) {
     ofdm_radar_plan_destroy(pl);
     cudaGetLastError();
@@ -334,6 +357,7 @@ int ofdm_radar_plan_create(const ofdm_radar_params* pin, ofdm_radar_plan** out) 
   if (e == cudaSuccess) e = cudaMemcpy(pl->d_df, df.data(), df.size() * sizeof(float4), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(pl->d_wstatus, 0, (size_t)p.max_frames * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemset(pl->d_ctr, 0, 3 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(pl->d_dettick, 0, 2 * (size_t)p.max_frames * sizeof(unsigned));
   if (e != cudaSuccess) {
     ofdm_radar_plan_destroy(pl);
     return cuda_fail(e);
@@ -450,6 +474,10 @@ DetectArgs detect_args(const ofdm_radar_plan* pl, int frames, int compact) {
   a.compact = compact;
   a.out_idx = nullptr;
   a.frame_mask = nullptr;
+  a.part_keys = pl->d_detkeys;
+  a.tickets = pl->d_dettick;
+  a.counts = pl->d_dettick + pl->p.max_frames;
+  a.eta = pl->d_eta;
   a.frame_stride = compact ? (long)pl->rows * pl->Mp : (long)pl->Np * pl->Mp;
   a.frames = frames;
   a.mode = p.detect_mode;
@@ -612,6 +640,9 @@ int ofdm_radar_process_host(ofdm_radar_plan* pl, const ofdm_c32* Yh, const ofdm_
     view.d_strip = pl->d_strip + (size_t)f0 * pl->rows * p.M;
     view.d_pow = pl->d_pow + (size_t)f0 * pl->rows * pl->Mp;
     view.d_wstatus = pl->d_wstatus + f0;
+    view.d_detkeys = pl->d_detkeys + (size_t)f0 * pl->det_bands * 32;
+    view.d_dettick = pl->d_dettick + f0;  // tickets[f0..]; counts stay max_frames further on
+    view.d_eta = pl->d_eta + f0;
     e = run_chain(&view, pl->d_Y + g0, pl->d_X + g0, nf, map_h ? pl->d_map + mapn * f0 : nullptr,
                   pl->d_tg + (size_t)p.max_targets * f0, pl->d_nt + f0, pl->d_st + f0, s, &launches);
     pl->ctr_base[view.ctr_slot] = view.ctr_base[view.ctr_slot];
@@ -1000,8 +1031,18 @@ int ofdm_radar_learned_prepare(ofdm_radar_plan* pl) {
   if (e == cudaSuccess) e = dalloc(&pl->d_w4, (size_t)pl->Mc);
   if (e == cudaSuccess) e = dalloc(&pl->d_twMc, tw.size());
   if (e == cudaSuccess) e = dalloc(&pl->d_mask, (size_t)p.max_frames);
+  if (e == cudaSuccess) e = dalloc(&pl->d_cand, (size_t)p.max_frames * 256);
+  if (e == cudaSuccess) e = dalloc(&pl->d_ncand, (size_t)p.max_frames);
+  if (e == cudaSuccess) e = dalloc(&pl->d_keys, (size_t)p.max_frames * 256 * 36);
   if (e == cudaSuccess) e = cudaMemcpy(pl->d_w4, w4.data(), w4.size() * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(pl->d_twMc, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice);
+  std::vector<float2> roots(p.M);
+  for (int m = 0; m < p.M; ++m) {
+    const double a = 2.0 * M_PI * m / p.M;
+    roots[m] = make_float2((float)cos(a), (float)-sin(a));
+  }
+  if (e == cudaSuccess) e = dalloc(&pl->d_rootsM, (size_t)p.M);
+  if (e == cudaSuccess) e = cudaMemcpy(pl->d_rootsM, roots.data(), roots.size() * sizeof(float2), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return e == cudaErrorMemoryAllocation ? OFDM_ERR_NO_MEMORY : cuda_fail(e);
@@ -1057,8 +1098,9 @@ int ofdm_radar_process_learned(ofdm_radar_plan* pl, const float* theta, const of
   ra.N = pl->p.N; ra.M = pl->p.M; ra.rows = pl->rows; ra.row0 = pl->row0; ra.Hc = pl->Hc; ra.Mc = pl->Mc;
   ra.frames = frames; ra.K = pl->p.max_targets; ra.cap = cap; ra.zthr = zthr;
   ra.inv_nm = (float)(1.0 / ((double)pl->p.N * pl->p.M));
-  ra.dd = da.dd; ra.dv = da.dv; ra.wl = pl->d_wl;
-  e = ofdm::launch_refine(pl->d_strip, pl->d_logit, out, nt, st, pl->d_wstatus, pl->d_mask, ra, s, &launches);
+  ra.dd = da.dd; ra.dv = da.dv; ra.wl = pl->d_wl; ra.rootsM = pl->d_rootsM;
+  e = ofdm::launch_refine(pl->d_strip, pl->d_logit, out, nt, st, pl->d_wstatus, pl->d_mask, pl->d_cand,
+                          pl->d_ncand, pl->d_keys, ra, s, &launches);
   // fallback: the full Doppler stage and detection on the flagged frames only
   if (e == cudaSuccess) {
     DopplerArgs dop = doppler_args(pl, frames);
