@@ -39,9 +39,15 @@ struct PipeCfg {
   static constexpr int BUF = smem_elems(N);  // float2 per row buffer
   static constexpr int FIT = (int)((227u * 1024u) / (3u * BUF * sizeof(float2)));
   static constexpr int WMAX = FIT < 10 ? FIT : 10;
-  static constexpr int WARPS = W > 0 && W < WMAX ? W : WMAX;
+  // N = 1024, widest variant: the pre-chirp and pass-1 twiddle tables (16 KB)
+  // live in shared memory, which leaves room for 8 warps instead of 9.
+  static constexpr bool SMEM_TABLES = (N == 1024 && W == 0);
+  static constexpr int TABLE_BYTES = SMEM_TABLES ? 2 * N * (int)sizeof(float2) : 0;
+  static constexpr int WFIT = (int)((227u * 1024u - TABLE_BYTES) / (3u * BUF * sizeof(float2)));
+  static constexpr int WMAX2 = WFIT < WMAX ? WFIT : WMAX;
+  static constexpr int WARPS = W > 0 && W < WMAX2 ? W : WMAX2;
   static constexpr int THREADS = 32 * WARPS;
-  static constexpr size_t SMEM = (size_t)WARPS * 3 * BUF * sizeof(float2);
+  static constexpr size_t SMEM = (size_t)WARPS * 3 * BUF * sizeof(float2) + TABLE_BYTES;
 };
 
 __device__ __forceinline__ uint64_t evict_first_policy() {
@@ -193,6 +199,18 @@ column_pipe_kernel(const float2* __restrict__ Y, const float2* __restrict__ X, f
   float2* ring = smem + (size_t)warp * 3 * C::BUF;
   const long total = (long)a.frames * a.M;
   const uint64_t pol = evict_first_policy();
+  const float2* pre = a.pre;
+  const float2* tw1 = a.tw;   // pass-1 table: tw1[r * 32 + u] for N = 1024
+  if constexpr (C::SMEM_TABLES) {
+    float2* tab = smem + (size_t)C::WARPS * 3 * C::BUF;
+    for (int i = threadIdx.x; i < N; i += C::THREADS) {
+      tab[i] = __ldg(a.pre + i);
+      tab[N + i] = __ldg(a.tw + i);
+    }
+    __syncthreads();
+    pre = tab;
+    tw1 = tab + N;
+  }
 
   auto issue_row = [&](const float2* g, float2* dst) {
     const char* gs = reinterpret_cast<const char*>(g);
@@ -240,7 +258,7 @@ column_pipe_kernel(const float2* __restrict__ Y, const float2* __restrict__ X, f
       for (int q = 0; q < E; ++q) {
         const int k = lane + 32 * q;
         const int s = (a.rinv == 1) ? k : (int)(((unsigned)a.rinv * (unsigned)k) & (N - 1));
-        v[q] = cmul(sa[s], __ldg(a.pre + s));
+        v[q] = cmul(sa[s], pre[s]);
       }
     } else {
       cp_async_wait<1>();                   // A(sym) and Y(sym)
@@ -264,7 +282,7 @@ column_pipe_kernel(const float2* __restrict__ Y, const float2* __restrict__ X, f
 #pragma unroll
           for (int r = 0; r < 32; ++r) v[r] = sa[pad32(lane + 32 * r)];
 #pragma unroll
-          for (int r = 1; r < 32; ++r) v[r] = cmul(v[r], __ldg(a.tw + r * 32 + lane));
+          for (int r = 1; r < 32; ++r) v[r] = cmul(v[r], tw1[r * 32 + lane]);
         }
         dft_reg<32, +1>(v);
         if (!(h & 1)) {
