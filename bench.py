@@ -155,10 +155,11 @@ def barrier_sync(dist, torch):
     torch.cuda.synchronize()
 
 
-def max_over_ranks(dist, torch, v):
+def max_over_ranks(dist, torch, v, device="cuda"):
+    """Largest value over the ranks (the slowest rank's time)."""
     if dist is None:
         return v
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    t = torch.tensor([v], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
