@@ -35,10 +35,10 @@ struct ofdm_radar_plan {
   float* d_eta = nullptr;
   int det_bands = 0;
   // Ticket counters of the dynamically scheduled column kernel: slot 0 for
-  // calls on the caller's stream, slots 1-2 for the two streams of the host
+  // calls on the caller's stream, slots 1-4 for the four streams of the host
   // pipeline (launches that may run concurrently need separate counters).
   unsigned long long* d_ctr = nullptr;
-  unsigned long long ctr_base[3] = {0, 0, 0};
+  unsigned long long ctr_base[1 + 4] = {0, 0, 0, 0, 0};
   int ctr_slot = 0;
   // host-buffer path (allocated on first use)
   float2* d_Y = nullptr;
@@ -47,8 +47,8 @@ struct ofdm_radar_plan {
   ofdm_target* d_tg = nullptr;
   int32_t* d_nt = nullptr;
   uint32_t* d_st = nullptr;
-  cudaStream_t hs[2] = {nullptr, nullptr};
-  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  cudaStream_t hs[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   int last_launches = 0;
   // learned proposal workspace (ofdm_radar_learned_prepare)
   int Hc = 0, Mc = 0;
@@ -326,7 +326,7 @@ int ofdm_radar_plan_create(const ofdm_radar_params* pin, ofdm_radar_plan** out) 
   if (e == cudaSuccess) e = dalloc(&pl->d_strip, (size_t)p.max_frames * pl->rows * M);
   if (e == cudaSuccess) e = dalloc(&pl->d_pow, (size_t)p.max_frames * pl->rows * Mp);
   if (e == cudaSuccess) e = dalloc(&pl->d_wstatus, (size_t)p.max_frames);
-  if (e == cudaSuccess) e = dalloc(&pl->d_ctr, 3);
+  if (e == cudaSuccess) e = dalloc(&pl->d_ctr, 5);
   {
     int br = 0;
     ofdm::detect_bands(pl->rows, Mp, &br, &pl->det_bands);
@@ -356,7 +356,7 @@ int ofdm_radar_plan_create(const ofdm_radar_params* pin, ofdm_radar_plan** out) 
   if (e == cudaSuccess) e = cudaMemcpy(pl->d_wl, wl.data(), M * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(pl->d_df, df.data(), df.size() * sizeof(float4), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(pl->d_wstatus, 0, (size_t)p.max_frames * sizeof(uint32_t));
-  if (e == cudaSuccess) e = cudaMemset(pl->d_ctr, 0, 3 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(pl->d_ctr, 0, 5 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(pl->d_dettick, 0, 2 * (size_t)p.max_frames * sizeof(unsigned));
   if (e != cudaSuccess) {
     ofdm_radar_plan_destroy(pl);
@@ -612,8 +612,8 @@ int ofdm_radar_process_host(ofdm_radar_plan* pl, const ofdm_c32* Yh, const ofdm_
     if (e == cudaSuccess) e = dalloc(&pl->d_tg, (size_t)p.max_targets * p.max_frames);
     if (e == cudaSuccess) e = dalloc(&pl->d_nt, (size_t)p.max_frames);
     if (e == cudaSuccess) e = dalloc(&pl->d_st, (size_t)p.max_frames);
-    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&pl->hs[i], cudaStreamNonBlocking);
-    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&pl->ev[i], cudaEventDisableTiming);
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&pl->hs[i], cudaStreamNonBlocking);
+    for (int i = 0; i < 5 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&pl->ev[i], cudaEventDisableTiming);
     if (e != cudaSuccess) {
       cudaFree(pl->d_Y); pl->d_Y = nullptr;
       cudaGetLastError();
@@ -621,22 +621,22 @@ int ofdm_radar_process_host(ofdm_radar_plan* pl, const ofdm_c32* Yh, const ofdm_
     }
   }
   cudaStream_t s0 = (cudaStream_t)stream;
-  // Chunks of frames alternate between two streams so that the copies of one
-  // chunk overlap the kernels of the other.
-  const int chunk = frames >= 8 ? (frames + 3) / 4 : frames;
+  // Chunks of frames rotate over four streams so that the copies of one
+  // chunk (in both directions) overlap the kernels and copies of the others.
+  const int chunk = frames >= 16 ? (frames + 7) / 8 : (frames >= 4 ? (frames + 3) / 4 : frames);
   e = cudaEventRecord(pl->ev[0], s0);
-  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(pl->hs[i], pl->ev[0], 0);
+  for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(pl->hs[i], pl->ev[0], 0);
   int launches = 0, k = 0;
   for (int f0 = 0; f0 < frames && e == cudaSuccess; f0 += chunk, ++k) {
     const int nf = frames - f0 < chunk ? frames - f0 : chunk;
-    cudaStream_t s = pl->hs[k & 1];
+    cudaStream_t s = pl->hs[k & 3];
     const size_t g0 = grid * f0, gn = grid * nf;
     e = cudaMemcpyAsync(pl->d_Y + g0, Yh + g0, gn * sizeof(float2), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(pl->d_X + g0, Xh + g0, gn * sizeof(float2), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) break;
     // The chunk uses its own slice of the workspace (frame offset f0).
     ofdm_radar_plan view = *pl;
-    view.ctr_slot = 1 + (k & 1);
+    view.ctr_slot = 1 + (k & 3);
     view.d_strip = pl->d_strip + (size_t)f0 * pl->rows * p.M;
     view.d_pow = pl->d_pow + (size_t)f0 * pl->rows * pl->Mp;
     view.d_wstatus = pl->d_wstatus + f0;
@@ -658,7 +658,7 @@ int ofdm_radar_process_host(ofdm_radar_plan* pl, const ofdm_c32* Yh, const ofdm_
     if (e == cudaSuccess && st_h)
       e = cudaMemcpyAsync(st_h + f0, pl->d_st + f0, nf * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
   }
-  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+  for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
     e = cudaEventRecord(pl->ev[1 + i], pl->hs[i]);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s0, pl->ev[1 + i], 0);
   }
