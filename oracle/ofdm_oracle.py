@@ -577,3 +577,12 @@ def coarse_map(g_rows: np.ndarray, window_kind: int) -> np.ndarray:
     for c in range(Mc):
         Cs[:, c] = C[:, (c - Mc // 2) % Mc]
     return np.log1p(Cs / Cs.mean())
+
+
+def papr(S: np.ndarray) -> np.ndarray:
+    """PAPR of each OFDM symbol (column of S), Eq. (25), with the time signal of
+    Eq. (1): x[n] = sum_k S[k] e^{+j 2 pi n k / N} (no 1/N).  Linear ratio."""
+    S = np.asarray(S, dtype=np.complex128)
+    x = dft_matrix(S.shape[0]).conj() @ S
+    p = np.abs(x) ** 2
+    return p.max(axis=0) / p.mean(axis=0)

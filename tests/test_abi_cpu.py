@@ -64,3 +64,19 @@ def test_null_arguments_rejected(radar):
     assert lib.ofdm_zc_precode(None, None, None, 1, 0, None) == -1
     assert lib.ofdm_radar_plan_create(None, None) == -1
     assert lib.ofdm_radar_strerror(-2).decode() == "unsupported size"
+
+
+def test_more_struct_layouts(radar):
+    assert ctypes.sizeof(radar.FrameDesc) == 32
+    assert ctypes.sizeof(radar.FpsParams) == 24
+    fp = radar.fps_default_params()
+    assert (fp.iterations, fp.offsets, fp.max_recover) == (4, 8, 32)
+    assert abs(fp.coherence_min - 0.95) < 1e-6
+
+
+def test_batch_and_fps_reject_bad_input_before_any_launch(radar):
+    lib = radar.lib()
+    assert lib.ofdm_radar_batch_create(None, None, 0, 0, None) == -1
+    assert lib.ofdm_fps_sft(None, None, None, 1, None, None, None, None, None) == -1
+    assert lib.ofdm_radar_process_learned(None, None, None, None, 1, 0.0, 8, None, None, None, None) == -1
+    assert radar.ofdm_cnn_param_count() == 16 * 9 + 16 + 16 * 16 * 9 + 16 + 16 * 9 + 1

@@ -468,3 +468,23 @@ def test_cnn_gradient_matches_finite_differences():
         e[i] = h
         fd = (loss(theta + e) - loss(theta - e)) / (2 * h)
         assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), i
+
+
+# ---------------------------------------------------------------- PAPR (Sec. III-B, Eq. (25))
+def test_papr_closed_forms():
+    N = 64
+    single = np.zeros((N, 1), complex)
+    single[5] = 1.0                       # one subcarrier: constant-modulus time signal
+    assert o.papr(single)[0] == pytest.approx(1.0)
+    flat = np.ones((N, 1), complex)       # all ones: x = N delta[n]
+    assert o.papr(flat)[0] == pytest.approx(N)
+
+
+def test_zc_precoding_lowers_papr():
+    # The paper's claim (Sec. III-B): ZC precoding reduces the OFDM PAPR.
+    rng = np.random.default_rng(0)
+    A = syn.qam_symbols(rng, (128, 200), 16)
+    p0 = 10 * np.log10(o.papr(A))
+    p1 = 10 * np.log10(o.papr(o.zc_precode(A, 1)))
+    assert np.median(p1) < np.median(p0) - 3.0
+    assert np.quantile(p1, 0.99) < np.quantile(p0, 0.5)
