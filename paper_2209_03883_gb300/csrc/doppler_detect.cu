@@ -16,60 +16,94 @@
 
 namespace ofdm {
 
-constexpr int kDopWarps = 8;
+constexpr int kDopWarps = 4;
 
+// Each warp transforms rows task, task + stride, ... (stride = all warps of
+// the grid); for M' <= 512 the next row's loads are issued before the
+// current row's transform so that their latency is hidden.
 template <int MP>
 __global__ void __launch_bounds__(32 * kDopWarps)
 doppler_kernel(const float2* __restrict__ strip, float* __restrict__ map, float* __restrict__ pow,
                DopplerArgs a) {
   const int warp = threadIdx.x >> 5, t = threadIdx.x & 31;
-  const long task = (long)blockIdx.x * kDopWarps + warp;
-  if (task >= (long)a.frames * a.rows) return;
-  const int f = (int)(task / a.rows);
-  if (a.frame_mask && !a.frame_mask[f]) return;
-  const int ri = (int)(task % a.rows);
-  const int r = (a.row0 + ri) % a.Np;
-  const float2* g = strip + task * a.M;
-  float* prow = pow + task * MP;
-  float* mrow = map ? map + (a.map_off ? (long)a.map_off[f] : (long)f * a.Np * MP) + (long)r * MP : nullptr;
+  const long nt = (long)a.frames * a.rows;
+  const long stride = (long)gridDim.x * kDopWarps;
+  long task = (long)blockIdx.x * kDopWarps + warp;
+  auto map_row = [&](int f, int r) -> float* {
+    return map ? map + (a.map_off ? (long)a.map_off[f] : (long)f * a.Np * MP) + (long)r * MP : nullptr;
+  };
 
   if constexpr (MP <= 32) {
-    // Direct DFT: lane s computes one bin; g[l] is broadcast by shuffles.
-    float2 gl = make_float2(0.f, 0.f);
-    if (t < a.M) gl = cscale(g[t], __ldg(a.wl + t));
-    float2 acc = make_float2(0.f, 0.f);
-    for (int l = 0; l < a.M; ++l) {
-      float2 x;
-      x.x = __shfl_sync(0xffffffffu, gl.x, l);
-      x.y = __shfl_sync(0xffffffffu, gl.y, l);
-      float2 w = __ldg(a.tw + ((l * t) & (MP - 1)));
-      w.y = -w.y;
-      acc = cadd(acc, cmul(x, w));
-    }
-    if (t < MP) {
-      const int c = (t + MP / 2) & (MP - 1);
-      const float p = (acc.x * acc.x + acc.y * acc.y) * a.inv_nm;
-      prow[c] = p;
-      if (mrow) mrow[c] = p;
+    for (; task < nt; task += stride) {
+      const int f = (int)(task / a.rows);
+      if (a.frame_mask && !a.frame_mask[f]) continue;
+      const int r = (a.row0 + (int)(task % a.rows)) % a.Np;
+      const float2* g = strip + task * a.M;
+      float* prow = pow + task * MP;
+      float* mrow = map_row(f, r);
+      // Direct DFT: lane s computes one bin; g[l] is broadcast by shuffles.
+      float2 gl = make_float2(0.f, 0.f);
+      if (t < a.M) gl = cscale(g[t], __ldg(a.wl + t));
+      float2 acc = make_float2(0.f, 0.f);
+      for (int l = 0; l < a.M; ++l) {
+        float2 x;
+        x.x = __shfl_sync(0xffffffffu, gl.x, l);
+        x.y = __shfl_sync(0xffffffffu, gl.y, l);
+        float2 w = __ldg(a.tw + ((l * t) & (MP - 1)));
+        w.y = -w.y;
+        acc = cadd(acc, cmul(x, w));
+      }
+      if (t < MP) {
+        const int c = (t + MP / 2) & (MP - 1);
+        const float p = (acc.x * acc.x + acc.y * acc.y) * a.inv_nm;
+        prow[c] = p;
+        if (mrow) mrow[c] = p;
+      }
     }
   } else {
     constexpr int E = MP / 32;
+    constexpr bool PF = E <= 16;
     extern __shared__ float2 smem[];
     float2* sm = smem + warp * smem_elems(MP);
-    float2 v[E];
+    float w[E];
 #pragma unroll
-    for (int q = 0; q < E; ++q) {
-      const int l = t + 32 * q;
-      v[q] = (l < a.M) ? cscale(g[l], __ldg(a.wl + l)) : make_float2(0.f, 0.f);
-    }
-    group_fft<MP, 32, -1>(v, sm, a.tw, t, 0);
+    for (int q = 0; q < E; ++q) w[q] = (t + 32 * q < a.M) ? __ldg(a.wl + t + 32 * q) : 0.f;
+    auto load = [&](long tk, float2* d) {
+      const float2* g = strip + tk * a.M;
 #pragma unroll
-    for (int q = 0; q < E; ++q) {
-      const int s = t + 32 * q;
-      const int c = (s + MP / 2) & (MP - 1);
-      const float p = (v[q].x * v[q].x + v[q].y * v[q].y) * a.inv_nm;
-      prow[c] = p;
-      if (mrow) __stcs(mrow + c, p);
+      for (int q = 0; q < E; ++q) d[q] = (t + 32 * q < a.M) ? g[t + 32 * q] : make_float2(0.f, 0.f);
+    };
+    float2 cur[E], nxt[PF ? E : 1];
+    if (PF && task < nt) load(task, cur);
+    for (; task < nt; task += stride) {
+      const long nx = task + stride;
+      if constexpr (PF) {
+        if (nx < nt) load(nx, nxt);
+      } else {
+        load(task, cur);
+      }
+      const int f = (int)(task / a.rows);
+      if (!a.frame_mask || a.frame_mask[f]) {
+        const int r = (a.row0 + (int)(task % a.rows)) % a.Np;
+        float* prow = pow + task * MP;
+        float* mrow = map_row(f, r);
+        float2 v[E];
+#pragma unroll
+        for (int q = 0; q < E; ++q) v[q] = cscale(cur[q], w[q]);
+        group_fft<MP, 32, -1>(v, sm, a.tw, t, 0);
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+          const int s = t + 32 * q;
+          const int c = (s + MP / 2) & (MP - 1);
+          const float p = (v[q].x * v[q].x + v[q].y * v[q].y) * a.inv_nm;
+          prow[c] = p;
+          if (mrow) __stcs(mrow + c, p);
+        }
+      }
+      if constexpr (PF) {
+#pragma unroll
+        for (int q = 0; q < E; ++q) cur[q] = nxt[q];
+      }
     }
   }
 }
@@ -123,116 +157,194 @@ __device__ void bitonic_desc(uint64_t* buf, int n) {
   }
 }
 
-// Key of the cell at tile row i (1..tr) and column c, or 0.  Fast path: float
-// comparisons with the eight neighbours; the map-index tie-break runs only
-// when a neighbour has exactly the same power.
-__device__ __forceinline__ uint64_t band_key(const float* tile, const DetectArgs& a, int t0, int i, int c,
-                                             float eta) {
-  const float p = tile[(i << a.logMp) + c];
-  if (!(p > 0.f) || (a.mode == OFDM_DETECT_THRESHOLD && !(p >= eta))) return 0;
-  const int cm = (c - 1) & (a.Mp - 1), cp = (c + 1) & (a.Mp - 1);
-  const float* up = tile + ((i - 1) << a.logMp);
-  const float* mid = tile + (i << a.logMp);
-  const float* dn = tile + ((i + 1) << a.logMp);
-  const float n0 = up[cm], n1 = up[c], n2 = up[cp], n3 = mid[cm], n4 = mid[cp], n5 = dn[cm], n6 = dn[c],
-              n7 = dn[cp];
-  const bool larger = (n0 > p) | (n1 > p) | (n2 > p) | (n3 > p) | (n4 > p) | (n5 > p) | (n6 > p) | (n7 > p);
-  if (larger) return 0;
-  const int r = (a.row0 + t0 + i - 1) & (a.Np - 1);
-  const uint32_t idx = ((uint32_t)r << a.logMp) + c;
-  const bool equal = (n0 == p) | (n1 == p) | (n2 == p) | (n3 == p) | (n4 == p) | (n5 == p) | (n6 == p) | (n7 == p);
-  if (equal) {
-    const float nb[8] = {n0, n1, n2, n3, n4, n5, n6, n7};
-    const int dr[8] = {-1, -1, -1, 0, 0, 1, 1, 1}, dc[8] = {-1, 0, 1, -1, 1, -1, 0, 1};
-    for (int k = 0; k < 8; ++k)
-      if (nb[k] == p) {
-        const uint32_t in_idx = ((uint32_t)((r + dr[k]) & (a.Np - 1)) << a.logMp) + ((c + dc[k]) & (a.Mp - 1));
-        if (in_idx < idx) return 0;
+// A local maximum with an 8-neighbour of exactly the same power keeps its
+// place only if its flat map index is the smaller one (the order of the
+// output).  `ti` is the cell's tile row, r its map row.  Kept out of line:
+// the scan calls it only for cells that have such a neighbour.
+__device__ __noinline__ bool tie_lost(const float* tile, int logMp, int Np, int r, int ti, int c, float p) {
+  const int Mp = 1 << logMp;
+  const uint32_t idx = ((uint32_t)r << logMp) + (uint32_t)c;
+  for (int dr = -1; dr <= 1; ++dr)
+    for (int dc = -1; dc <= 1; ++dc) {
+      if (dr == 0 && dc == 0) continue;
+      const int cc = (c + dc) & (Mp - 1);
+      if (tile[((ti + dr) << logMp) + cc] == p) {
+        const uint32_t nidx = ((uint32_t)((r + dr) & (Np - 1)) << logMp) + (uint32_t)cc;
+        if (nidx < idx) return true;
       }
-  }
-  return ((uint64_t)__float_as_uint(p) << 32) | (uint64_t)(~idx);
+    }
+  return false;
 }
 
+// Warp-wide bitonic sort of one key per lane, descending (lane 0 the largest).
+__device__ __forceinline__ uint64_t warp_sort_desc(uint64_t v, int lane) {
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const uint64_t o = __shfl_xor_sync(0xffffffffu, v, j);
+      const bool keep_max = ((lane & j) == 0) == ((lane & k) == 0);
+      v = keep_max ? (v > o ? v : o) : (v < o ? v : o);
+    }
+  }
+  return v;
+}
+
+// Largest key of the warp: the larger power word, then the larger index word.
+__device__ __forceinline__ uint64_t warp_max_key(uint64_t v) {
+  const unsigned hi = (unsigned)(v >> 32);
+  const unsigned mh = __reduce_max_sync(0xffffffffu, hi);
+  const unsigned ml = __reduce_max_sync(0xffffffffu, hi == mh ? (unsigned)v : 0u);
+  return ((uint64_t)mh << 32) | ml;
+}
+
+// LOGC = log2 of the columns each thread scans: 0 for M' <= 256, 1 for 512,
+// 2 for 1024 (the band always holds 8192 / M' rows, 32 cells per thread).
+template <int LOGC>
 __global__ void __launch_bounds__(kDetThreads)
 detect_band_kernel(const float* __restrict__ src, ofdm_target* __restrict__ out, int32_t* __restrict__ n_out,
                    uint32_t* __restrict__ status, uint32_t* __restrict__ wstatus, DetectArgs a) {
+  constexpr int C = 1 << LOGC, NR = 32 >> LOGC;
   extern __shared__ __align__(16) unsigned char det_smem[];
   __shared__ uint64_t buf[kBandCap];
-  __shared__ uint32_t bits[8192 / 32 + 32];
   __shared__ unsigned s_n, s_cnt;
+  __shared__ uint64_t s_floor;
   __shared__ int s_last;
-  float* tile = reinterpret_cast<float*>(det_smem);
+  float* tile = reinterpret_cast<float*>(det_smem);  // (8192 / M' + 2) rows of M'
   const int band = blockIdx.x, f = blockIdx.y;
   if (a.frame_mask && !a.frame_mask[f]) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int K = a.K;
+  const int K = a.K, Mp = a.Mp, logMp = a.logMp;
   const int t0 = band * a.band_rows;
   const int tr = min(a.band_rows, a.rows - t0);
   const float* base = src + (long)f * a.frame_stride;
-  const float eta = a.mode == OFDM_DETECT_THRESHOLD ? (a.use_fixed_eta ? a.eta_fixed : a.eta[f]) : 0.f;
+  const bool thr = a.mode == OFDM_DETECT_THRESHOLD;
+  const float eta = thr ? (a.use_fixed_eta ? a.eta_fixed : a.eta[f]) : 0.f;
 
   // stage rows t0 - 1 .. t0 + tr; rows outside a partial support are zero, a full support wraps
-  const int n4 = ((tr + 2) << a.logMp) >> 2;
+  const int n4 = ((tr + 2) << logMp) >> 2;
   for (int v = tid; v < n4; v += kDetThreads) {
     const int idx = v << 2;
-    const int i = idx >> a.logMp, c = idx & (a.Mp - 1);
+    const int i = idx >> logMp, c = idx & (Mp - 1);
     int rj = t0 - 1 + i;
-    float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
     if (a.full) rj &= (a.rows - 1);
     if (rj >= 0 && rj < a.rows) {
       const int row = a.compact ? rj : ((a.row0 + rj) & (a.Np - 1));
-      val = *reinterpret_cast<const float4*>(base + ((long)row << a.logMp) + c);
+      const unsigned d = (unsigned)__cvta_generic_to_shared(tile + idx);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(base + ((long)row << logMp) + c)
+                   : "memory");
+    } else {
+      *reinterpret_cast<float4*>(tile + idx) = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    *reinterpret_cast<float4*>(tile + idx) = val;
   }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
   if (tid == 0) { s_n = 0; s_cnt = 0; }
+
+  // The map rows outside the support are zero: this CTA's share of its
+  // frame, one streaming store per scanned row and the rest after the scan.
+  float4* zp = nullptr;
+  long zj = 0, zj1 = 0;
+  if (a.zmap) {
+    const long per = a.z_floats >> 2;
+    zj = per * band / a.bands + tid;
+    zj1 = per * (band + 1) / a.bands;
+    zp = reinterpret_cast<float4*>(a.zmap + (a.zmap_off ? (long)a.zmap_off[f] : (long)f * a.zframe) + a.z_off);
+  }
+  const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
   __syncthreads();
 
-  // scan 1: candidate bits, count, each thread's best key
-  const int nt = tr << a.logMp;
-  uint64_t best = 0;
+  // Scan: each thread walks down C columns c0 + 256 q over NR band rows from
+  // i0, keeping the 3-wide maxima of the rows above and below in registers.
+  // Bit q NR + k of `mine` marks a local maximum at band row i0 + k.  Rows at
+  // or past tr read tile rows that were not staged and are masked out.
+  const int c0 = LOGC == 0 ? (tid & (Mp - 1)) : tid;
+  const int i0 = LOGC == 0 ? ((tid >> logMp) << 5) : 0;
+  const uint32_t rbase = (uint32_t)(a.row0 + t0);
+  uint32_t mine = 0;
   unsigned cnt = 0;
-  for (int e0 = 0; e0 < nt; e0 += kDetThreads) {
-    const int e = e0 + tid;
-    const uint64_t key = e < nt ? band_key(tile, a, t0, 1 + (e >> a.logMp), e & (a.Mp - 1), eta) : 0;
-    const unsigned m = __ballot_sync(0xffffffffu, key != 0);
-    if (lane == 0) bits[(e0 >> 5) + warp] = m;
-    cnt += key ? 1u : 0u;
-    best = key > best ? key : best;
+  uint64_t best = 0;
+#pragma unroll
+  for (int q = 0; q < C; ++q) {
+    const int c = c0 + (q << 8);
+    const int cm = (c - 1) & (Mp - 1), cp = (c + 1) & (Mp - 1);
+    const float* row = tile + (i0 << logMp);          // tile row i0 = band row i0 - 1
+    float up3 = fmaxf(row[c], fmaxf(row[cm], row[cp]));
+    row += Mp;
+    float ml = row[cm], mc = row[c], mr = row[cp];
+#pragma unroll 8
+    for (int k = 0; k < NR; ++k) {
+      const int i = i0 + k;
+      row += Mp;                                      // band row i + 1
+      const float dl = row[cm], dc = row[c], dr = row[cp];
+      const float mid2 = fmaxf(ml, mr);
+      const float nmax = fmaxf(up3, fmaxf(mid2, fmaxf(dc, fmaxf(dl, dr))));
+      const float p = mc;
+      // fmaxf skips NaN, so this is "no neighbour compares greater"
+      bool cand = i < tr && p > 0.f && !(nmax > p) && (!thr || p >= eta);
+      const uint32_t r = (rbase + (uint32_t)i) & (uint32_t)(a.Np - 1);
+      if (cand && nmax == p) cand = !tie_lost(tile, logMp, a.Np, (int)r, i + 1, c, p);
+      const uint64_t key =
+          cand ? ((uint64_t)__float_as_uint(p) << 32) | (uint64_t)(~((r << logMp) + (uint32_t)c)) : 0ull;
+      best = key > best ? key : best;
+      mine |= (uint32_t)cand << (q * NR + k);
+      cnt += cand ? 1u : 0u;
+      up3 = fmaxf(mid2, mc);
+      ml = dl; mc = dc; mr = dr;
+      if (zj < zj1) { __stcs(zp + zj, zero4); zj += kDetThreads; }
+    }
   }
+  for (; zj < zj1; zj += kDetThreads) __stcs(zp + zj, zero4);
   cnt = __reduce_add_sync(0xffffffffu, cnt);
   if (lane == 0) atomicAdd(&s_cnt, cnt);
-  buf[tid] = best;
+
+  // Floor = the K-th best of the 256 per-thread best keys: each warp sorts its
+  // 32, warp 0 merges the eight sorted lists for K steps.  Every key of the
+  // band's top K is at or above it, and at most K threads hold keys there.
+  buf[tid] = warp_sort_desc(best, lane);
   __syncthreads();
-  bitonic_desc(buf, kDetThreads);      // the K-th best per-thread key is a floor for the band's top K
-  const uint64_t floor_key = buf[K - 1];
+  if (warp == 0) {
+    int h = 0;
+    uint64_t head = lane < kDetThreads / 32 ? buf[lane << 5] : 0, m = 0;
+    for (int r = 0; r < K; ++r) {
+      m = warp_max_key(head);
+      if (m == 0) break;                              // fewer than K threads found a maximum
+      if (head == m) { ++h; head = h < 32 ? buf[(lane << 5) + h] : 0; }
+    }
+    if (lane == 0) s_floor = m;
+  }
   __syncthreads();
-  for (int i = tid; i < kBandCap; i += kDetThreads) buf[i] = 0;
-  __syncthreads();
-  // scan 2: keys >= floor (only cells with their candidate bit set)
-  for (int e0 = 0; e0 < nt; e0 += kDetThreads) {
-    const int e = e0 + tid;
-    uint64_t key = 0;
-    if (e < nt && ((bits[e >> 5] >> (e & 31)) & 1u))
-      key = band_key(tile, a, t0, 1 + (e >> a.logMp), e & (a.Mp - 1), eta);
-    const bool keep = key != 0 && key >= floor_key;
-    const unsigned km = __ballot_sync(0xffffffffu, keep);
-    if (km) {
-      unsigned wb = 0;
-      if (lane == 0) wb = atomicAdd(&s_n, (unsigned)__popc(km));
-      wb = __shfl_sync(0xffffffffu, wb, 0);
-      const unsigned pos = wb + __popc(km & ((1u << lane) - 1u));
-      if (keep && pos < kBandCap) buf[pos] = key;
+  const uint64_t floor_key = s_floor;
+  // keys at or above the floor (at most 32 K <= kBandCap)
+  if (best != 0 && best >= floor_key) {
+    for (uint32_t m = mine; m; m &= m - 1) {
+      const int b = __ffs(m) - 1;
+      const int q = b / NR, i = i0 + (b % NR), c = c0 + (q << 8);
+      const float p = tile[((i + 1) << logMp) + c];
+      const uint32_t r = (rbase + (uint32_t)i) & (uint32_t)(a.Np - 1);
+      const uint64_t key = ((uint64_t)__float_as_uint(p) << 32) | (uint64_t)(~((r << logMp) + (uint32_t)c));
+      if (key >= floor_key) {
+        const unsigned pos = atomicAdd(&s_n, 1u);
+        if (pos < (unsigned)kBandCap) buf[pos] = key;
+      }
     }
   }
   __syncthreads();
-  // At most K threads have a best key at or above the floor and each scans at
-  // most 8192 / kDetThreads = 32 cells, so s_n <= 32 K <= kBandCap.
-  int sn = min((int)s_n, kBandCap), sort_n = 32;
-  while (sort_n < sn) sort_n <<= 1;
-  bitonic_desc(buf, sort_n);
+  const int sn = min((int)s_n, kBandCap);
   uint64_t* pk = a.part_keys + ((long)f * a.bands + band) * 32;
-  if (tid < 32) pk[tid] = tid < K ? buf[tid] : 0;
+  if (sn <= 32) {
+    if (warp == 0) {
+      const uint64_t v = warp_sort_desc(lane < sn ? buf[lane] : 0, lane);
+      pk[lane] = lane < K ? v : 0;
+    }
+  } else {
+    int sort_n = 64;
+    while (sort_n < sn) sort_n <<= 1;
+    for (int i = sn + tid; i < sort_n; i += kDetThreads) buf[i] = 0;
+    __syncthreads();
+    bitonic_desc(buf, sort_n);
+    if (tid < 32) pk[tid] = tid < K ? buf[tid] : 0;
+  }
   if (tid == 0) atomicAdd(a.counts + f, s_cnt);
   __threadfence();
   __syncthreads();
@@ -240,26 +352,41 @@ detect_band_kernel(const float* __restrict__ src, ofdm_target* __restrict__ out,
   __syncthreads();
   if (!s_last) return;
 
-  // last CTA of the frame: merge the bands
+  // last CTA of the frame: merge the bands' sorted top-K lists
   __threadfence();
-  uint64_t* mbuf = reinterpret_cast<uint64_t*>(det_smem);
-  const int nk = a.bands * 32;
-  int mn = 32;
-  while (mn < nk) mn <<= 1;
   const volatile uint64_t* all = a.part_keys + (long)f * a.bands * 32;
-  for (int i = tid; i < mn; i += kDetThreads) mbuf[i] = i < nk ? all[i] : 0;
-  __syncthreads();
-  bitonic_desc(mbuf, mn);
-  if (tid < 32) {
-    const uint64_t key = lane < K ? mbuf[lane] : 0;
-    const bool valid = key != 0;
+  uint64_t key = 0;
+  if (a.bands <= 32) {
+    for (int i = tid; i < (a.bands << 5); i += kDetThreads) buf[i] = all[i];
+    __syncthreads();
+    if (warp == 0) {
+      int h = 0;
+      uint64_t head = lane < a.bands ? buf[lane << 5] : 0;
+      for (int r = 0; r < K; ++r) {
+        const uint64_t m = warp_max_key(head);
+        if (lane == r) key = m;
+        if (m != 0 && head == m) { ++h; head = h < K ? buf[(lane << 5) + h] : 0; }
+      }
+    }
+  } else {
+    uint64_t* mbuf = reinterpret_cast<uint64_t*>(det_smem);
+    const int nk = a.bands * 32;
+    int mn = 32;
+    while (mn < nk) mn <<= 1;
+    for (int i = tid; i < mn; i += kDetThreads) mbuf[i] = i < nk ? all[i] : 0;
+    __syncthreads();
+    bitonic_desc(mbuf, mn);
+    if (warp == 0) key = lane < K ? mbuf[lane] : 0;
+  }
+  if (warp == 0) {
+    const bool valid = lane < K && key != 0;
     const int nv = __popc(__ballot_sync(0xffffffffu, valid));
     const long g = a.out_idx ? (long)a.out_idx[f] : (long)f;  // index into the caller's outputs
     if (valid && out) {
       const uint32_t idx = ~(uint32_t)(key & 0xffffffffu);
       ofdm_target tg;
-      tg.r = (int32_t)(idx >> a.logMp);
-      tg.s = (int32_t)(idx & (uint32_t)(a.Mp - 1)) - a.Mp / 2;
+      tg.r = (int32_t)(idx >> logMp);
+      tg.s = (int32_t)(idx & (uint32_t)(Mp - 1)) - Mp / 2;
       tg.power = __uint_as_float((uint32_t)(key >> 32));
       tg.range_m = (float)tg.r * a.dd;
       tg.vel_mps = (float)tg.s * a.dv;
@@ -321,8 +448,22 @@ static cudaError_t launch_doppler_m(const float2* strip, float* map, float* pow,
                                          (int)smem);
     if (e != cudaSuccess) return e;
   }
+  // One wave of CTAs, each warp taking about the same number of rows.
+  static int per_sm = 0, sms = 0;
+  if (!per_sm) {
+    int dev = 0, n = 0, occ = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, doppler_kernel<MP>, 32 * kDopWarps, smem);
+    if (e != cudaSuccess) return e;
+    sms = n;
+    per_sm = occ > 0 ? occ : 1;
+  }
   const long tasks = (long)a.frames * a.rows;
-  const long blocks = (tasks + kDopWarps - 1) / kDopWarps;
+  const long slots = (long)sms * per_sm * kDopWarps;
+  const long rows_per_warp = (tasks + slots - 1) / slots;
+  const long blocks = (tasks + kDopWarps * rows_per_warp - 1) / (kDopWarps * rows_per_warp);
   doppler_kernel<MP><<<(unsigned)blocks, 32 * kDopWarps, smem, s>>>(strip, map, pow, a);
   return cudaGetLastError();
 }
@@ -362,14 +503,18 @@ cudaError_t launch_detect(const float* pow, ofdm_target* out, int32_t* n_out, ui
     ++*launches;
     median_kernel<<<a.frames, 1024, 0, s>>>(pow, a);
   }
-  const size_t tile = (size_t)(a.band_rows + 2) * a.Mp * sizeof(float);
+  // the scan reads up to 8192 / M' + 2 tile rows whatever the band's height
+  const int full_rows = 8192 / a.Mp > 1 ? 8192 / a.Mp : 1;
+  const size_t tile = (size_t)(full_rows + 2) * a.Mp * sizeof(float);
   int mn = 32;
   while (mn < a.bands * 32) mn <<= 1;
   const size_t smem = tile > (size_t)mn * sizeof(uint64_t) ? tile : (size_t)mn * sizeof(uint64_t);
-  cudaError_t e = cudaFuncSetAttribute(detect_band_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (a.logMp > 10) return cudaErrorInvalidValue;
+  auto kern = a.logMp <= 8 ? detect_band_kernel<0> : (a.logMp == 9 ? detect_band_kernel<1> : detect_band_kernel<2>);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   ++*launches;
-  detect_band_kernel<<<dim3(a.bands, a.frames), kDetThreads, smem, s>>>(pow, out, n_out, status, wstatus, a);
+  kern<<<dim3(a.bands, a.frames), kDetThreads, smem, s>>>(pow, out, n_out, status, wstatus, a);
   return cudaGetLastError();
 }
 

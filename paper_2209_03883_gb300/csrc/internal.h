@@ -67,6 +67,10 @@ struct DetectArgs {
   unsigned* counts;               // [frames] candidates found
   float* eta;                     // [frames] threshold from the median pre-pass
   int bands, band_rows;           // set by detect_bands()
+  // optional: the detection launch also zeroes map rows [z0, z0 + nz) of each frame
+  float* zmap = nullptr;          // the map, or null (no zeroing)
+  const long long* zmap_off = nullptr;  // per-frame float offset of the map, or null (f * zframe)
+  long zframe = 0, z_off = 0, z_floats = 0;  // floats per frame, z0 * M', nz * M' (multiples of 4)
 };
 
 // Row bands of the detection grid: about 8192 cells per CTA.

@@ -279,8 +279,12 @@ extern "C" int ofdm_radar_process_noalloc(const ofdm_radar_params* pin, const of
   e = launch_column(N, reinterpret_cast<const float2*>(Y), reinterpret_cast<const float2*>(X), strip, wstatus, ca,
                     s, &launches, &tk);
   st.ctr_base += tk;
-  if (e == cudaSuccess && out_map)
-    e = launch_zero_rows(out_map, frames, N, Mp, (row0 + rows) % N, N - rows, s, &launches);
+  if (out_map && rows < N) {  // the detection launch zeroes the rows outside the support
+    ta.zmap = out_map;
+    ta.zframe = (long)N * Mp;
+    ta.z_off = (long)((row0 + rows) % N) * Mp;
+    ta.z_floats = (long)(N - rows) * Mp;
+  }
   if (e == cudaSuccess) e = launch_doppler(Mp, strip, out_map, pow, da, s, &launches);
   if (e == cudaSuccess) e = launch_detect(pow, out_targets, n_targets, status, wstatus, ta, s, &launches);
   return e == cudaSuccess ? OFDM_OK : OFDM_ERR_CUDA;

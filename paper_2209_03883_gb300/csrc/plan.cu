@@ -495,6 +495,15 @@ DetectArgs detect_args(const ofdm_radar_plan* pl, int frames, int compact) {
   return a;
 }
 
+void set_zero_rows(const ofdm_radar_plan* pl, float* map, const long long* map_off, DetectArgs* a) {
+  if (!map || pl->nz <= 0) return;
+  a->zmap = map;
+  a->zmap_off = map_off;
+  a->zframe = (long)pl->Np * pl->Mp;
+  a->z_off = (long)pl->z0 * pl->Mp;
+  a->z_floats = (long)pl->nz * pl->Mp;
+}
+
 bool bad_frames(const ofdm_radar_plan* pl, int frames) { return frames < 1 || frames > pl->p.max_frames; }
 
 int finish(ofdm_radar_plan* pl, int launches, cudaError_t e) {
@@ -514,18 +523,15 @@ cudaError_t run_chain(ofdm_radar_plan* pl, const float2* Y, const float2* X, int
     pl->ctr_base[pl->ctr_slot] += tk;
   }
   if (e != cudaSuccess) return e;
-  if (map && pl->nz > 0) {
-    ScopedTimer tm(pl, s, K_ZERO);
-    e = ofdm::launch_zero_rows(map, frames, pl->Np, pl->Mp, pl->z0, pl->nz, s, launches);
-    if (e != cudaSuccess) return e;
-  }
   {
     ScopedTimer tm(pl, s, K_DOPPLER);
     e = ofdm::launch_doppler(pl->Mp, pl->d_strip, map, pl->d_pow, doppler_args(pl, frames), s, launches);
   }
   if (e != cudaSuccess) return e;
   ScopedTimer tm(pl, s, K_DETECT);
-  return ofdm::launch_detect(pl->d_pow, tg, nt, st, pl->d_wstatus, detect_args(pl, frames, 1), s, launches);
+  DetectArgs ta = detect_args(pl, frames, 1);
+  set_zero_rows(pl, map, nullptr, &ta);   // the detection launch zeroes the rows outside the support
+  return ofdm::launch_detect(pl->d_pow, tg, nt, st, pl->d_wstatus, ta, s, launches);
 }
 
 }  // namespace
@@ -781,16 +787,13 @@ cudaError_t run_group(BatchGroup& g, const float2* Y, const float2* X, float* ma
   unsigned long long tk = 0;
   e = ofdm::launch_column(g.N, Y, X, pl->d_strip, pl->d_wstatus, ca, s, launches, &tk);
   if (e != cudaSuccess) return e;
-  if (map) {
-    e = ofdm::launch_zero_rows(map, g.n, pl->Np, pl->Mp, pl->z0, pl->nz, s, launches, g.d_map_off);
-    if (e != cudaSuccess) return e;
-  }
   DopplerArgs da = doppler_args(pl, g.n);
   da.map_off = g.d_map_off;
   e = ofdm::launch_doppler(pl->Mp, pl->d_strip, map, pl->d_pow, da, s, launches);
   if (e != cudaSuccess) return e;
   DetectArgs ta = detect_args(pl, g.n, 1);
   ta.out_idx = g.d_idx;
+  set_zero_rows(pl, map, g.d_map_off, &ta);
   return ofdm::launch_detect(pl->d_pow, tg, nt, st, pl->d_wstatus, ta, s, launches);
 }
 
