@@ -133,6 +133,8 @@ __global__ void zero_rows_kernel(float* __restrict__ map, int frames, long frame
 // median_kernel: threshold mode without a given noise level -- the lower
 // median of P over the scanned rows (radix select on the float bits).
 constexpr int kDetThreads = 256;
+constexpr int kCells = kDetBandCells / kDetThreads;   // cells scanned per thread (16)
+static_assert(kCells <= 32 && (kCells & (kCells - 1)) == 0, "one candidate bit per cell");
 constexpr int kBandCap = 1024;          // keys kept per band before compaction
 
 __device__ __forceinline__ float det_value(const float* base, const DetectArgs& a, int ri, int c) {
@@ -198,19 +200,35 @@ __device__ __forceinline__ uint64_t warp_max_key(uint64_t v) {
   return ((uint64_t)mh << 32) | ml;
 }
 
+// Merge of up to 32 key lists, each sorted descending with its first K
+// entries valid, list j at src[32 j]: lane r < K receives the r-th largest
+// key of all lists (0 when fewer exist).
+template <typename P>
+__device__ __forceinline__ uint64_t warp_merge_lists(P src, int nlists, int K, int lane) {
+  int h = 0;
+  uint64_t head = lane < nlists ? src[lane << 5] : 0, out = 0;
+  for (int r = 0; r < K; ++r) {
+    const uint64_t m = warp_max_key(head);
+    if (lane == r) out = m;
+    if (m != 0 && head == m) { ++h; head = h < K ? src[(lane << 5) + h] : 0; }
+  }
+  return out;
+}
+
 // LOGC = log2 of the columns each thread scans: 0 for M' <= 256, 1 for 512,
-// 2 for 1024 (the band always holds 8192 / M' rows, 32 cells per thread).
+// 2 for 1024 (the band always holds kDetBandCells / M' rows, kCells cells
+// per thread).
 template <int LOGC>
 __global__ void __launch_bounds__(kDetThreads)
 detect_band_kernel(const float* __restrict__ src, ofdm_target* __restrict__ out, int32_t* __restrict__ n_out,
                    uint32_t* __restrict__ status, uint32_t* __restrict__ wstatus, DetectArgs a) {
-  constexpr int C = 1 << LOGC, NR = 32 >> LOGC;
+  constexpr int C = 1 << LOGC, NR = kCells >> LOGC;
   extern __shared__ __align__(16) unsigned char det_smem[];
   __shared__ uint64_t buf[kBandCap];
   __shared__ unsigned s_n, s_cnt;
   __shared__ uint64_t s_floor;
   __shared__ int s_last;
-  float* tile = reinterpret_cast<float*>(det_smem);  // (8192 / M' + 2) rows of M'
+  float* tile = reinterpret_cast<float*>(det_smem);  // (kDetBandCells / M' + 2) rows of M'
   const int band = blockIdx.x, f = blockIdx.y;
   if (a.frame_mask && !a.frame_mask[f]) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -241,7 +259,7 @@ detect_band_kernel(const float* __restrict__ src, ofdm_target* __restrict__ out,
   if (tid == 0) { s_n = 0; s_cnt = 0; }
 
   // The map rows outside the support are zero: this CTA's share of its
-  // frame, one streaming store per scanned row and the rest after the scan.
+  // frame, two streaming stores per scanned row and the rest after the scan.
   float4* zp = nullptr;
   long zj = 0, zj1 = 0;
   if (a.zmap) {
@@ -259,7 +277,7 @@ detect_band_kernel(const float* __restrict__ src, ofdm_target* __restrict__ out,
   // Bit q NR + k of `mine` marks a local maximum at band row i0 + k.  Rows at
   // or past tr read tile rows that were not staged and are masked out.
   const int c0 = LOGC == 0 ? (tid & (Mp - 1)) : tid;
-  const int i0 = LOGC == 0 ? ((tid >> logMp) << 5) : 0;
+  const int i0 = LOGC == 0 ? (tid >> logMp) * NR : 0;
   const uint32_t rbase = (uint32_t)(a.row0 + t0);
   uint32_t mine = 0;
   unsigned cnt = 0;
@@ -292,6 +310,7 @@ detect_band_kernel(const float* __restrict__ src, ofdm_target* __restrict__ out,
       up3 = fmaxf(mid2, mc);
       ml = dl; mc = dc; mr = dr;
       if (zj < zj1) { __stcs(zp + zj, zero4); zj += kDetThreads; }
+      if (zj < zj1) { __stcs(zp + zj, zero4); zj += kDetThreads; }
     }
   }
   for (; zj < zj1; zj += kDetThreads) __stcs(zp + zj, zero4);
@@ -301,21 +320,24 @@ detect_band_kernel(const float* __restrict__ src, ofdm_target* __restrict__ out,
   // Floor = the K-th best of the 256 per-thread best keys: each warp sorts its
   // 32, warp 0 merges the eight sorted lists for K steps.  Every key of the
   // band's top K is at or above it, and at most K threads hold keys there.
-  buf[tid] = warp_sort_desc(best, lane);
-  __syncthreads();
-  if (warp == 0) {
-    int h = 0;
-    uint64_t head = lane < kDetThreads / 32 ? buf[lane << 5] : 0, m = 0;
+  if (K <= 8) {  // the warp's K best, largest first, by repeated maximum
+    uint64_t v = best;
     for (int r = 0; r < K; ++r) {
-      m = warp_max_key(head);
-      if (m == 0) break;                              // fewer than K threads found a maximum
-      if (head == m) { ++h; head = h < 32 ? buf[(lane << 5) + h] : 0; }
+      const uint64_t m = warp_max_key(v);
+      if (lane == 0) buf[(warp << 5) + r] = m;
+      if (v == m) v = 0;
     }
-    if (lane == 0) s_floor = m;
+  } else {
+    buf[tid] = warp_sort_desc(best, lane);
+  }
+  __syncthreads();
+  if (warp == 0) {  // 0 when fewer than K threads found a maximum
+    const uint64_t m = warp_merge_lists(buf, kDetThreads / 32, K, lane);
+    if (lane == K - 1) s_floor = m;
   }
   __syncthreads();
   const uint64_t floor_key = s_floor;
-  // keys at or above the floor (at most 32 K <= kBandCap)
+  // keys at or above the floor (at most kCells K <= kBandCap)
   if (best != 0 && best >= floor_key) {
     for (uint32_t m = mine; m; m &= m - 1) {
       const int b = __ffs(m) - 1;
@@ -352,31 +374,23 @@ detect_band_kernel(const float* __restrict__ src, ofdm_target* __restrict__ out,
   __syncthreads();
   if (!s_last) return;
 
-  // last CTA of the frame: merge the bands' sorted top-K lists
+  // last CTA of the frame: merge the bands' sorted top-K lists (stride 32),
+  // directly for up to 32 bands, else per group of 32 bands and then the groups
   __threadfence();
   const volatile uint64_t* all = a.part_keys + (long)f * a.bands * 32;
   uint64_t key = 0;
   if (a.bands <= 32) {
     for (int i = tid; i < (a.bands << 5); i += kDetThreads) buf[i] = all[i];
     __syncthreads();
-    if (warp == 0) {
-      int h = 0;
-      uint64_t head = lane < a.bands ? buf[lane << 5] : 0;
-      for (int r = 0; r < K; ++r) {
-        const uint64_t m = warp_max_key(head);
-        if (lane == r) key = m;
-        if (m != 0 && head == m) { ++h; head = h < K ? buf[(lane << 5) + h] : 0; }
-      }
-    }
+    if (warp == 0) key = warp_merge_lists(buf, a.bands, K, lane);
   } else {
-    uint64_t* mbuf = reinterpret_cast<uint64_t*>(det_smem);
-    const int nk = a.bands * 32;
-    int mn = 32;
-    while (mn < nk) mn <<= 1;
-    for (int i = tid; i < mn; i += kDetThreads) mbuf[i] = i < nk ? all[i] : 0;
+    const int groups = (a.bands + 31) >> 5;             // at most 32 (bands <= 1024)
+    for (int g = warp; g < groups; g += kDetThreads / 32) {
+      const uint64_t v = warp_merge_lists(all + ((long)g << 10), min(32, a.bands - (g << 5)), K, lane);
+      buf[(g << 5) + lane] = lane < K ? v : 0;
+    }
     __syncthreads();
-    bitonic_desc(mbuf, mn);
-    if (warp == 0) key = lane < K ? mbuf[lane] : 0;
+    if (warp == 0) key = warp_merge_lists(buf, groups, K, lane);
   }
   if (warp == 0) {
     const bool valid = lane < K && key != 0;
@@ -503,13 +517,11 @@ cudaError_t launch_detect(const float* pow, ofdm_target* out, int32_t* n_out, ui
     ++*launches;
     median_kernel<<<a.frames, 1024, 0, s>>>(pow, a);
   }
-  // the scan reads up to 8192 / M' + 2 tile rows whatever the band's height
-  const int full_rows = 8192 / a.Mp > 1 ? 8192 / a.Mp : 1;
+  // the scan reads up to kDetBandCells / M' + 2 tile rows whatever the band's height
+  const int full_rows = kDetBandCells / a.Mp > 1 ? kDetBandCells / a.Mp : 1;
   const size_t tile = (size_t)(full_rows + 2) * a.Mp * sizeof(float);
-  int mn = 32;
-  while (mn < a.bands * 32) mn <<= 1;
-  const size_t smem = tile > (size_t)mn * sizeof(uint64_t) ? tile : (size_t)mn * sizeof(uint64_t);
-  if (a.logMp > 10) return cudaErrorInvalidValue;
+  const size_t smem = tile;
+  if (a.logMp > 10 || a.bands > 1024) return cudaErrorInvalidValue;
   auto kern = a.logMp <= 8 ? detect_band_kernel<0> : (a.logMp == 9 ? detect_band_kernel<1> : detect_band_kernel<2>);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

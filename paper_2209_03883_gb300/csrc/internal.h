@@ -73,9 +73,10 @@ struct DetectArgs {
   long zframe = 0, z_off = 0, z_floats = 0;  // floats per frame, z0 * M', nz * M' (multiples of 4)
 };
 
-// Row bands of the detection grid: about 8192 cells per CTA.
+// Row bands of the detection grid: kDetBandCells cells per CTA.
+constexpr int kDetBandCells = 4096;
 inline void detect_bands(int rows, int Mp, int* band_rows, int* bands) {
-  int br = 8192 / Mp;
+  int br = kDetBandCells / Mp;
   if (br < 1) br = 1;
   if (br > rows) br = rows;
   *band_rows = br;

@@ -41,8 +41,8 @@ constexpr size_t kOffStatus = align256(kOffWl + kMaxM * sizeof(float));     // u
 constexpr size_t kOffStrip = align256(kOffStatus + kNoallocMaxFrames * sizeof(uint32_t));
 constexpr size_t kOffPow = align256(kOffStrip + (size_t)kNoallocMaxCells * sizeof(float2));
 constexpr size_t kOffCtr = align256(kOffPow + (size_t)kNoallocMaxCells * sizeof(float));  // ticket counter
-// detection workspace: frames * bands <= 2^20 / 8192 + frames (see detect_bands)
-constexpr size_t kMaxBandSlots = (kNoallocMaxCells / 8192) + kNoallocMaxFrames;
+// detection workspace: frames * bands <= 2^20 / kDetBandCells + frames (see detect_bands)
+constexpr size_t kMaxBandSlots = (kNoallocMaxCells / kDetBandCells) + kNoallocMaxFrames;
 constexpr size_t kOffDetKeys = align256(kOffCtr + sizeof(unsigned long long));
 constexpr size_t kOffDetTick = align256(kOffDetKeys + kMaxBandSlots * 32 * sizeof(uint64_t));
 constexpr size_t kOffEta = align256(kOffDetTick + 2 * kNoallocMaxFrames * sizeof(unsigned));
