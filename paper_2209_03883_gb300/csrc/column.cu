@@ -276,6 +276,9 @@ column_pipe_kernel(const float2* __restrict__ Y, const float2* __restrict__ X, f
       // (instruction-cache footprint): even h reads the registers and writes
       // the transposed exchange, odd h reads it back and applies the
       // exp(+2 pi i lane r / 1024) twiddles (pass-1 table, u = lane).
+      // DFT-CE keeps taps n = lane + 32 q < L_cp only, so for L_cp <= 128 the
+      // last half-pass needs outputs q < 4 alone (pruned transform).
+      const bool prune4 = a.L_cp <= 128;
 #pragma unroll 1
       for (int h = 2 * pass0; h < 4; ++h) {
         if (h & 1) {
@@ -283,6 +286,13 @@ column_pipe_kernel(const float2* __restrict__ Y, const float2* __restrict__ X, f
           for (int r = 0; r < 32; ++r) v[r] = sa[pad32(lane + 32 * r)];
 #pragma unroll
           for (int r = 1; r < 32; ++r) v[r] = cmul(v[r], tw1[r * 32 + lane]);
+        }
+        if (h == 3 && prune4) {
+          float2 y[4];
+          pruned_dft<32, 4, 0, 1, +1>(v, y);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) v[q] = y[q];
+          break;
         }
         dft_reg<32, +1>(v);
         if (!(h & 1)) {

@@ -121,14 +121,36 @@ __device__ __forceinline__ float2 tw_const_mul(float2 b) {
   }
 }
 
+// Radix-2 butterflies (a, b) -> (a + w b, a - w b), w = exp(DIR 2 pi i K / LEN).
+// A twiddle other than 1 or +-i is applied in the FMA form of Linzer and
+// Feig ("Modified FFTs for fused multiply-add architectures", Math. Comp.
+// 1993): with w = c + i s and |c| >= |s|, w b = c (b.x - t b.y, b.y + t b.x),
+// t = s / c, so both outputs take six FMAs instead of eight operations
+// (|s| > |c|: w b = s (t b.x - b.y, b.x + t b.y), t = c / s).
 template <int R, int LEN, int K, int DIR>
 __device__ __forceinline__ void bfly_k(float2* v) {
+  constexpr bool kTrivial = K == 0 || 4 * K == LEN;
+  constexpr double cd = cx_cos(2.0 * kPi * K / LEN), sd = DIR * cx_sin(2.0 * kPi * K / LEN);
+  constexpr bool kCosMajor = (cd < 0 ? -cd : cd) >= (sd < 0 ? -sd : sd);
 #pragma unroll
   for (int i = 0; i < R; i += LEN) {
     const float2 a = v[i + K];
-    const float2 b = tw_const_mul<LEN, K, DIR>(v[i + K + LEN / 2]);
-    v[i + K] = cadd(a, b);
-    v[i + K + LEN / 2] = csub(a, b);
+    const float2 b = v[i + K + LEN / 2];
+    if constexpr (kTrivial) {
+      const float2 wb = tw_const_mul<LEN, K, DIR>(b);
+      v[i + K] = cadd(a, wb);
+      v[i + K + LEN / 2] = csub(a, wb);
+    } else if constexpr (kCosMajor) {
+      constexpr float t = (float)(sd / cd), c = (float)cd;
+      const float u = __fmaf_rn(-t, b.y, b.x), w = __fmaf_rn(t, b.x, b.y);
+      v[i + K] = make_float2(__fmaf_rn(c, u, a.x), __fmaf_rn(c, w, a.y));
+      v[i + K + LEN / 2] = make_float2(__fmaf_rn(-c, u, a.x), __fmaf_rn(-c, w, a.y));
+    } else {
+      constexpr float t = (float)(cd / sd), sn = (float)sd;
+      const float u = __fmaf_rn(t, b.x, -b.y), w = __fmaf_rn(t, b.y, b.x);
+      v[i + K] = make_float2(__fmaf_rn(sn, u, a.x), __fmaf_rn(sn, w, a.y));
+      v[i + K + LEN / 2] = make_float2(__fmaf_rn(-sn, u, a.x), __fmaf_rn(-sn, w, a.y));
+    }
   }
 }
 template <int R, int LEN, int DIR, int... Ks>
@@ -158,6 +180,43 @@ __device__ __forceinline__ void dft_reg(float2* v) {
   if constexpr (R > 1) {
     brev_perm<R>(v, std::make_integer_sequence<int, R>{});
     dit_stages<R, DIR, 2>(v);
+  }
+}
+
+// ---------------------------------------------------------------- output-pruned DFT
+// a + w b with w = exp(DIR 2 pi i K / LEN) a compile-time twiddle.
+template <int LEN, int K, int DIR>
+__device__ __forceinline__ float2 cmac_const(float2 a, float2 b) {
+  if constexpr (K == 0 || 4 * K == LEN) {
+    return cadd(a, tw_const_mul<LEN, K, DIR>(b));
+  } else {
+    constexpr float c = (float)cx_cos(2.0 * kPi * K / LEN);
+    constexpr float s = (float)(DIR * cx_sin(2.0 * kPi * K / LEN));
+    return make_float2(__fmaf_rn(c, b.x, __fmaf_rn(-s, b.y, a.x)), __fmaf_rn(c, b.y, __fmaf_rn(s, b.x, a.y)));
+  }
+}
+template <int L, int DIR, int... Ks>
+__device__ __forceinline__ void pruned_combine(float2* y, const float2* e, const float2* o,
+                                               std::integer_sequence<int, Ks...>) {
+  ((y[Ks] = cmac_const<L, Ks, DIR>(e[Ks], o[Ks])), ...);
+}
+// The first QO outputs y[k] = sum_m x[OFF + STRIDE m] exp(DIR 2 pi i m k / L),
+// k < QO <= L, by radix-2 decimation in time that drops the outputs it does
+// not need: X[k] = E[k] + exp(DIR 2 pi i k / L) O[k] for k < QO <= L / 2.
+template <int L, int QO, int OFF, int STRIDE, int DIR>
+__device__ __forceinline__ void pruned_dft(const float2* x, float2* y) {
+  if constexpr (L <= QO) {
+    float2 t[L];
+#pragma unroll
+    for (int m = 0; m < L; ++m) t[m] = x[OFF + STRIDE * m];
+    dft_reg<L, DIR>(t);
+#pragma unroll
+    for (int k = 0; k < L; ++k) y[k] = t[k];
+  } else {
+    float2 e[QO], o[QO];
+    pruned_dft<L / 2, QO, OFF, 2 * STRIDE, DIR>(x, e);
+    pruned_dft<L / 2, QO, OFF + STRIDE, 2 * STRIDE, DIR>(x, o);
+    pruned_combine<L, DIR>(y, e, o, std::make_integer_sequence<int, QO>{});
   }
 }
 

@@ -174,6 +174,12 @@ VARIANTS = [
     ("n4096_m16", dict(N=4096, M=16, L_cp=512, window=o.WINDOW_RECT)),
     ("m32_direct", dict(N=128, M=32, L_cp=16)),
     ("lcp_1", dict(N=64, M=16, L_cp=1, window=o.WINDOW_HANN)),
+    # N = 1024: the last DFT-CE half-pass is output-pruned for L_cp <= 128 only
+    ("n1024_lcp200", dict(N=1024, M=32, L_cp=200)),
+    ("n1024_lcp5_hamming", dict(N=1024, M=32, L_cp=5, window=o.WINDOW_HAMMING)),
+    # full support: 1024 rows x 256 bins = 64 detection bands (two-level merge)
+    ("n1024_full_rect", dict(N=1024, M=256, L_cp=1024, window=o.WINDOW_RECT)),
+    ("m512", dict(N=256, M=512, L_cp=32)),
 ]
 
 
