@@ -110,9 +110,11 @@ int ofdm_radar_process(ofdm_radar_plan* plan, const ofdm_c32* Y, const ofdm_c32*
 
 /* Same as ofdm_radar_process with HOST buffers (pinned memory gives
  * asynchronous, overlapped copies).  The plan allocates device staging for
- * max_frames on the first call; copies run in chunks overlapped with the
- * kernels on four internal streams ordered after `stream`; the call returns
- * after everything, copies included, has finished.  NULL outputs are skipped. */
+ * max_frames on the first call.  The frames go in up to 8 chunks through
+ * three internal streams ordered after `stream`: uploads back to back on
+ * one, each chunk's kernels on a second once its upload is done, and its
+ * results back on a third.  The call returns after everything, copies
+ * included, has finished.  NULL outputs are skipped. */
 int ofdm_radar_process_host(ofdm_radar_plan* plan, const ofdm_c32* Y_host,
                             const ofdm_c32* X_host, int32_t frames, float* map_host,
                             ofdm_target* targets_host, int32_t* n_targets_host,

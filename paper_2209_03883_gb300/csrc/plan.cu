@@ -15,6 +15,8 @@ using ofdm::DetectArgs;
 using ofdm::DopplerArgs;
 using ofdm::ZctArgs;
 
+constexpr int kHostChunks = 8;  // frame chunks of the host-buffer pipeline
+
 struct ofdm_radar_plan {
   ofdm_radar_params p;
   int Np, Mp;
@@ -35,8 +37,9 @@ struct ofdm_radar_plan {
   float* d_eta = nullptr;
   int det_bands = 0;
   // Ticket counters of the dynamically scheduled column kernel: slot 0 for
-  // calls on the caller's stream, slots 1-4 for the four streams of the host
-  // pipeline (launches that may run concurrently need separate counters).
+  // calls on the caller's stream, slot 1 for the kernel stream of the host
+  // pipeline (launches that may run concurrently need separate counters);
+  // slots 2-4 are spare.
   unsigned long long* d_ctr = nullptr;
   unsigned long long ctr_base[1 + 4] = {0, 0, 0, 0, 0};
   int ctr_slot = 0;
@@ -47,8 +50,8 @@ struct ofdm_radar_plan {
   ofdm_target* d_tg = nullptr;
   int32_t* d_nt = nullptr;
   uint32_t* d_st = nullptr;
-  cudaStream_t hs[4] = {nullptr, nullptr, nullptr, nullptr};
-  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  cudaStream_t hs[3] = {nullptr, nullptr, nullptr};   // uploads, kernels, downloads
+  cudaEvent_t ev[2 + 2 * kHostChunks] = {};            // fork, join, per-chunk upload / kernel done
   int last_launches = 0;
   // learned proposal workspace (ofdm_radar_learned_prepare)
   int Hc = 0, Mc = 0;
@@ -618,31 +621,37 @@ int ofdm_radar_process_host(ofdm_radar_plan* pl, const ofdm_c32* Yh, const ofdm_
     if (e == cudaSuccess) e = dalloc(&pl->d_tg, (size_t)p.max_targets * p.max_frames);
     if (e == cudaSuccess) e = dalloc(&pl->d_nt, (size_t)p.max_frames);
     if (e == cudaSuccess) e = dalloc(&pl->d_st, (size_t)p.max_frames);
-    for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&pl->hs[i], cudaStreamNonBlocking);
-    for (int i = 0; i < 5 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&pl->ev[i], cudaEventDisableTiming);
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&pl->hs[i], cudaStreamNonBlocking);
+    for (int i = 0; i < 2 + 2 * kHostChunks && e == cudaSuccess; ++i)
+      e = cudaEventCreateWithFlags(&pl->ev[i], cudaEventDisableTiming);
     if (e != cudaSuccess) {
       cudaFree(pl->d_Y); pl->d_Y = nullptr;
       cudaGetLastError();
       return e == cudaErrorMemoryAllocation ? OFDM_ERR_NO_MEMORY : cuda_fail(e);
     }
   }
-  cudaStream_t s0 = (cudaStream_t)stream;
-  // Chunks of frames rotate over four streams so that the copies of one
-  // chunk (in both directions) overlap the kernels and copies of the others.
-  const int chunk = frames >= 16 ? (frames + 7) / 8 : (frames >= 4 ? (frames + 3) / 4 : frames);
+  // Three-stage pipeline over chunks of frames.  All uploads run back to back
+  // on one stream (the host link is the bottleneck); chunk k's kernels start
+  // when its upload is done, and its results go back on a third stream while
+  // later chunks are still uploading or computing.
+  cudaStream_t s0 = (cudaStream_t)stream, up = pl->hs[0], comp = pl->hs[1], down = pl->hs[2];
+  cudaEvent_t* up_done = pl->ev + 2;
+  cudaEvent_t* comp_done = pl->ev + 2 + kHostChunks;
+  const int chunk = (frames + kHostChunks - 1) / kHostChunks;
   e = cudaEventRecord(pl->ev[0], s0);
-  for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(pl->hs[i], pl->ev[0], 0);
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(pl->hs[i], pl->ev[0], 0);
   int launches = 0, k = 0;
   for (int f0 = 0; f0 < frames && e == cudaSuccess; f0 += chunk, ++k) {
     const int nf = frames - f0 < chunk ? frames - f0 : chunk;
-    cudaStream_t s = pl->hs[k & 3];
     const size_t g0 = grid * f0, gn = grid * nf;
-    e = cudaMemcpyAsync(pl->d_Y + g0, Yh + g0, gn * sizeof(float2), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(pl->d_X + g0, Xh + g0, gn * sizeof(float2), cudaMemcpyHostToDevice, s);
+    e = cudaMemcpyAsync(pl->d_Y + g0, Yh + g0, gn * sizeof(float2), cudaMemcpyHostToDevice, up);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(pl->d_X + g0, Xh + g0, gn * sizeof(float2), cudaMemcpyHostToDevice, up);
+    if (e == cudaSuccess) e = cudaEventRecord(up_done[k], up);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(comp, up_done[k], 0);
     if (e != cudaSuccess) break;
     // The chunk uses its own slice of the workspace (frame offset f0).
     ofdm_radar_plan view = *pl;
-    view.ctr_slot = 1 + (k & 3);
+    view.ctr_slot = 1;
     view.d_strip = pl->d_strip + (size_t)f0 * pl->rows * p.M;
     view.d_pow = pl->d_pow + (size_t)f0 * pl->rows * pl->Mp;
     view.d_wstatus = pl->d_wstatus + f0;
@@ -650,24 +659,25 @@ int ofdm_radar_process_host(ofdm_radar_plan* pl, const ofdm_c32* Yh, const ofdm_
     view.d_dettick = pl->d_dettick + f0;  // tickets[f0..]; counts stay max_frames further on
     view.d_eta = pl->d_eta + f0;
     e = run_chain(&view, pl->d_Y + g0, pl->d_X + g0, nf, map_h ? pl->d_map + mapn * f0 : nullptr,
-                  pl->d_tg + (size_t)p.max_targets * f0, pl->d_nt + f0, pl->d_st + f0, s, &launches);
-    pl->ctr_base[view.ctr_slot] = view.ctr_base[view.ctr_slot];
+                  pl->d_tg + (size_t)p.max_targets * f0, pl->d_nt + f0, pl->d_st + f0, comp, &launches);
+    pl->ctr_base[1] = view.ctr_base[1];
+    if (e == cudaSuccess) e = cudaEventRecord(comp_done[k], comp);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(down, comp_done[k], 0);
     if (e != cudaSuccess) break;
     if (map_h)
       e = cudaMemcpyAsync(map_h + mapn * f0, pl->d_map + mapn * f0, mapn * nf * sizeof(float),
-                          cudaMemcpyDeviceToHost, s);
+                          cudaMemcpyDeviceToHost, down);
     if (e == cudaSuccess && tg_h)
       e = cudaMemcpyAsync(tg_h + (size_t)p.max_targets * f0, pl->d_tg + (size_t)p.max_targets * f0,
-                          (size_t)p.max_targets * nf * sizeof(ofdm_target), cudaMemcpyDeviceToHost, s);
+                          (size_t)p.max_targets * nf * sizeof(ofdm_target), cudaMemcpyDeviceToHost, down);
     if (e == cudaSuccess && nt_h)
-      e = cudaMemcpyAsync(nt_h + f0, pl->d_nt + f0, nf * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+      e = cudaMemcpyAsync(nt_h + f0, pl->d_nt + f0, nf * sizeof(int32_t), cudaMemcpyDeviceToHost, down);
     if (e == cudaSuccess && st_h)
-      e = cudaMemcpyAsync(st_h + f0, pl->d_st + f0, nf * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+      e = cudaMemcpyAsync(st_h + f0, pl->d_st + f0, nf * sizeof(uint32_t), cudaMemcpyDeviceToHost, down);
   }
-  for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
-    e = cudaEventRecord(pl->ev[1 + i], pl->hs[i]);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(s0, pl->ev[1 + i], 0);
-  }
+  // the downloads come last in every chunk's chain: joining them joins all three streams
+  if (e == cudaSuccess) e = cudaEventRecord(pl->ev[1], down);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s0, pl->ev[1], 0);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s0);
   return finish(pl, launches, e);
 }
