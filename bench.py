@@ -512,6 +512,31 @@ def run_ours(args):
     h2d = Yh.numel() * 8 + Xh.numel() * 8
     d2h = mh.numel() * 4 + th.numel() + nh.numel() * 4 + sh.numel() * 4
 
+    # The host link alone: the same bytes as one end-to-end step, uploads on one
+    # stream and the map download on another, no kernels (the floor of e2e).
+    dY, dX = torch.empty_like(Yh, device="cuda"), torch.empty_like(Xh, device="cuda")
+    dM = torch.empty_like(mh, device="cuda")
+    s_up, s_dn = torch.cuda.Stream(), torch.cuda.Stream()
+    link_ms = []
+    for _ in range(4):
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        s_up.wait_event(ev0)
+        s_dn.wait_event(ev0)
+        with torch.cuda.stream(s_up):
+            dY.copy_(Yh, non_blocking=True)
+            dX.copy_(Xh, non_blocking=True)
+        with torch.cuda.stream(s_dn):
+            mh.copy_(dM, non_blocking=True)
+        torch.cuda.current_stream().wait_stream(s_up)
+        torch.cuda.current_stream().wait_stream(s_dn)
+        ev1.record()
+        ev1.synchronize()
+        link_ms.append(ev0.elapsed_time(ev1))
+    link_floor = FRAMES / (min(link_ms) / 1e3)
+    del dY, dX, dM
+
     # detection sanity on the last step's output (targets within one bin)
     tv = radar.targets_view(th, FRAMES, plan.max_targets)
     hits = 0
@@ -536,7 +561,9 @@ def run_ours(args):
         "kernel_ms": kernel_ms,
         "gpu_launches": launches_per_step * args.steps,
         "e2e": {"value": e2e_val, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "entry": "ofdm_radar_process_host (pinned host buffers, map + targets read back)"},
+                "entry": "ofdm_radar_process_host (pinned host buffers, map + targets read back)",
+                "link_floor": {"value": world * link_floor, "unit": "frames/s",
+                               "how": "the step's Y, X upload and map download as plain copies, no kernels"}},
         "clocks": clocks,
         "detection_hits": f"{hits}/{5 * FRAMES} targets within one bin",
     }
