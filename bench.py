@@ -402,6 +402,18 @@ def extra_learned(radar, torch, dev, stream, steps, train_steps=150, n_eval=16):
                                                    po["status"], stream))
     ms_l = t_of(lambda: radar.ofdm_radar_process_learned(plan, tr.theta, Y, A, n_eval, thr, 256, lo["targets"],
                                                            lo["n_targets"], lo["status"], stream))
+    # per-stage event times of one more call of each form (the library's timing hook)
+    stage_ms = {}
+    for name, fn in (("plain", lambda: radar.ofdm_radar_process(plan, Y, A, n_eval, None, po["targets"],
+                                                                 po["n_targets"], po["status"], stream)),
+                     ("learned", lambda: radar.ofdm_radar_process_learned(plan, tr.theta, Y, A, n_eval, thr, 256,
+                                                                          lo["targets"], lo["n_targets"],
+                                                                          lo["status"], stream))):
+        plan.timing_enable(True)
+        fn()
+        torch.cuda.synchronize()
+        plan.timing_enable(False)
+        stage_ms[name] = {k: round(v[0], 4) for k, v in plan.timing_read().items() if v[1]}
     K = cfg.detect_k
     hp = _hits(radar.targets_view(po["targets"], n_eval, K), po["n_targets"].cpu().numpy(), truth, M)
     hl = _hits(radar.targets_view(lo["targets"], n_eval, K), lo["n_targets"].cpu().numpy(), truth, M)
@@ -412,6 +424,7 @@ def extra_learned(radar, torch, dev, stream, steps, train_steps=150, n_eval=16):
            "learned": {"value": n_eval / (ms_l / 1e3), "unit": "frames/s", "ms_per_step": ms_l,
                        "target_hits": f"{hl}/{32 * n_eval}", "fallback_frames": fb, "logit_threshold": thr},
            "gain": ms_p / ms_l,
+           "stage_ms": stage_ms,
            "training": {"steps": train_steps, "frames_per_step": B, "seconds": train_s,
                         "final_loss": float(loss)}}
     plan.close()
@@ -552,7 +565,7 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "frames_per_step": FRAMES, "N": CFG.N, "M": CFG.M,
                    "L_cp": CFG.L_cp, "precision": "fp32", "parallelism": f"replicas x{world} (frames)",
                    "l2": f"inputs {2 * FRAMES * CFG.N * CFG.M * 8 / 1e6:.0f} MB per step > 129 MB L2; no flush"},
-        "roofline": {"bound": "hbm", "kernel": "column_kernel<1024>", "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "hbm", "kernel": "column_pipe_kernel<1024>", "achieved": achieved, "peak": peak,
                      "peak_source": f"{peak_kind} hbm_gbs", "unit": "GB/s", "frac": achieved / peak,
                      "traffic": captured_traffic(),
                      "algorithmic_bytes_per_launch": COLUMN_BYTES_PER_FRAME * FRAMES,

@@ -296,7 +296,10 @@ int ofdm_radar_last_launch_count(const ofdm_radar_plan* plan);
  * launching stream (up to 4096 launches, then recording stops); enable = 0
  * stops.  ofdm_radar_timing_read waits for the recorded events, writes up to
  * `n` entries of per-kernel-kind totals (milliseconds) and launch counts in
- * the order column, zero_rows, doppler, detect, zct, and clears the record.
+ * the order column, zero_rows, doppler, detect, zct, coarse, cnn, refine
+ * (the last three from ofdm_radar_process_learned; cnn spans its three
+ * layers, refine its select, candidate and merge kernels), and clears the
+ * record.
  * Returns the number of kinds written. */
 int ofdm_radar_timing_enable(ofdm_radar_plan* plan, int32_t enable);
 int ofdm_radar_timing_read(ofdm_radar_plan* plan, float* total_ms, int32_t* launches, int32_t n);

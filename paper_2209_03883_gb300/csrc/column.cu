@@ -336,48 +336,103 @@ column_pipe_kernel(const float2* __restrict__ Y, const float2* __restrict__ X, f
   cp_async_wait<0>();
 }
 
-// ---------------------------------------------------------------- N >= 2048: multi-warp groups
+// ---------------------------------------------------------------- N >= 2048: pipelined multi-warp groups
+// The same ring-of-three-rows pipeline as above, with a symbol owned by a
+// group of T = N / 32 threads (2 warps for N = 2048, 4 for 4096) that meets
+// at a named barrier (id = group + 1) wherever one warp would use __syncwarp.
 template <int N>
-__global__ void __launch_bounds__(ColCfg<N>::THREADS)
-column_kernel(const float2* __restrict__ Y, const float2* __restrict__ X, float2* __restrict__ strip,
-              uint32_t* __restrict__ wstatus, ColumnArgs a) {
-  using C = ColCfg<N>;
+struct GroupPipeCfg {
+  static constexpr int T = N / 32;
+  static constexpr int E = 32;
+  static constexpr int BUF = smem_elems(N);
+  static constexpr int GROUPS = (int)((227u * 1024u) / (3u * BUF * sizeof(float2)));  // 4 for 2048, 2 for 4096
+  static constexpr int THREADS = T * GROUPS;
+  static constexpr size_t SMEM = (size_t)GROUPS * 3 * BUF * sizeof(float2);
+  static_assert(GROUPS >= 1 && GROUPS <= 15, "named barriers 1..15");
+};
+
+template <int N>
+__global__ void __launch_bounds__(GroupPipeCfg<N>::THREADS, 1)
+column_group_pipe_kernel(const float2* __restrict__ Y, const float2* __restrict__ X, float2* __restrict__ strip,
+                         uint32_t* __restrict__ wstatus, ColumnArgs a) {
+  using C = GroupPipeCfg<N>;
   constexpr int T = C::T, E = C::E;
   extern __shared__ float2 smem[];
-  const int group = threadIdx.x / T;
-  const int t = threadIdx.x % T;
-  const int lane = threadIdx.x & 31;
-  float2* sm = smem + group * smem_elems(N);
+  __shared__ long long s_tk[C::GROUPS][2];
+  const int group = threadIdx.x / T, t = threadIdx.x % T, lane = threadIdx.x & 31;
+  float2* ring = smem + (size_t)group * 3 * C::BUF;
   const long total = (long)a.frames * a.M;
+  const uint64_t pol = evict_first_policy();
 
-  for (long sym = (long)blockIdx.x * C::GROUPS + group; sym < total; sym += (long)gridDim.x * C::GROUPS) {
+  auto issue_row = [&](const float2* g, float2* dst) {
+    const char* gs = reinterpret_cast<const char*>(g);
+    char* ds = reinterpret_cast<char*>(dst);
+#pragma unroll
+    for (int c = t; c < N / 2; c += T) cp_async16(ds + 16 * c, gs + 16 * c, pol);
+  };
+  // Group-wide ticket: thread 0 of the group draws it, the group's barrier
+  // publishes it.  Two slots alternate so that a slot is rewritten only after
+  // every thread has passed the barrier that follows its last read.
+  int slot = 0;
+  auto ticket = [&]() -> long {
+    if (t == 0) s_tk[group][slot] = (long long)(atomicAdd(a.work_ctr, 1ull) - a.work_base);
+    group_sync<T>(group);
+    const long v = (long)s_tk[group][slot];
+    slot ^= 1;
+    return v;
+  };
+  auto row_off = [&](long sm) -> long {
+    if (!a.frame_off) return sm * N;
+    return (long)a.frame_off[sm / a.M] + (sm % a.M) * N;
+  };
+  int ia = 0, iy = 1, ifree = 2;
+  long sym = ticket();
+  if (sym < total) issue_row(X + row_off(sym), ring + ia * C::BUF);
+  cp_async_commit();
+  if (sym < total) issue_row(Y + row_off(sym), ring + iy * C::BUF);
+  cp_async_commit();
+  long nxt = sym < total ? ticket() : total;
+  for (; sym < total; sym = nxt, nxt = (nxt < total ? ticket() : total)) {
+    if (nxt < total) issue_row(X + row_off(nxt), ring + ifree * C::BUF);
+    cp_async_commit();
     const int f = (int)(sym / a.M);
     const int l = (int)(sym % a.M);
-    const long ro = a.frame_off ? (long)a.frame_off[f] + (long)l * N : sym * N;
-    const float2* x = X + ro;
-    const float2* y = Y + ro;
+    float2* sa = ring + ia * C::BUF;        // A row, then the FFT exchange buffer
+    const float2* sy = ring + iy * C::BUF;  // Y row
     float2 v[E];
     uint32_t flags = 0;
     if (a.zc) {
-      // b~[k'] = pre[s] A[s], s = r'^{-1} k' mod N, so that the DFT below
-      // yields B[r' i] = sum_k pre_k A_k e^{+2 pi i r' i k / N} at position i.
+      cp_async_wait<2>();                   // A(sym) has landed (this thread's copies) ...
+      group_sync<T>(group);                 // ... and every thread's
 #pragma unroll
       for (int q = 0; q < E; ++q) {
         const int k = t + T * q;
-        const int s = (a.rinv == 1) ? k : (int)(((unsigned)a.rinv * (unsigned)k) & (N - 1));
-        const float2 xv = (a.rinv == 1) ? ld_stream(x + s) : __ldg(x + s);
-        v[q] = cmul(xv, __ldg(a.pre + s));
+        const int s2 = (a.rinv == 1) ? k : (int)(((unsigned)a.rinv * (unsigned)k) & (N - 1));
+        v[q] = cmul(sa[s2], __ldg(a.pre + s2));   // the row lands unpadded
       }
-      group_fft<N, T, +1>(v, sm, a.tw, t, group);
-      if (a.refine_tau > 0.f) refine_small_cells<N, T, E>(v, x, a, t, lane);
-      flags |= divide_precoded<T, E>(v, y, false, a, t);
+      group_fft<N, T, +1>(v, sa, a.tw, t, group);
+      if (a.refine_tau > 0.f) refine_small_cells<N, T, E>(v, X + row_off(sym), a, t, lane);
+      cp_async_wait<1>();                   // Y(sym)
+      group_sync<T>(group);
+      flags |= divide_precoded<T, E>(v, sy, true, a, t);
     } else {
-      flags |= divide_plain<T, E>(v, x, y, false, t);
+      cp_async_wait<1>();                   // A(sym) and Y(sym)
+      group_sync<T>(group);
+      flags |= divide_plain<T, E>(v, sa, sy, true, t);
     }
-    group_fft<N, T, +1>(v, sm, a.tw, t, group);
-    flags |= stencil_write<N, T, E>(v, sm, strip, a, f, l, t, group);
-    if (flags) atomicOr(wstatus + f, flags);
+    group_sync<T>(group);                   // every thread is done with the Y row
+    if (nxt < total) issue_row(Y + row_off(nxt), ring + iy * C::BUF);
+    cp_async_commit();
+    group_fft<N, T, +1>(v, sa, a.tw, t, group);
+    flags |= stencil_write<N, T, E>(v, sa, strip, a, f, l, t, group);
+    flags = __reduce_or_sync(0xffffffffu, flags);
+    if (lane == 0 && flags) atomicOr(wstatus + f, flags);
+    group_sync<T>(group);                   // every thread is done with sa before it is refilled
+    const int tmp = ia;
+    ia = ifree;
+    ifree = tmp;
   }
+  cp_async_wait<0>();
 }
 
 template <int N>
@@ -443,12 +498,18 @@ static cudaError_t launch_column_n(const float2* Y, const float2* X, float2* str
     if (a.pipe_warps == 4) return launch_pipe<N, 4>(Y, X, strip, wstatus, a, s, tickets, sms, total);
     return launch_pipe<N, 0>(Y, X, strip, wstatus, a, s, tickets, sms, total);
   } else {
-    using C = ColCfg<N>;
-    cudaError_t e = cudaFuncSetAttribute(column_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    using C = GroupPipeCfg<N>;
+    cudaError_t e = cudaFuncSetAttribute(column_group_pipe_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)C::SMEM);
     if (e != cudaSuccess) return e;
-    const long blocks = (total + C::GROUPS - 1) / C::GROUPS;
-    column_kernel<N><<<(unsigned)blocks, C::THREADS, C::SMEM, s>>>(Y, X, strip, wstatus, a);
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, column_group_pipe_kernel<N>, C::THREADS, C::SMEM);
+    if (e != cudaSuccess) return e;
+    long blocks = (long)sms * (per_sm > 0 ? per_sm : 1);
+    const long need = (total + C::GROUPS - 1) / C::GROUPS;
+    if (blocks > need) blocks = need;
+    column_group_pipe_kernel<N><<<(unsigned)blocks, C::THREADS, C::SMEM, s>>>(Y, X, strip, wstatus, a);
+    *tickets = (unsigned long long)total + (unsigned long long)blocks * C::GROUPS;
   }
   return cudaGetLastError();
 }

@@ -73,17 +73,20 @@ doppler_kernel(const float2* __restrict__ strip, float* __restrict__ map, float*
 #pragma unroll
       for (int q = 0; q < E; ++q) d[q] = (t + 32 * q < a.M) ? g[t + 32 * q] : make_float2(0.f, 0.f);
     };
+    // rows of frames outside the mask are neither loaded nor transformed
+    auto wanted = [&](long tk) { return !a.frame_mask || a.frame_mask[tk / a.rows] != 0; };
     float2 cur[E], nxt[PF ? E : 1];
-    if (PF && task < nt) load(task, cur);
+    if (PF && task < nt && wanted(task)) load(task, cur);
     for (; task < nt; task += stride) {
       const long nx = task + stride;
+      const bool want = wanted(task);
       if constexpr (PF) {
-        if (nx < nt) load(nx, nxt);
+        if (nx < nt && wanted(nx)) load(nx, nxt);
       } else {
-        load(task, cur);
+        if (want) load(task, cur);
       }
       const int f = (int)(task / a.rows);
-      if (!a.frame_mask || a.frame_mask[f]) {
+      if (want) {
         const int r = (a.row0 + (int)(task % a.rows)) % a.Np;
         float* prow = pow + task * MP;
         float* mrow = map_row(f, r);

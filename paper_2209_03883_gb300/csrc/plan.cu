@@ -77,8 +77,8 @@ namespace {
 // the LS division meets a near-zero precoded cell.
 constexpr float kRefineTau = 1e-4f;
 constexpr int kMaxTimed = 4096;
-constexpr int kKinds = 5;  // column, zero_rows, doppler, detect, zct
-enum { K_COLUMN = 0, K_ZERO = 1, K_DOPPLER = 2, K_DETECT = 3, K_ZCT = 4 };
+constexpr int kKinds = 8;  // column, zero_rows, doppler, detect, zct, coarse, cnn, refine
+enum { K_COLUMN = 0, K_ZERO = 1, K_DOPPLER = 2, K_DETECT = 3, K_ZCT = 4, K_COARSE = 5, K_CNN = 6, K_REFINE = 7 };
 
 // Records an event pair around one launch when timing is enabled.
 struct ScopedTimer {
@@ -1095,13 +1095,20 @@ int ofdm_radar_process_learned(ofdm_radar_plan* pl, const float* theta, const of
   cudaStream_t s = (cudaStream_t)stream;
   int launches = 0;
   unsigned long long tk = 0;
-  cudaError_t e = ofdm::launch_column(pl->p.N, (const float2*)Y, (const float2*)X, pl->d_strip, pl->d_wstatus,
-                                      column_args(pl, frames), s, &launches, &tk);
-  pl->ctr_base[pl->ctr_slot] += tk;
-  if (e == cudaSuccess)
+  cudaError_t e;
+  {
+    ScopedTimer tm(pl, s, K_COLUMN);
+    e = ofdm::launch_column(pl->p.N, (const float2*)Y, (const float2*)X, pl->d_strip, pl->d_wstatus,
+                            column_args(pl, frames), s, &launches, &tk);
+    pl->ctr_base[pl->ctr_slot] += tk;
+  }
+  if (e == cudaSuccess) {
+    ScopedTimer tm(pl, s, K_COARSE);
     e = ofdm::launch_coarse(pl->d_strip, pl->d_cpow, pl->d_cx, pl->rows, pl->p.M, frames, pl->d_w4, pl->d_twMc, s,
                             &launches);
+  }
   if (e == cudaSuccess) {
+    ScopedTimer tm(pl, s, K_CNN);
     e = ofdm::cnn_forward(theta, 1, pl->d_cx, frames, pl->Hc, pl->Mc, pl->d_a1, pl->d_a2, pl->d_logit, s);
     launches += 3;
   }
@@ -1112,15 +1119,20 @@ int ofdm_radar_process_learned(ofdm_radar_plan* pl, const float* theta, const of
   ra.frames = frames; ra.K = pl->p.max_targets; ra.cap = cap; ra.zthr = zthr;
   ra.inv_nm = (float)(1.0 / ((double)pl->p.N * pl->p.M));
   ra.dd = da.dd; ra.dv = da.dv; ra.wl = pl->d_wl; ra.rootsM = pl->d_rootsM;
-  e = ofdm::launch_refine(pl->d_strip, pl->d_logit, out, nt, st, pl->d_wstatus, pl->d_mask, pl->d_cand,
-                          pl->d_ncand, pl->d_keys, ra, s, &launches);
+  {
+    ScopedTimer tm(pl, s, K_REFINE);
+    e = ofdm::launch_refine(pl->d_strip, pl->d_logit, out, nt, st, pl->d_wstatus, pl->d_mask, pl->d_cand,
+                            pl->d_ncand, pl->d_keys, ra, s, &launches);
+  }
   // fallback: the full Doppler stage and detection on the flagged frames only
   if (e == cudaSuccess) {
+    ScopedTimer tm(pl, s, K_DOPPLER);
     DopplerArgs dop = doppler_args(pl, frames);
     dop.frame_mask = pl->d_mask;
     e = ofdm::launch_doppler(pl->Mp, pl->d_strip, nullptr, pl->d_pow, dop, s, &launches);
   }
   if (e == cudaSuccess) {
+    ScopedTimer tm(pl, s, K_DETECT);
     DetectArgs det = detect_args(pl, frames, 1);
     det.frame_mask = pl->d_mask;
     e = ofdm::launch_detect(pl->d_pow, out, nt, st, pl->d_wstatus, det, s, &launches);

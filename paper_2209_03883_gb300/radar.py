@@ -205,7 +205,7 @@ class Plan:
     def last_launch_count(self):
         return _lib.ofdm_radar_last_launch_count(self._h)
 
-    KERNEL_KINDS = ("column", "zero_rows", "doppler", "detect", "zct")
+    KERNEL_KINDS = ("column", "zero_rows", "doppler", "detect", "zct", "coarse", "cnn", "refine")
 
     def timing_enable(self, on=True):
         _check(_lib.ofdm_radar_timing_enable(self._h, int(bool(on))), "ofdm_radar_timing_enable")
