@@ -121,6 +121,76 @@ __device__ __forceinline__ void refine_small_cells(float2* v, const float2* __re
   }
 }
 
+// True if `pred` holds on any thread of the group (named barrier reduction;
+// every thread of the group must call it).
+template <int T>
+__device__ __forceinline__ bool group_any(int group, bool pred) {
+  unsigned r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, %2, %3, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((unsigned)pred), "r"(group + 1), "r"(T)
+      : "memory");
+  return r != 0;
+}
+
+constexpr int kRefineList = 64;  // flagged cells refined per symbol (more stay FP32)
+
+// Group form of refine_small_cells for T > 32: the same cells (a warp-local
+// mean sets the threshold) are recomputed by all T threads of the group, each
+// summing N / T terms, so no warp idles at the group's next barrier while
+// another recomputes a cell alone.
+template <int N, int T, int E>
+__device__ __forceinline__ void refine_small_cells_group(float2* v, const float2* __restrict__ x, const ColumnArgs& a,
+                                                         int t, int lane, int group, int* cnt, int* list,
+                                                         cdf* part) {
+  float s2 = 0.f;
+#pragma unroll
+  for (int q = 0; q < E; ++q) s2 += v[q].x * v[q].x + v[q].y * v[q].y;
+#pragma unroll
+  for (int off = 16; off; off >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+  const float thr = a.refine_tau * s2 * (1.f / (32.f * E));
+  unsigned flags = 0;
+#pragma unroll
+  for (int q = 0; q < E; ++q) flags |= (v[q].x * v[q].x + v[q].y * v[q].y < thr) ? (1u << q) : 0u;
+  if (!group_any<T>(group, flags != 0)) return;
+  for (unsigned m = flags; m; m &= m - 1) {
+    const int pos = atomicAdd(cnt, 1);
+    if (pos < kRefineList) list[pos] = (t << 8) | (__ffs(m) - 1);
+  }
+  group_sync<T>(group);
+  const int n = min(*cnt, kRefineList);
+  for (int j = 0; j < n; ++j) {
+    const int code = list[j], tt = code >> 8, qq = code & 255;
+    const int i = tt + T * qq;
+    cdf acc = {{0.f, 0.f}, {0.f, 0.f}};
+    for (int k = t; k < N; k += T) {
+      const cdf b = cdf_mulf(cdf_ld(a.pre_df + k), __ldg(x + k));
+      const unsigned mi = ((unsigned)a.rprime * (unsigned)i * (unsigned)k) & (unsigned)(N - 1);
+      acc = cdf_add(acc, cdf_mul(b, cdf_ld(a.w_df + mi)));
+    }
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+      acc.re = df_add(acc.re, df_shfl_xor(acc.re, off));
+      acc.im = df_add(acc.im, df_shfl_xor(acc.im, off));
+    }
+    if (lane == 0) part[(t >> 5)] = acc;
+    group_sync<T>(group);
+    if (t == tt) {
+      cdf tot = part[0];
+#pragma unroll
+      for (int w = 1; w < T / 32; ++w) tot = cdf_add(tot, part[w]);
+      const float2 val = make_float2(tot.re.hi + tot.re.lo, tot.im.hi + tot.im.lo);
+#pragma unroll
+      for (int q = 0; q < E; ++q)
+        if (q == qq) v[q] = val;
+    }
+    group_sync<T>(group);  // part[] is rewritten by the next cell
+  }
+  if (t == 0) *cnt = 0;    // the next symbol appends after its group_any barrier
+}
+
 // F_i = Y_i / X_p,i with X_p,i = post_i B_i / sqrt(N), B in v:
 //   F_i = Y_i conj(post_i) sqrt(N) conj(B_i) / |B_i|^2   (Eq. (16)).
 template <int T, int E>
@@ -359,7 +429,12 @@ column_group_pipe_kernel(const float2* __restrict__ Y, const float2* __restrict_
   constexpr int T = C::T, E = C::E;
   extern __shared__ float2 smem[];
   __shared__ long long s_tk[C::GROUPS][2];
+  __shared__ int s_rcnt[C::GROUPS];
+  __shared__ int s_rlist[C::GROUPS][kRefineList];
+  __shared__ cdf s_rpart[C::GROUPS][T / 32];
   const int group = threadIdx.x / T, t = threadIdx.x % T, lane = threadIdx.x & 31;
+  if (t == 0) s_rcnt[group] = 0;
+  __syncthreads();
   float2* ring = smem + (size_t)group * 3 * C::BUF;
   const long total = (long)a.frames * a.M;
   const uint64_t pol = evict_first_policy();
@@ -411,7 +486,9 @@ column_group_pipe_kernel(const float2* __restrict__ Y, const float2* __restrict_
         v[q] = cmul(sa[s2], __ldg(a.pre + s2));   // the row lands unpadded
       }
       group_fft<N, T, +1>(v, sa, a.tw, t, group);
-      if (a.refine_tau > 0.f) refine_small_cells<N, T, E>(v, X + row_off(sym), a, t, lane);
+      if (a.refine_tau > 0.f)
+        refine_small_cells_group<N, T, E>(v, X + row_off(sym), a, t, lane, group, &s_rcnt[group], s_rlist[group],
+                                          s_rpart[group]);
       cp_async_wait<1>();                   // Y(sym)
       group_sync<T>(group);
       flags |= divide_precoded<T, E>(v, sy, true, a, t);
