@@ -410,22 +410,27 @@ column_pipe_kernel(const float2* __restrict__ Y, const float2* __restrict__ X, f
 // The same ring-of-three-rows pipeline as above, with a symbol owned by a
 // group of T = N / 32 threads (2 warps for N = 2048, 4 for 4096) that meets
 // at a named barrier (id = group + 1) wherever one warp would use __syncwarp.
-template <int N>
+// T = N / 32 (32 points per thread) for N >= 2048; N = 1024 also has a
+// 2-warp form (T = 64, 16 points per thread, at most 512 threads per CTA so
+// that 128 registers per thread fit).
+template <int N, int TT = N / 32>
 struct GroupPipeCfg {
-  static constexpr int T = N / 32;
-  static constexpr int E = 32;
+  static constexpr int T = TT;
+  static constexpr int E = N / T;
   static constexpr int BUF = smem_elems(N);
-  static constexpr int GROUPS = (int)((227u * 1024u) / (3u * BUF * sizeof(float2)));  // 4 for 2048, 2 for 4096
+  static constexpr int FIT = (int)((227u * 1024u) / (3u * BUF * sizeof(float2)));  // 4 for 2048, 2 for 4096
+  static constexpr int GROUPS = (E < 32 && FIT > 512 / T) ? 512 / T : FIT;
   static constexpr int THREADS = T * GROUPS;
   static constexpr size_t SMEM = (size_t)GROUPS * 3 * BUF * sizeof(float2);
   static_assert(GROUPS >= 1 && GROUPS <= 15, "named barriers 1..15");
+  static_assert(T % 32 == 0, "whole warps");
 };
 
-template <int N>
-__global__ void __launch_bounds__(GroupPipeCfg<N>::THREADS, 1)
+template <int N, int TT = N / 32>
+__global__ void __launch_bounds__(GroupPipeCfg<N, TT>::THREADS, 1)
 column_group_pipe_kernel(const float2* __restrict__ Y, const float2* __restrict__ X, float2* __restrict__ strip,
                          uint32_t* __restrict__ wstatus, ColumnArgs a) {
-  using C = GroupPipeCfg<N>;
+  using C = GroupPipeCfg<N, TT>;
   constexpr int T = C::T, E = C::E;
   extern __shared__ float2 smem[];
   __shared__ long long s_tk[C::GROUPS][2];
@@ -563,6 +568,25 @@ static cudaError_t launch_pipe(const float2* Y, const float2* X, float2* strip, 
   return cudaGetLastError();
 }
 
+template <int N, int TT = N / 32>
+static cudaError_t launch_group_pipe(const float2* Y, const float2* X, float2* strip, uint32_t* wstatus,
+                                     const ColumnArgs& a, cudaStream_t s, unsigned long long* tickets, int sms,
+                                     long total) {
+  using C = GroupPipeCfg<N, TT>;
+  cudaError_t e = cudaFuncSetAttribute(column_group_pipe_kernel<N, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)C::SMEM);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, column_group_pipe_kernel<N, TT>, C::THREADS, C::SMEM);
+  if (e != cudaSuccess) return e;
+  long blocks = (long)sms * (per_sm > 0 ? per_sm : 1);
+  const long need = (total + C::GROUPS - 1) / C::GROUPS;
+  if (blocks > need) blocks = need;
+  column_group_pipe_kernel<N, TT><<<(unsigned)blocks, C::THREADS, C::SMEM, s>>>(Y, X, strip, wstatus, a);
+  *tickets = (unsigned long long)total + (unsigned long long)blocks * C::GROUPS;
+  return cudaGetLastError();
+}
+
 template <int N>
 static cudaError_t launch_column_n(const float2* Y, const float2* X, float2* strip, uint32_t* wstatus,
                                    const ColumnArgs& a, cudaStream_t s, unsigned long long* tickets) {
@@ -573,20 +597,16 @@ static cudaError_t launch_column_n(const float2* Y, const float2* X, float2* str
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if constexpr (N <= 1024) {
     if (a.pipe_warps == 4) return launch_pipe<N, 4>(Y, X, strip, wstatus, a, s, tickets, sms, total);
+    if constexpr (N == 1024) {
+      if (a.pipe_warps == 2 && a.tw_group) {
+        ColumnArgs g = a;
+        g.tw = a.tw_group;
+        return launch_group_pipe<N, 64>(Y, X, strip, wstatus, g, s, tickets, sms, total);
+      }
+    }
     return launch_pipe<N, 0>(Y, X, strip, wstatus, a, s, tickets, sms, total);
   } else {
-    using C = GroupPipeCfg<N>;
-    cudaError_t e = cudaFuncSetAttribute(column_group_pipe_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)C::SMEM);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, column_group_pipe_kernel<N>, C::THREADS, C::SMEM);
-    if (e != cudaSuccess) return e;
-    long blocks = (long)sms * (per_sm > 0 ? per_sm : 1);
-    const long need = (total + C::GROUPS - 1) / C::GROUPS;
-    if (blocks > need) blocks = need;
-    column_group_pipe_kernel<N><<<(unsigned)blocks, C::THREADS, C::SMEM, s>>>(Y, X, strip, wstatus, a);
-    *tickets = (unsigned long long)total + (unsigned long long)blocks * C::GROUPS;
+    return launch_group_pipe<N>(Y, X, strip, wstatus, a, s, tickets, sms, total);
   }
   return cudaGetLastError();
 }

@@ -26,6 +26,7 @@ struct ofdm_radar_plan {
   float c0, c1;
   float2* d_tables = nullptr;  // one allocation: pre, post, pre_conj, post_conj, twN, twM
   float2 *pre, *post, *pre_conj, *post_conj, *twN, *twM;
+  float2* twG = nullptr;       // N = 1024: twiddles for 16 points per thread (two-warp groups)
   float4* d_df = nullptr;      // double-float pre-chirp [N] and roots of unity [N]
   float* d_wl = nullptr;
   float2* d_strip = nullptr;   // [max_frames][rows][M]
@@ -304,8 +305,9 @@ int ofdm_radar_plan_create(const ofdm_radar_params* pin, ofdm_radar_plan** out) 
     if (((long long)c * r) % N == 1) { rinv = c; break; }
   pl->rinv = rinv;
 
-  std::vector<float2> twN, twM;
+  std::vector<float2> twN, twM, twG;
   build_twiddles(twN, N, column_points_per_thread(N));
+  if (N == 1024) build_twiddles(twG, N, 16);   // two-warp groups of the column kernel
   if (Mp <= 32) {
     twM.resize(Mp);
     for (int m = 0; m < Mp; ++m) {
@@ -322,7 +324,7 @@ int ofdm_radar_plan_create(const ofdm_radar_params* pin, ofdm_radar_plan** out) 
           : p.window == OFDM_WINDOW_HAMMING ? (float)(0.54 - 0.46 * c) : 1.f;
   }
 
-  const size_t ntab = 4 * (size_t)N + twN.size() + twM.size();
+  const size_t ntab = 4 * (size_t)N + twN.size() + twM.size() + twG.size();
   cudaError_t e = dalloc(&pl->d_tables, ntab);
   if (e == cudaSuccess) e = dalloc(&pl->d_df, 2 * (size_t)N);
   if (e == cudaSuccess) e = dalloc(&pl->d_wl, (size_t)M);
@@ -348,6 +350,7 @@ int ofdm_radar_plan_create(const ofdm_radar_params* pin, ofdm_radar_plan** out) 
   pl->post_conj = pl->pre_conj + N;
   pl->twN = pl->post_conj + N;
   pl->twM = pl->twN + twN.size();
+  pl->twG = twG.empty() ? nullptr : pl->twM + twM.size();
   std::vector<float2> host(ntab);
   memcpy(host.data(), pre.data(), N * sizeof(float2));
   memcpy(host.data() + N, post.data(), N * sizeof(float2));
@@ -355,6 +358,8 @@ int ofdm_radar_plan_create(const ofdm_radar_params* pin, ofdm_radar_plan** out) 
   memcpy(host.data() + 3 * N, postc.data(), N * sizeof(float2));
   memcpy(host.data() + 4 * N, twN.data(), twN.size() * sizeof(float2));
   memcpy(host.data() + 4 * N + twN.size(), twM.data(), twM.size() * sizeof(float2));
+  if (!twG.empty())
+    memcpy(host.data() + 4 * N + twN.size() + twM.size(), twG.data(), twG.size() * sizeof(float2));
   e = cudaMemcpy(pl->d_tables, host.data(), ntab * sizeof(float2), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(pl->d_wl, wl.data(), M * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(pl->d_df, df.data(), df.size() * sizeof(float4), cudaMemcpyHostToDevice);
@@ -443,7 +448,8 @@ ColumnArgs column_args(const ofdm_radar_plan* pl, int frames) {
   a.work_ctr = pl->d_ctr + pl->ctr_slot;
   a.work_base = pl->ctr_base[pl->ctr_slot];
   a.frame_off = nullptr;
-  a.pipe_warps = 0;
+  a.pipe_warps = pl->twG ? 2 : 0;   // N = 1024: two-warp groups (measured faster), else the widest CTA
+  a.tw_group = pl->twG;
   return a;
 }
 
@@ -793,7 +799,7 @@ cudaError_t run_group(BatchGroup& g, const float2* Y, const float2* X, float* ma
   ColumnArgs ca = column_args(pl, g.n);
   ca.work_base = 0;
   ca.frame_off = g.d_frame_off;
-  ca.pipe_warps = pipe_warps < 0 ? 0 : pipe_warps;
+  if (pipe_warps >= 0) ca.pipe_warps = pipe_warps;   // else the plan's default
   unsigned long long tk = 0;
   e = ofdm::launch_column(g.N, Y, X, pl->d_strip, pl->d_wstatus, ca, s, launches, &tk);
   if (e != cudaSuccess) return e;
@@ -816,13 +822,14 @@ cudaError_t tune_group(BatchGroup& g, const float2* Y, const float2* X, cudaStre
     if (it != g_tune.end()) { g.pipe_warps = it->second; return cudaSuccess; }
   }
   if (g.N > 1024) { g.pipe_warps = -1; return cudaSuccess; }
-  const int variants[2] = {0, 4};
+  const int variants[3] = {0, 4, 2};   // widest one-warp CTA, 4-warp CTAs, two-warp groups (N = 1024)
+  const int nvar = g.plan->twG ? 3 : 2;
   float best = 1e30f;
   int pick = 0;
   cudaEvent_t e0, e1;
   cudaError_t e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
-  for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
+  for (int v = 0; v < nvar && e == cudaSuccess; ++v) {
     float ms = 0.f;
     for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
       int launches = 0;
