@@ -92,6 +92,16 @@ __host__ __device__ constexpr int tw_size(int N, int E) { return tw_offset(N, E,
 // stride-32 writes of the first pass free of bank conflicts.
 __host__ __device__ constexpr int smem_elems(int N) { return N + N / 32; }
 __device__ __forceinline__ int pad32(int i) { return i + (i >> 5); }
+// Exchange-buffer position of element i.  With 16 points per thread the
+// first pass writes at stride 16, which the stride-32 padding leaves 2-way
+// bank-conflicted; rotating each 16-element block by its block index spreads
+// those writes over all banks and keeps 16 consecutive elements on distinct
+// banks (a permutation of [0, N), no padding needed).
+template <int E>
+__device__ __forceinline__ int xidx(int i) {
+  if constexpr (E == 16) return (i & ~15) | ((i + (i >> 4)) & 15);
+  else return pad32(i);
+}
 
 // ---------------------------------------------------------------- complex helpers
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
@@ -245,7 +255,7 @@ __device__ __forceinline__ void stockham_pass(float2* v, float2* sm, const float
 #pragma unroll
     for (int g = 0; g < G; ++g)
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[g + r * G] = sm[pad32(t + T * g + r * (N / R))];
+      for (int r = 0; r < R; ++r) v[g + r * G] = sm[xidx<E>(t + T * g + r * (N / R))];
   }
 #pragma unroll
   for (int g = 0; g < G; ++g) {
@@ -273,7 +283,7 @@ __device__ __forceinline__ void stockham_pass(float2* v, float2* sm, const float
       const int u = j & (NS - 1);
       const int base = (j / NS) * NS * R + u;
 #pragma unroll
-      for (int r = 0; r < R; ++r) sm[pad32(base + r * NS)] = v[g + r * G];
+      for (int r = 0; r < R; ++r) sm[xidx<E>(base + r * NS)] = v[g + r * G];
     }
     group_sync<T>(group);
   }
