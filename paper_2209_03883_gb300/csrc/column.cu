@@ -421,7 +421,11 @@ struct GroupPipeCfg {
   static constexpr int FIT = (int)((227u * 1024u) / (3u * BUF * sizeof(float2)));  // 4 for 2048, 2 for 4096
   static constexpr int GROUPS = (E < 32 && FIT > 512 / T) ? 512 / T : FIT;
   static constexpr int THREADS = T * GROUPS;
-  static constexpr size_t SMEM = (size_t)GROUPS * 3 * BUF * sizeof(float2);
+  // 16 points per thread: the pre-chirp and the pass twiddles live in shared
+  // memory behind the rings (18 KB for N = 1024)
+  static constexpr bool SMEM_TABLES = E < 32;
+  static constexpr int TABLE_ELEMS = SMEM_TABLES ? N + tw_size(N, E) : 0;
+  static constexpr size_t SMEM = (size_t)GROUPS * 3 * BUF * sizeof(float2) + (size_t)TABLE_ELEMS * sizeof(float2);
   static_assert(GROUPS >= 1 && GROUPS <= 15, "named barriers 1..15");
   static_assert(T % 32 == 0, "whole warps");
 };
@@ -439,6 +443,15 @@ column_group_pipe_kernel(const float2* __restrict__ Y, const float2* __restrict_
   __shared__ cdf s_rpart[C::GROUPS][T / 32];
   const int group = threadIdx.x / T, t = threadIdx.x % T, lane = threadIdx.x & 31;
   if (t == 0) s_rcnt[group] = 0;
+  const float2* pre = a.pre;
+  const float2* tw = a.tw;
+  if constexpr (C::SMEM_TABLES) {
+    float2* tab = smem + (size_t)C::GROUPS * 3 * C::BUF;
+    for (int i = threadIdx.x; i < N; i += C::THREADS) tab[i] = __ldg(a.pre + i);
+    for (int i = threadIdx.x; i < tw_size(N, E); i += C::THREADS) tab[N + i] = __ldg(a.tw + i);
+    pre = tab;
+    tw = tab + N;
+  }
   __syncthreads();
   float2* ring = smem + (size_t)group * 3 * C::BUF;
   const long total = (long)a.frames * a.M;
@@ -488,9 +501,9 @@ column_group_pipe_kernel(const float2* __restrict__ Y, const float2* __restrict_
       for (int q = 0; q < E; ++q) {
         const int k = t + T * q;
         const int s2 = (a.rinv == 1) ? k : (int)(((unsigned)a.rinv * (unsigned)k) & (N - 1));
-        v[q] = cmul(sa[s2], __ldg(a.pre + s2));   // the row lands unpadded
+        v[q] = cmul(sa[s2], C::SMEM_TABLES ? pre[s2] : __ldg(pre + s2));   // the row lands unpadded
       }
-      group_fft<N, T, +1>(v, sa, a.tw, t, group);
+      group_fft<N, T, +1, C::SMEM_TABLES>(v, sa, tw, t, group);
       if (a.refine_tau > 0.f)
         refine_small_cells_group<N, T, E>(v, X + row_off(sym), a, t, lane, group, &s_rcnt[group], s_rlist[group],
                                           s_rpart[group]);
@@ -505,7 +518,7 @@ column_group_pipe_kernel(const float2* __restrict__ Y, const float2* __restrict_
     group_sync<T>(group);                   // every thread is done with the Y row
     if (nxt < total) issue_row(Y + row_off(nxt), ring + iy * C::BUF);
     cp_async_commit();
-    group_fft<N, T, +1>(v, sa, a.tw, t, group);
+    group_fft<N, T, +1, C::SMEM_TABLES>(v, sa, tw, t, group);
     flags |= stencil_write<N, T, E>(v, sa, strip, a, f, l, t, group);
     flags = __reduce_or_sync(0xffffffffu, flags);
     if (lane == 0 && flags) atomicOr(wstatus + f, flags);

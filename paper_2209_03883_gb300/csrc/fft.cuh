@@ -242,7 +242,7 @@ __device__ __forceinline__ void group_sync(int group) {
 }
 
 // ---------------------------------------------------------------- Stockham passes
-template <int N, int T, int DIR, int P>
+template <int N, int T, int DIR, int P, bool TW_SHARED = false>
 __device__ __forceinline__ void stockham_pass(float2* v, float2* sm, const float2* __restrict__ tw,
                                               int t, int group) {
   constexpr int E = N / T;
@@ -266,7 +266,7 @@ __device__ __forceinline__ void stockham_pass(float2* v, float2* sm, const float
       const int u = (t + T * g) & (NS - 1);
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        float2 tv = __ldg(tw + tw_offset(N, E, P) + r * NS + u);
+        float2 tv = TW_SHARED ? tw[tw_offset(N, E, P) + r * NS + u] : __ldg(tw + tw_offset(N, E, P) + r * NS + u);
         if (DIR < 0) tv.y = -tv.y;
         w[r] = cmul(w[r], tv);
       }
@@ -289,21 +289,22 @@ __device__ __forceinline__ void stockham_pass(float2* v, float2* sm, const float
   }
 }
 
-template <int N, int T, int DIR, int... Ps>
+template <int N, int T, int DIR, bool TW_SHARED, int... Ps>
 __device__ __forceinline__ void run_passes(float2* v, float2* sm, const float2* __restrict__ tw, int t,
                                            int group, std::integer_sequence<int, Ps...>) {
-  (stockham_pass<N, T, DIR, Ps>(v, sm, tw, t, group), ...);
+  (stockham_pass<N, T, DIR, Ps, TW_SHARED>(v, sm, tw, t, group), ...);
 }
 
 // Unnormalised N-point DFT  X[m] = sum_n x[n] exp(DIR 2 pi i m n / N)
 // on the group's registers (layout t + T q in and out).  `sm` holds
 // smem_elems(N) float2 private to the group; `tw` is the host-built table
-// for DIR = +1 (conjugated on the fly for DIR = -1).
-template <int N, int T, int DIR>
+// for DIR = +1 (conjugated on the fly for DIR = -1).  TW_SHARED: `tw` is a
+// copy of the table in shared memory (plain loads instead of __ldg).
+template <int N, int T, int DIR, bool TW_SHARED = false>
 __device__ __forceinline__ void group_fft(float2* v, float2* sm, const float2* __restrict__ tw, int t,
                                           int group) {
   static_assert(N % T == 0 && N / T >= 2, "at least two points per thread");
-  run_passes<N, T, DIR>(v, sm, tw, t, group, std::make_integer_sequence<int, num_passes(N, N / T)>{});
+  run_passes<N, T, DIR, TW_SHARED>(v, sm, tw, t, group, std::make_integer_sequence<int, num_passes(N, N / T)>{});
 }
 
 // ---------------------------------------------------------------- double-float
