@@ -518,7 +518,14 @@ column_group_pipe_kernel(const float2* __restrict__ Y, const float2* __restrict_
     group_sync<T>(group);                   // every thread is done with the Y row
     if (nxt < total) issue_row(Y + row_off(nxt), ring + iy * C::BUF);
     cp_async_commit();
-    group_fft<N, T, +1, C::SMEM_TABLES>(v, sa, tw, t, group);
+    // DFT-CE keeps taps n = t + T q < L_cp only: for N = 1024 in two-warp
+    // groups and L_cp <= 128 that is q < 2, so the last pass is pruned.
+    if constexpr (N == 1024 && T == 64) {
+      if (a.L_cp <= 2 * T) group_fft_pruned<N, T, +1, C::SMEM_TABLES, 2>(v, sa, tw, t, group);
+      else group_fft<N, T, +1, C::SMEM_TABLES>(v, sa, tw, t, group);
+    } else {
+      group_fft<N, T, +1, C::SMEM_TABLES>(v, sa, tw, t, group);
+    }
     flags |= stencil_write<N, T, E>(v, sa, strip, a, f, l, t, group);
     flags = __reduce_or_sync(0xffffffffu, flags);
     if (lane == 0 && flags) atomicOr(wstatus + f, flags);

@@ -307,6 +307,46 @@ __device__ __forceinline__ void group_fft(float2* v, float2* sm, const float2* _
   run_passes<N, T, DIR, TW_SHARED>(v, sm, tw, t, group, std::make_integer_sequence<int, num_passes(N, N / T)>{});
 }
 
+// Output-pruned form of group_fft: the last pass produces only the outputs
+// t + T q with q < QO (the others are left unset), which is all that is read
+// when the transform's later use keeps a prefix of its outputs.  QO must not
+// exceed the last pass's G = E / R, so each kept output is the r = 0 output of
+// its radix-R butterfly group: the plain sum of the R twiddled inputs.
+template <int N, int T, int DIR, int P, bool TW_SHARED, int QO>
+__device__ __forceinline__ void stockham_last_pruned(float2* v, const float2* sm, const float2* __restrict__ tw,
+                                                     int t) {
+  constexpr int E = N / T;
+  constexpr int R = pass_radix(N, E, P);
+  constexpr int NS = pass_ns(N, E, P);
+  constexpr int G = E / R;
+  static_assert(P > 0 && P == num_passes(N, E) - 1, "the last pass");
+  static_assert(QO >= 1 && QO <= G, "kept outputs are r = 0 outputs");
+#pragma unroll
+  for (int g = 0; g < QO; ++g) {
+    const int u = (t + T * g) & (NS - 1);
+    float2 acc = sm[xidx<E>(t + T * g)];
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      float2 tv = TW_SHARED ? tw[tw_offset(N, E, P) + r * NS + u] : __ldg(tw + tw_offset(N, E, P) + r * NS + u);
+      if (DIR < 0) tv.y = -tv.y;
+      acc = cadd(acc, cmul(sm[xidx<E>(t + T * g + r * (N / R))], tv));
+    }
+    v[g] = acc;
+  }
+}
+template <int N, int T, int DIR, bool TW_SHARED, int QO, int... Ps>
+__device__ __forceinline__ void run_passes_pruned(float2* v, float2* sm, const float2* __restrict__ tw, int t,
+                                                  int group, std::integer_sequence<int, Ps...>) {
+  (stockham_pass<N, T, DIR, Ps, TW_SHARED>(v, sm, tw, t, group), ...);
+  stockham_last_pruned<N, T, DIR, (int)sizeof...(Ps), TW_SHARED, QO>(v, sm, tw, t);
+}
+template <int N, int T, int DIR, bool TW_SHARED, int QO>
+__device__ __forceinline__ void group_fft_pruned(float2* v, float2* sm, const float2* __restrict__ tw, int t,
+                                                 int group) {
+  run_passes_pruned<N, T, DIR, TW_SHARED, QO>(v, sm, tw, t, group,
+                                              std::make_integer_sequence<int, num_passes(N, N / T) - 1>{});
+}
+
 // ---------------------------------------------------------------- double-float
 // Unevaluated pairs hi + lo of floats (about 48-bit significands) built from
 // the error-free transformations TwoSum (Knuth) and TwoProd (via FMA), after
