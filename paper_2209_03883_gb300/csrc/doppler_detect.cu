@@ -1,14 +1,17 @@
 // doppler_detect.cu -- the per-range-row half of the chain (steps a6-a7).
 //
-// doppler_kernel: one warp per (frame, support row r): the window over l,
-//   the M'-point Doppler DFT  D[s] = sum_l w_l g[r, l] e^{-2 pi i l s / M'}
+// doppler_kernel: one warp per (frame, support row r) at a time: the window
+//   over l, the M'-point Doppler DFT  D[s] = sum_l w_l g[r, l] e^{-2 pi i l s / M'}
 //   and P = |D|^2 / (N M) (Eq. (17)); column c = s + M'/2 (mod M').  Each row
 //   goes to the compact power strip used by detection and, when asked, to the
 //   full map.
-// zero_rows_kernel: the map rows outside the DFT-CE support are exactly zero.
-// detect_kernel: one CTA per frame: 8-neighbour local maxima (circular in r
-//   and s), optional threshold eta = -sigma^2 ln(P_fa) with sigma^2 from the
-//   lower median (Eq. (18)), top-K by (power desc, map index asc), Eq. (19).
+// zero_rows_kernel: the map rows outside the DFT-CE support are exactly zero
+//   (the standalone Doppler step; the full chain has the detection launch
+//   write them).
+// detect_band_kernel: one CTA per band of rows: 8-neighbour local maxima
+//   (circular in r and s), optional threshold eta = -sigma^2 ln(P_fa) with
+//   sigma^2 from the lower median (Eq. (18)), top-K by (power desc, map index
+//   asc), Eq. (19).
 #include <float.h>
 
 #include "fft.cuh"
