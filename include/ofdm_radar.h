@@ -110,7 +110,7 @@ int ofdm_radar_process(ofdm_radar_plan* plan, const ofdm_c32* Y, const ofdm_c32*
 
 /* Same as ofdm_radar_process with HOST buffers (pinned memory gives
  * asynchronous, overlapped copies).  The plan allocates device staging for
- * max_frames on the first call.  The frames go in up to 8 chunks through
+ * max_frames on the first call.  The frames go in up to 16 chunks through
  * three internal streams ordered after `stream`: uploads back to back on
  * one, each chunk's kernels on a second once its upload is done, and its
  * results back on a third.  The call returns after everything, copies

@@ -15,7 +15,7 @@ using ofdm::DetectArgs;
 using ofdm::DopplerArgs;
 using ofdm::ZctArgs;
 
-constexpr int kHostChunks = 8;  // frame chunks of the host-buffer pipeline
+constexpr int kHostChunks = 16;  // frame chunks of the host-buffer pipeline
 
 struct ofdm_radar_plan {
   ofdm_radar_params p;
