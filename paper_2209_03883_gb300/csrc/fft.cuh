@@ -89,17 +89,19 @@ __host__ __device__ constexpr int tw_offset(int N, int E, int p) {
 __host__ __device__ constexpr int tw_size(int N, int E) { return tw_offset(N, E, num_passes(N, E)); }
 
 // Padded shared-memory index: one spare slot per 32 elements keeps the
-// stride-32 writes of the first pass free of bank conflicts.
-__host__ __device__ constexpr int smem_elems(int N) { return N + N / 32; }
+// stride-32 writes of the first pass free of bank conflicts.  Exchange
+// buffers hold N + N / 16 elements, room for either padding below.
+__host__ __device__ constexpr int smem_elems(int N) { return N + N / 16; }
 __device__ __forceinline__ int pad32(int i) { return i + (i >> 5); }
 // Exchange-buffer position of element i.  With 16 points per thread the
 // first pass writes at stride 16, which the stride-32 padding leaves 2-way
-// bank-conflicted; rotating each 16-element block by its block index spreads
-// those writes over all banks and keeps 16 consecutive elements on distinct
-// banks (a permutation of [0, N), no padding needed).
+// bank-conflicted; one spare slot per 16 elements spreads those writes over
+// all banks, keeps 16 consecutive elements (a 16-aligned half-warp) on
+// distinct banks, and stays linear in i, so constant offsets fold into the
+// load and store instructions.
 template <int E>
 __device__ __forceinline__ int xidx(int i) {
-  if constexpr (E == 16) return (i & ~15) | ((i + (i >> 4)) & 15);
+  if constexpr (E == 16) return i + (i >> 4);
   else return pad32(i);
 }
 
