@@ -423,7 +423,9 @@ struct GroupPipeCfg {
   static constexpr int THREADS = T * GROUPS;
   // 16 points per thread: the pre-chirp and the pass twiddles live in shared
   // memory behind the rings (18 KB for N = 1024)
-  static constexpr bool SMEM_TABLES = E < 32;
+  static constexpr size_t RING_BYTES = (size_t)GROUPS * 3 * BUF * sizeof(float2);
+  static constexpr bool SMEM_TABLES =
+      E < 32 && RING_BYTES + (size_t)(N + tw_size(N, E)) * sizeof(float2) + 4096 <= 227u * 1024u;
   static constexpr int TABLE_ELEMS = SMEM_TABLES ? N + tw_size(N, E) : 0;
   static constexpr size_t SMEM = (size_t)GROUPS * 3 * BUF * sizeof(float2) + (size_t)TABLE_ELEMS * sizeof(float2);
   static_assert(GROUPS >= 1 && GROUPS <= 15, "named barriers 1..15");
@@ -520,7 +522,9 @@ column_group_pipe_kernel(const float2* __restrict__ Y, const float2* __restrict_
     cp_async_commit();
     // DFT-CE keeps taps n = t + T q < L_cp only: for N = 1024 in two-warp
     // groups and L_cp <= 128 that is q < 2, so the last pass is pruned.
-    if constexpr (N == 1024 && T == 64) {
+    // (same for N = 2048 in four-warp groups, whose last pass is radix 8, G = 2)
+    constexpr int LASTG = E / pass_radix(N, E, num_passes(N, E) - 1);
+    if constexpr (E == 16 && LASTG >= 2) {
       if (a.L_cp <= 2 * T) group_fft_pruned<N, T, +1, C::SMEM_TABLES, 2>(v, sa, tw, t, group);
       else group_fft<N, T, +1, C::SMEM_TABLES>(v, sa, tw, t, group);
     } else {
@@ -626,6 +630,11 @@ static cudaError_t launch_column_n(const float2* Y, const float2* X, float2* str
     }
     return launch_pipe<N, 0>(Y, X, strip, wstatus, a, s, tickets, sms, total);
   } else {
+    if (a.pipe_warps == 2 && a.tw_group) {   // groups of N / 16 threads, 16 points each
+      ColumnArgs g = a;
+      g.tw = a.tw_group;
+      return launch_group_pipe<N, N / 16>(Y, X, strip, wstatus, g, s, tickets, sms, total);
+    }
     return launch_group_pipe<N>(Y, X, strip, wstatus, a, s, tickets, sms, total);
   }
   return cudaGetLastError();

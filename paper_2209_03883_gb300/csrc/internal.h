@@ -28,8 +28,8 @@ struct ColumnArgs {
   unsigned long long work_base;  // counter value at the start of this launch
   const long long* frame_off;    // per-frame complex offset of the Y / X rows, or null (f * M * N)
   int pipe_warps;                // pipelined kernel variant: 0 = most warps that fit, 4 = 4 warps per CTA,
-                                 // 2 = two-warp groups (N = 1024, needs tw_group)
-  const float2* tw_group = nullptr;  // N = 1024: pass twiddles for 16 points per thread, or null
+                                 // 2 = groups of N / 16 threads, 16 points each (N >= 1024, needs tw_group)
+  const float2* tw_group = nullptr;  // N >= 1024: pass twiddles for 16 points per thread, or null
 };
 
 struct ZctArgs {

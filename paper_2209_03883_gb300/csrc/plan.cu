@@ -26,7 +26,7 @@ struct ofdm_radar_plan {
   float c0, c1;
   float2* d_tables = nullptr;  // one allocation: pre, post, pre_conj, post_conj, twN, twM
   float2 *pre, *post, *pre_conj, *post_conj, *twN, *twM;
-  float2* twG = nullptr;       // N = 1024: twiddles for 16 points per thread (two-warp groups)
+  float2* twG = nullptr;       // N >= 1024: twiddles for 16 points per thread (groups of N / 16 threads)
   float4* d_df = nullptr;      // double-float pre-chirp [N] and roots of unity [N]
   float* d_wl = nullptr;
   float2* d_strip = nullptr;   // [max_frames][rows][M]
@@ -307,7 +307,7 @@ int ofdm_radar_plan_create(const ofdm_radar_params* pin, ofdm_radar_plan** out) 
 
   std::vector<float2> twN, twM, twG;
   build_twiddles(twN, N, column_points_per_thread(N));
-  if (N == 1024) build_twiddles(twG, N, 16);   // two-warp groups of the column kernel
+  if (N >= 1024) build_twiddles(twG, N, 16);   // column kernel in groups of N / 16 threads
   if (Mp <= 32) {
     twM.resize(Mp);
     for (int m = 0; m < Mp; ++m) {
@@ -448,7 +448,7 @@ ColumnArgs column_args(const ofdm_radar_plan* pl, int frames) {
   a.work_ctr = pl->d_ctr + pl->ctr_slot;
   a.work_base = pl->ctr_base[pl->ctr_slot];
   a.frame_off = nullptr;
-  a.pipe_warps = pl->twG ? 2 : 0;   // N = 1024: two-warp groups (measured faster), else the widest CTA
+  a.pipe_warps = pl->twG ? 2 : 0;   // N >= 1024: groups of N / 16 threads (measured faster), else the widest CTA
   a.tw_group = pl->twG;
   return a;
 }
