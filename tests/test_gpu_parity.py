@@ -288,23 +288,27 @@ def test_detect_entry_point_on_given_map(env):
     assert [(int(t["r"]), int(t["s"])) for t in tg[:n]] == list(zip(det32.r.tolist(), det32.s.tolist()))
 
 
-def test_host_buffer_path_matches_device_path(env):
+@pytest.mark.parametrize("config,frames", [(2, 8), (1, 37)])
+def test_host_buffer_path_matches_device_path(env, config, frames):
+    """Host buffers through the chunked three-stream pipeline equal the device
+    path bit for bit; 37 frames give 13 chunks of 3 and a last chunk of 1."""
     radar, torch, dev = env
-    cfg, fr = make_frames(2, 8)
+    cfg, fr = make_frames(config, frames)
     p = oracle_params(cfg)
     dres = run_chain(env, p, [f[2] for f in fr], [f[0].A for f in fr])
-    plan = radar.Plan(**plan_kwargs(p, 8))
+    plan = radar.Plan(**plan_kwargs(p, frames))
     Yh = torch.from_numpy(stack_lk([f[2] for f in fr])).pin_memory()
     Xh = torch.from_numpy(stack_lk([f[0].A for f in fr])).pin_memory()
-    mh = torch.empty((8, p.N, p.M), dtype=torch.float32).pin_memory()
-    th = torch.zeros((8 * p.max_targets * radar.TARGET_BYTES,), dtype=torch.uint8).pin_memory()
-    nh = torch.zeros((8,), dtype=torch.int32).pin_memory()
-    sh = torch.zeros((8,), dtype=torch.int32).pin_memory()
-    radar.ofdm_radar_process_host(plan, Yh, Xh, 8, mh, th, nh, sh)
+    mh = torch.empty((frames, p.N, p.M), dtype=torch.float32).pin_memory()
+    th = torch.zeros((frames * p.max_targets * radar.TARGET_BYTES,), dtype=torch.uint8).pin_memory()
+    nh = torch.zeros((frames,), dtype=torch.int32).pin_memory()
+    sh = torch.zeros((frames,), dtype=torch.int32).pin_memory()
+    radar.ofdm_radar_process_host(plan, Yh, Xh, frames, mh, th, nh, sh)
     assert np.array_equal(mh.numpy(), dres["map"])
     assert np.array_equal(nh.numpy(), dres["n"])
-    tv = radar.targets_view(th, 8, p.max_targets)
-    for i in range(8):
+    assert np.array_equal(sh.numpy().view(np.uint32), dres["status"])
+    tv = radar.targets_view(th, frames, p.max_targets)
+    for i in range(frames):
         n = int(nh[i])
         assert np.array_equal(tv[i][:n], dres["tg"][i][:n])
 
