@@ -224,44 +224,24 @@ __device__ __forceinline__ uint64_t warp_merge_lists(P src, int nlists, int K, i
 // LOGC = log2 of the columns each thread scans: 0 for M' <= 256, 1 for 512,
 // 2 for 1024 (the band always holds kDetBandCells / M' rows, kCells cells
 // per thread).
+// Everything after the band's power rows are in `tile` (tile row i = band row
+// i - 1; this thread's own writes to it complete): the zero map rows, the
+// scan, the floor, the band's top K and the last CTA's merge.  Shared by the
+// detection kernel (which stages the rows from the power strip) and the fused
+// Doppler + detection kernel (which computes them).
 template <int LOGC>
-__global__ void __launch_bounds__(kDetThreads)
-detect_band_kernel(const float* __restrict__ src, ofdm_target* __restrict__ out, int32_t* __restrict__ n_out,
-                   uint32_t* __restrict__ status, uint32_t* __restrict__ wstatus, DetectArgs a) {
+__device__ __forceinline__ void band_detect(float* tile, ofdm_target* __restrict__ out, int32_t* __restrict__ n_out,
+                                            uint32_t* __restrict__ status, uint32_t* __restrict__ wstatus,
+                                            const DetectArgs& a, int band, int f, int t0, int tr) {
   constexpr int C = 1 << LOGC, NR = kCells >> LOGC;
-  extern __shared__ __align__(16) unsigned char det_smem[];
   __shared__ uint64_t buf[kBandCap];
   __shared__ unsigned s_n, s_cnt;
   __shared__ uint64_t s_floor;
   __shared__ int s_last;
-  float* tile = reinterpret_cast<float*>(det_smem);  // (kDetBandCells / M' + 2) rows of M'
-  const int band = blockIdx.x, f = blockIdx.y;
-  if (a.frame_mask && !a.frame_mask[f]) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int K = a.K, Mp = a.Mp, logMp = a.logMp;
-  const int t0 = band * a.band_rows;
-  const int tr = min(a.band_rows, a.rows - t0);
-  const float* base = src + (long)f * a.frame_stride;
   const bool thr = a.mode == OFDM_DETECT_THRESHOLD;
   const float eta = thr ? (a.use_fixed_eta ? a.eta_fixed : a.eta[f]) : 0.f;
-
-  // stage rows t0 - 1 .. t0 + tr; rows outside a partial support are zero, a full support wraps
-  const int n4 = ((tr + 2) << logMp) >> 2;
-  for (int v = tid; v < n4; v += kDetThreads) {
-    const int idx = v << 2;
-    const int i = idx >> logMp, c = idx & (Mp - 1);
-    int rj = t0 - 1 + i;
-    if (a.full) rj &= (a.rows - 1);
-    if (rj >= 0 && rj < a.rows) {
-      const int row = a.compact ? rj : ((a.row0 + rj) & (a.Np - 1));
-      const unsigned d = (unsigned)__cvta_generic_to_shared(tile + idx);
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(base + ((long)row << logMp) + c)
-                   : "memory");
-    } else {
-      *reinterpret_cast<float4*>(tile + idx) = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-  }
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
   if (tid == 0) { s_n = 0; s_cnt = 0; }
 
   // The map rows outside the support are zero: this CTA's share of its
@@ -275,7 +255,6 @@ detect_band_kernel(const float* __restrict__ src, ofdm_target* __restrict__ out,
     zp = reinterpret_cast<float4*>(a.zmap + (a.zmap_off ? (long)a.zmap_off[f] : (long)f * a.zframe) + a.z_off);
   }
   const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  asm volatile("cp.async.wait_all;\n" ::: "memory");
   __syncthreads();
 
   // Scan: each thread walks down C columns c0 + 256 q over NR band rows from
@@ -425,6 +404,95 @@ detect_band_kernel(const float* __restrict__ src, ofdm_target* __restrict__ out,
   }
 }
 
+
+template <int LOGC>
+__global__ void __launch_bounds__(kDetThreads)
+detect_band_kernel(const float* __restrict__ src, ofdm_target* __restrict__ out, int32_t* __restrict__ n_out,
+                   uint32_t* __restrict__ status, uint32_t* __restrict__ wstatus, DetectArgs a) {
+  extern __shared__ __align__(16) unsigned char det_smem[];
+  float* tile = reinterpret_cast<float*>(det_smem);  // (kDetBandCells / M' + 2) rows of M'
+  const int band = blockIdx.x, f = blockIdx.y;
+  if (a.frame_mask && !a.frame_mask[f]) return;
+  const int tid = threadIdx.x;
+  const int Mp = a.Mp, logMp = a.logMp;
+  const int t0 = band * a.band_rows;
+  const int tr = min(a.band_rows, a.rows - t0);
+  const float* base = src + (long)f * a.frame_stride;
+
+  // stage rows t0 - 1 .. t0 + tr; rows outside a partial support are zero, a full support wraps
+  const int n4 = ((tr + 2) << logMp) >> 2;
+  for (int v = tid; v < n4; v += kDetThreads) {
+    const int idx = v << 2;
+    const int i = idx >> logMp, c = idx & (Mp - 1);
+    int rj = t0 - 1 + i;
+    if (a.full) rj &= (a.rows - 1);
+    if (rj >= 0 && rj < a.rows) {
+      const int row = a.compact ? rj : ((a.row0 + rj) & (a.Np - 1));
+      const unsigned d = (unsigned)__cvta_generic_to_shared(tile + idx);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(base + ((long)row << logMp) + c)
+                   : "memory");
+    } else {
+      *reinterpret_cast<float4*>(tile + idx) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  band_detect<LOGC>(tile, out, n_out, status, wstatus, a, band, f, t0, tr);
+}
+
+// Fused Doppler stage and detection (top-K mode, M' >= 64; frames outside an
+// optional mask are skipped): each CTA computes
+// the M'-point Doppler transforms of its band's support rows and the two halo
+// rows (the neighbouring bands compute those too) straight into its tile,
+// writes its own rows to the map, and detects.  Same arithmetic as
+// doppler_kernel; the power strip is not written.
+template <int MP>
+__global__ void __launch_bounds__(kDetThreads)
+doppler_band_kernel(const float2* __restrict__ strip, float* __restrict__ map, ofdm_target* __restrict__ out,
+                    int32_t* __restrict__ n_out, uint32_t* __restrict__ status, uint32_t* __restrict__ wstatus,
+                    DetectArgs a, DopplerArgs d) {
+  constexpr int LOGC = MP <= 256 ? 0 : (MP == 512 ? 1 : 2);
+  constexpr int E = MP / 32;
+  constexpr int TILE = (kDetBandCells / MP + 2) * MP;   // floats
+  extern __shared__ __align__(16) unsigned char det_smem[];
+  float* tile = reinterpret_cast<float*>(det_smem);
+  const int band = blockIdx.x, f = blockIdx.y;
+  if (a.frame_mask && !a.frame_mask[f]) return;   // the whole CTA, before any barrier
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float2* sm = reinterpret_cast<float2*>(det_smem + (size_t)TILE * sizeof(float)) + warp * smem_elems(MP);
+  const int t0 = band * a.band_rows;
+  const int tr = min(a.band_rows, a.rows - t0);
+  float w[E];
+#pragma unroll
+  for (int q = 0; q < E; ++q) w[q] = (lane + 32 * q < d.M) ? __ldg(d.wl + lane + 32 * q) : 0.f;
+  float* fmap = map ? map + (d.map_off ? (long)d.map_off[f] : (long)f * d.Np * MP) : nullptr;
+  for (int i = warp; i < tr + 2; i += kDetThreads / 32) {   // tile row i = band row i - 1
+    float* trow = tile + i * MP;
+    int rj = t0 - 1 + i;
+    if (a.full) rj &= (a.rows - 1);
+    if (rj < 0 || rj >= a.rows) {
+#pragma unroll
+      for (int q = 0; q < E; ++q) trow[lane + 32 * q] = 0.f;
+      continue;
+    }
+    const float2* g = strip + ((long)f * a.rows + rj) * d.M;
+    float2 v[E];
+#pragma unroll
+    for (int q = 0; q < E; ++q)
+      v[q] = (lane + 32 * q < d.M) ? cscale(g[lane + 32 * q], w[q]) : make_float2(0.f, 0.f);
+    group_fft<MP, 32, -1>(v, sm, d.tw, lane, 0);
+    float* mrow = (fmap && i >= 1 && i <= tr) ? fmap + (long)((d.row0 + rj) % d.Np) * MP : nullptr;
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      const int c = (lane + 32 * q + MP / 2) & (MP - 1);
+      const float p = (v[q].x * v[q].x + v[q].y * v[q].y) * d.inv_nm;
+      trow[c] = p;
+      if (mrow) __stcs(mrow + c, p);
+    }
+  }
+  band_detect<LOGC>(tile, out, n_out, status, wstatus, a, band, f, t0, tr);
+}
+
 __global__ void __launch_bounds__(1024) median_kernel(const float* __restrict__ src, DetectArgs a) {
   __shared__ uint32_t hist[256];
   __shared__ uint32_t s_prefix, s_rank;
@@ -534,6 +602,38 @@ cudaError_t launch_detect(const float* pow, ofdm_target* out, int32_t* n_out, ui
   ++*launches;
   kern<<<dim3(a.bands, a.frames), kDetThreads, smem, s>>>(pow, out, n_out, status, wstatus, a);
   return cudaGetLastError();
+}
+
+template <int MP>
+static cudaError_t launch_doppler_band_m(const float2* strip, float* map, ofdm_target* out, int32_t* n_out,
+                                        uint32_t* status, uint32_t* wstatus, const DetectArgs& a,
+                                        const DopplerArgs& d, cudaStream_t s) {
+  const size_t smem = (size_t)(kDetBandCells / MP + 2) * MP * sizeof(float) +
+                      (size_t)(kDetThreads / 32) * smem_elems(MP) * sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(doppler_band_kernel<MP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  doppler_band_kernel<MP><<<dim3(a.bands, a.frames), kDetThreads, smem, s>>>(strip, map, out, n_out, status,
+                                                                              wstatus, a, d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_doppler_detect(int Mp, const float2* strip, float* map, ofdm_target* out, int32_t* n_out,
+                                  uint32_t* status, uint32_t* wstatus, const DetectArgs& a_in, const DopplerArgs& d,
+                                  cudaStream_t s, int* launches) {
+  DetectArgs a = a_in;
+  detect_bands(a.rows, a.Mp, &a.band_rows, &a.bands);
+  if (a.mode != OFDM_DETECT_TOPK || a.frame_mask != d.frame_mask || a.bands > 1024 || !a.compact)
+    return cudaErrorInvalidValue;
+  ++*launches;
+  switch (Mp) {
+    case 64: return launch_doppler_band_m<64>(strip, map, out, n_out, status, wstatus, a, d, s);
+    case 128: return launch_doppler_band_m<128>(strip, map, out, n_out, status, wstatus, a, d, s);
+    case 256: return launch_doppler_band_m<256>(strip, map, out, n_out, status, wstatus, a, d, s);
+    case 512: return launch_doppler_band_m<512>(strip, map, out, n_out, status, wstatus, a, d, s);
+    case 1024: return launch_doppler_band_m<1024>(strip, map, out, n_out, status, wstatus, a, d, s);
+    default: --*launches; return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace ofdm

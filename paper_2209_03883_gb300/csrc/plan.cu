@@ -532,14 +532,19 @@ cudaError_t run_chain(ofdm_radar_plan* pl, const float2* Y, const float2* X, int
     pl->ctr_base[pl->ctr_slot] += tk;
   }
   if (e != cudaSuccess) return e;
+  DetectArgs ta = detect_args(pl, frames, 1);
+  set_zero_rows(pl, map, nullptr, &ta);   // the detection launch zeroes the rows outside the support
+  if (ofdm::doppler_detect_fusable(ta, pl->Mp)) {
+    ScopedTimer tm(pl, s, K_DETECT);      // Doppler stage included
+    return ofdm::launch_doppler_detect(pl->Mp, pl->d_strip, map, tg, nt, st, pl->d_wstatus, ta,
+                                       doppler_args(pl, frames), s, launches);
+  }
   {
     ScopedTimer tm(pl, s, K_DOPPLER);
     e = ofdm::launch_doppler(pl->Mp, pl->d_strip, map, pl->d_pow, doppler_args(pl, frames), s, launches);
   }
   if (e != cudaSuccess) return e;
   ScopedTimer tm(pl, s, K_DETECT);
-  DetectArgs ta = detect_args(pl, frames, 1);
-  set_zero_rows(pl, map, nullptr, &ta);   // the detection launch zeroes the rows outside the support
   return ofdm::launch_detect(pl->d_pow, tg, nt, st, pl->d_wstatus, ta, s, launches);
 }
 
@@ -805,11 +810,13 @@ cudaError_t run_group(BatchGroup& g, const float2* Y, const float2* X, float* ma
   if (e != cudaSuccess) return e;
   DopplerArgs da = doppler_args(pl, g.n);
   da.map_off = g.d_map_off;
-  e = ofdm::launch_doppler(pl->Mp, pl->d_strip, map, pl->d_pow, da, s, launches);
-  if (e != cudaSuccess) return e;
   DetectArgs ta = detect_args(pl, g.n, 1);
   ta.out_idx = g.d_idx;
   set_zero_rows(pl, map, g.d_map_off, &ta);
+  if (ofdm::doppler_detect_fusable(ta, pl->Mp))
+    return ofdm::launch_doppler_detect(pl->Mp, pl->d_strip, map, tg, nt, st, pl->d_wstatus, ta, da, s, launches);
+  e = ofdm::launch_doppler(pl->Mp, pl->d_strip, map, pl->d_pow, da, s, launches);
+  if (e != cudaSuccess) return e;
   return ofdm::launch_detect(pl->d_pow, tg, nt, st, pl->d_wstatus, ta, s, launches);
 }
 
@@ -1131,18 +1138,25 @@ int ofdm_radar_process_learned(ofdm_radar_plan* pl, const float* theta, const of
     e = ofdm::launch_refine(pl->d_strip, pl->d_logit, out, nt, st, pl->d_wstatus, pl->d_mask, pl->d_cand,
                             pl->d_ncand, pl->d_keys, ra, s, &launches);
   }
-  // fallback: the full Doppler stage and detection on the flagged frames only
-  if (e == cudaSuccess) {
-    ScopedTimer tm(pl, s, K_DOPPLER);
-    DopplerArgs dop = doppler_args(pl, frames);
-    dop.frame_mask = pl->d_mask;
-    e = ofdm::launch_doppler(pl->Mp, pl->d_strip, nullptr, pl->d_pow, dop, s, &launches);
-  }
-  if (e == cudaSuccess) {
+  // fallback: the full Doppler stage and detection on the flagged frames only,
+  // through the same kernels as ofdm_radar_process (so the outputs are equal)
+  DopplerArgs dop = doppler_args(pl, frames);
+  dop.frame_mask = pl->d_mask;
+  DetectArgs det = detect_args(pl, frames, 1);
+  det.frame_mask = pl->d_mask;
+  if (e == cudaSuccess && ofdm::doppler_detect_fusable(det, pl->Mp)) {
     ScopedTimer tm(pl, s, K_DETECT);
-    DetectArgs det = detect_args(pl, frames, 1);
-    det.frame_mask = pl->d_mask;
-    e = ofdm::launch_detect(pl->d_pow, out, nt, st, pl->d_wstatus, det, s, &launches);
+    e = ofdm::launch_doppler_detect(pl->Mp, pl->d_strip, nullptr, out, nt, st, pl->d_wstatus, det, dop, s,
+                                    &launches);
+  } else {
+    if (e == cudaSuccess) {
+      ScopedTimer tm(pl, s, K_DOPPLER);
+      e = ofdm::launch_doppler(pl->Mp, pl->d_strip, nullptr, pl->d_pow, dop, s, &launches);
+    }
+    if (e == cudaSuccess) {
+      ScopedTimer tm(pl, s, K_DETECT);
+      e = ofdm::launch_detect(pl->d_pow, out, nt, st, pl->d_wstatus, det, s, &launches);
+    }
   }
   if (e == cudaSuccess) e = mark_fallback(pl->d_mask, st, frames, s);
   return finish(pl, launches, e);

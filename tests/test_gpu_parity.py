@@ -107,7 +107,7 @@ def test_chain_matches_oracle(env, ci, frames):
     cfg, fr = make_frames(ci, frames)
     p = oracle_params(cfg)
     res = run_chain(env, p, [f[2] for f in fr], [f[0].A for f in fr])
-    assert res["launches"] >= 3
+    assert res["launches"] >= 2   # column + fused Doppler/detection (M' >= 64), else three kernels
     for i, (frm, Xp, Y) in enumerate(fr):
         ref = o.process(Y, frm.A, p)
         assert rel_l2(res["map"][i], ref["P"]) < MAP_TOL
