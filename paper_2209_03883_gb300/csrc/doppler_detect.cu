@@ -440,8 +440,8 @@ detect_band_kernel(const float* __restrict__ src, ofdm_target* __restrict__ out,
   band_detect<LOGC>(tile, out, n_out, status, wstatus, a, band, f, t0, tr);
 }
 
-// Fused Doppler stage and detection (top-K mode, M' >= 64; frames outside an
-// optional mask are skipped): each CTA computes
+// Fused Doppler stage and detection (top-K mode, 64 <= M' <= 256; frames
+// outside an optional mask are skipped): each CTA computes
 // the M'-point Doppler transforms of its band's support rows and the two halo
 // rows (the neighbouring bands compute those too) straight into its tile,
 // writes its own rows to the map, and detects.  Same arithmetic as
@@ -630,8 +630,6 @@ cudaError_t launch_doppler_detect(int Mp, const float2* strip, float* map, ofdm_
     case 64: return launch_doppler_band_m<64>(strip, map, out, n_out, status, wstatus, a, d, s);
     case 128: return launch_doppler_band_m<128>(strip, map, out, n_out, status, wstatus, a, d, s);
     case 256: return launch_doppler_band_m<256>(strip, map, out, n_out, status, wstatus, a, d, s);
-    case 512: return launch_doppler_band_m<512>(strip, map, out, n_out, status, wstatus, a, d, s);
-    case 1024: return launch_doppler_band_m<1024>(strip, map, out, n_out, status, wstatus, a, d, s);
     default: --*launches; return cudaErrorInvalidValue;
   }
 }

@@ -127,11 +127,12 @@ cudaError_t launch_zero_rows(float* map, int frames, int Np, int Mp, int z0, int
                              int* launches, const long long* map_off = nullptr);
 cudaError_t launch_detect(const float* pow, ofdm_target* out, int32_t* n_out, uint32_t* status,
                           uint32_t* wstatus, const DetectArgs& a, cudaStream_t s, int* launches);
-// Doppler stage and top-K detection in one launch (M' >= 64, compact strip;
-// the Doppler and detection arguments carry the same frame mask, if any): the
-// power strip is not written.
+// Doppler stage and top-K detection in one launch (64 <= M' <= 256, compact
+// strip; the Doppler and detection arguments carry the same frame mask, if
+// any): the power strip is not written.  For M' >= 512 the fused kernel needs
+// too many registers per thread and the two kernels were measured faster.
 inline bool doppler_detect_fusable(const DetectArgs& a, int Mp) {
-  return a.mode == OFDM_DETECT_TOPK && Mp >= 64 && Mp <= 1024 && a.compact;
+  return a.mode == OFDM_DETECT_TOPK && Mp >= 64 && Mp <= 256 && a.compact;
 }
 cudaError_t launch_doppler_detect(int Mp, const float2* strip, float* map, ofdm_target* out, int32_t* n_out,
                                   uint32_t* status, uint32_t* wstatus, const DetectArgs& a, const DopplerArgs& d,
