@@ -77,10 +77,15 @@ struct DetectArgs {
 
 // Row bands of the detection grid: kDetBandCells cells per CTA.
 constexpr int kDetBandCells = 4096;
+// The rows are spread evenly over the fewest bands of at most
+// kDetBandCells / M' rows (130 rows at M' = 256: 9 bands of 15 or 10, not 16
+// and a last band of 2), so that no CTA carries much more than the others.
 inline void detect_bands(int rows, int Mp, int* band_rows, int* bands) {
   int br = kDetBandCells / Mp;
   if (br < 1) br = 1;
   if (br > rows) br = rows;
+  const int nb = (rows + br - 1) / br;
+  br = (rows + nb - 1) / nb;
   *band_rows = br;
   *bands = (rows + br - 1) / br;
 }
