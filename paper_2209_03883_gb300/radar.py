@@ -160,6 +160,43 @@ def _ptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
 
 
+_DTYPES = {"c64": ("complex64",), "f32": ("float32",), "i32": ("int32", "uint32"), "u8": ("uint8",)}
+
+
+def _buf(t, kind, need, where, name, host=False):
+    """Pointer of tensor `t` after checking it against what the C call reads
+    or writes: dtype, contiguity, device (CUDA, or host memory for the *_host
+    entry point) and at least `need` elements.  None passes as NULL."""
+    if t is None:
+        return None
+    dt = str(t.dtype).replace("torch.", "")
+    if dt not in _DTYPES[kind]:
+        raise TypeError(f"{where}: {name} must be {_DTYPES[kind][0]}, got {dt}")
+    if not t.is_contiguous():
+        raise ValueError(f"{where}: {name} must be contiguous")
+    if host == bool(t.is_cuda):
+        raise ValueError(f"{where}: {name} must be a {'host' if host else 'CUDA'} tensor")
+    if t.numel() < need:
+        raise ValueError(f"{where}: {name} has {t.numel()} elements, the call needs {need}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _frames(frames, where, cap=None):
+    frames = int(frames)
+    if frames < 1 or (cap is not None and frames > cap):
+        raise ValueError(f"{where}: frames = {frames} outside [1, {cap}]")
+    return frames
+
+
+def _chain_ptrs(where, frames, N, M, Np, Mp, K, Y, X, out_map, out_targets, n_targets, status, host=False):
+    g = frames * M * N
+    return (_buf(Y, "c64", g, where, "Y", host), _buf(X, "c64", g, where, "X", host),
+            _buf(out_map, "f32", frames * Np * Mp, where, "out_map", host),
+            _buf(out_targets, "u8", frames * K * TARGET_BYTES, where, "out_targets", host),
+            _buf(n_targets, "i32", frames, where, "n_targets", host),
+            _buf(status, "i32", frames, where, "status", host))
+
+
 def _stream(stream):
     if stream is None:
         import torch
@@ -180,6 +217,7 @@ class Plan:
         self.N, self.M = p.N, p.M
         self.Np, self.Mp = p.N_pad or p.N, p.M_pad or p.M
         self.max_targets, self.max_frames = p.max_targets, p.max_frames
+        self.n_rows = _check(_lib.ofdm_radar_support_rows(self._h, None), "ofdm_radar_support_rows")
 
     @property
     def handle(self):
@@ -223,48 +261,70 @@ class Plan:
 
 def ofdm_radar_process(plan: Plan, Y, X, frames, out_map=None, out_targets=None, n_targets=None,
                        status=None, stream=None):
-    return _check(_lib.ofdm_radar_process(plan.handle, _ptr(Y), _ptr(X), frames, _ptr(out_map),
-                                          _ptr(out_targets), _ptr(n_targets), _ptr(status),
-                                          _stream(stream)), "ofdm_radar_process")
+    w = "ofdm_radar_process"
+    frames = _frames(frames, w, plan.max_frames)
+    ptrs = _chain_ptrs(w, frames, plan.N, plan.M, plan.Np, plan.Mp, plan.max_targets, Y, X, out_map,
+                       out_targets, n_targets, status)
+    return _check(_lib.ofdm_radar_process(plan.handle, ptrs[0], ptrs[1], frames, *ptrs[2:], _stream(stream)), w)
 
 
 def ofdm_radar_process_host(plan: Plan, Y_host, X_host, frames, map_host=None, targets_host=None,
                             n_targets_host=None, status_host=None, stream=None):
-    return _check(_lib.ofdm_radar_process_host(plan.handle, _ptr(Y_host), _ptr(X_host), frames,
-                                               _ptr(map_host), _ptr(targets_host),
-                                               _ptr(n_targets_host), _ptr(status_host),
-                                               _stream(stream)), "ofdm_radar_process_host")
+    w = "ofdm_radar_process_host"
+    frames = _frames(frames, w, plan.max_frames)
+    ptrs = _chain_ptrs(w, frames, plan.N, plan.M, plan.Np, plan.Mp, plan.max_targets, Y_host, X_host, map_host,
+                       targets_host, n_targets_host, status_host, host=True)
+    return _check(_lib.ofdm_radar_process_host(plan.handle, ptrs[0], ptrs[1], frames, *ptrs[2:], _stream(stream)),
+                  w)
 
 
 def ofdm_radar_process_noalloc(params: Params, Y, X, frames, out_map=None, out_targets=None,
                                n_targets=None, status=None, stream=None):
     """The chain without any device allocation (no plan; fixed in-library scratch)."""
-    return _check(_lib.ofdm_radar_process_noalloc(ctypes.byref(params), _ptr(Y), _ptr(X), frames,
-                                                  _ptr(out_map), _ptr(out_targets), _ptr(n_targets),
-                                                  _ptr(status), _stream(stream)),
-                  "ofdm_radar_process_noalloc")
+    w = "ofdm_radar_process_noalloc"
+    frames = _frames(frames, w)
+    ptrs = _chain_ptrs(w, frames, params.N, params.M, params.N_pad or params.N, params.M_pad or params.M,
+                       params.max_targets, Y, X, out_map, out_targets, n_targets, status)
+    # Y and X are checked for one frame: the library rejects frame counts
+    # beyond its fixed array before it reads them.
+    return _check(_lib.ofdm_radar_process_noalloc(ctypes.byref(params), ptrs[0], ptrs[1], frames, *ptrs[2:],
+                                                  _stream(stream)), w)
 
 
 def ofdm_zc_precode(plan: Plan, inp, out, frames, inverse=False, stream=None):
-    return _check(_lib.ofdm_zc_precode(plan.handle, _ptr(inp), _ptr(out), frames, int(bool(inverse)),
-                                       _stream(stream)), "ofdm_zc_precode")
+    w = "ofdm_zc_precode"
+    frames = _frames(frames, w)
+    g = frames * plan.M * plan.N
+    return _check(_lib.ofdm_zc_precode(plan.handle, _buf(inp, "c64", g, w, "in"), _buf(out, "c64", g, w, "out"),
+                                       frames, int(bool(inverse)), _stream(stream)), w)
 
 
 def ofdm_radar_range_profile(plan: Plan, Y, X, frames, strip, stream=None):
-    return _check(_lib.ofdm_radar_range_profile(plan.handle, _ptr(Y), _ptr(X), frames, _ptr(strip),
-                                                _stream(stream)), "ofdm_radar_range_profile")
+    w = "ofdm_radar_range_profile"
+    frames = _frames(frames, w, plan.max_frames)
+    g = frames * plan.M * plan.N
+    return _check(_lib.ofdm_radar_range_profile(plan.handle, _buf(Y, "c64", g, w, "Y"), _buf(X, "c64", g, w, "X"),
+                                                frames, _buf(strip, "c64", frames * plan.n_rows * plan.M, w, "strip"),
+                                                _stream(stream)), w)
 
 
 def ofdm_radar_doppler(plan: Plan, strip, frames, out_map, stream=None):
-    return _check(_lib.ofdm_radar_doppler(plan.handle, _ptr(strip), frames, _ptr(out_map),
-                                          _stream(stream)), "ofdm_radar_doppler")
+    w = "ofdm_radar_doppler"
+    frames = _frames(frames, w, plan.max_frames)
+    return _check(_lib.ofdm_radar_doppler(plan.handle, _buf(strip, "c64", frames * plan.n_rows * plan.M, w, "strip"),
+                                          frames, _buf(out_map, "f32", frames * plan.Np * plan.Mp, w, "out_map"),
+                                          _stream(stream)), w)
 
 
 def ofdm_radar_detect(plan: Plan, map_, frames, out_targets=None, n_targets=None, status=None,
                       stream=None):
-    return _check(_lib.ofdm_radar_detect(plan.handle, _ptr(map_), frames, _ptr(out_targets),
-                                         _ptr(n_targets), _ptr(status), _stream(stream)),
-                  "ofdm_radar_detect")
+    w = "ofdm_radar_detect"
+    frames = _frames(frames, w, plan.max_frames)
+    return _check(_lib.ofdm_radar_detect(plan.handle, _buf(map_, "f32", frames * plan.Np * plan.Mp, w, "map"), frames,
+                                         _buf(out_targets, "u8", frames * plan.max_targets * TARGET_BYTES, w,
+                                              "out_targets"),
+                                         _buf(n_targets, "i32", frames, w, "n_targets"),
+                                         _buf(status, "i32", frames, w, "status"), _stream(stream)), w)
 
 
 def targets_view(raw, frames, max_targets):
@@ -311,9 +371,15 @@ def fps_default_params(**kw) -> FpsParams:
 def ofdm_fps_sft(plan: Plan, Y, X, frames, fp: FpsParams, slices, out_targets=None, n_targets=None,
                  stream=None):
     """FPS-SFT; `slices` is a device int32 tensor [frames][iterations][2 + 2 * offsets]."""
-    return _check(_lib.ofdm_fps_sft(plan.handle, _ptr(Y), _ptr(X), frames, ctypes.byref(fp),
-                                    _ptr(slices), _ptr(out_targets), _ptr(n_targets),
-                                    _stream(stream)), "ofdm_fps_sft")
+    w = "ofdm_fps_sft"
+    frames = _frames(frames, w, plan.max_frames)
+    g = frames * plan.M * plan.N
+    return _check(_lib.ofdm_fps_sft(plan.handle, _buf(Y, "c64", g, w, "Y"), _buf(X, "c64", g, w, "X"), frames,
+                                    ctypes.byref(fp),
+                                    _buf(slices, "i32", frames * fp.iterations * (2 + 2 * fp.offsets), w, "slices"),
+                                    _buf(out_targets, "u8", frames * plan.max_targets * TARGET_BYTES, w,
+                                         "out_targets"),
+                                    _buf(n_targets, "i32", frames, w, "n_targets"), _stream(stream)), w)
 
 
 class Batch:
@@ -325,6 +391,8 @@ class Batch:
             arr[i] = FrameDesc(*d[:3], 0, d[3], d[4])
         self.nframes = len(descs)
         self.max_targets = params.max_targets
+        self.yx_extent = max(int(d[3]) + int(d[0]) * int(d[1]) for d in descs)
+        self.map_extent = max(int(d[4]) + int(d[0]) * int(d[1]) for d in descs)
         h = ctypes.c_void_p()
         _check(_lib.ofdm_radar_batch_create(ctypes.byref(params), ctypes.cast(arr, ctypes.c_void_p),
                                             len(descs), flags, ctypes.byref(h)), "ofdm_radar_batch_create")
@@ -340,9 +408,14 @@ class Batch:
         return bool(_lib.ofdm_radar_batch_used_graph(self._h))
 
     def process(self, Y, X, out_map, targets, n_targets, status, stream=None):
-        return _check(_lib.ofdm_radar_batch_process(self._h, _ptr(Y), _ptr(X), _ptr(out_map), _ptr(targets),
-                                                    _ptr(n_targets), _ptr(status), _stream(stream)),
-                      "ofdm_radar_batch_process")
+        w, n = "ofdm_radar_batch_process", self.nframes
+        return _check(_lib.ofdm_radar_batch_process(self._h, _buf(Y, "c64", self.yx_extent, w, "Y"),
+                                                    _buf(X, "c64", self.yx_extent, w, "X"),
+                                                    _buf(out_map, "f32", self.map_extent, w, "out_map"),
+                                                    _buf(targets, "u8", n * self.max_targets * TARGET_BYTES, w,
+                                                         "targets"),
+                                                    _buf(n_targets, "i32", n, w, "n_targets"),
+                                                    _buf(status, "i32", n, w, "status"), _stream(stream)), w)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -369,16 +442,28 @@ def ofdm_radar_learned_prepare(plan: Plan):
 
 
 def ofdm_radar_coarse_map(plan: Plan, Y, X, frames, x_out=None, stream=None):
-    return _check(_lib.ofdm_radar_coarse_map(plan.handle, _ptr(Y), _ptr(X), frames, _ptr(x_out),
-                                             _stream(stream)), "ofdm_radar_coarse_map")
+    w = "ofdm_radar_coarse_map"
+    frames = _frames(frames, w, plan.max_frames)
+    g = frames * plan.M * plan.N
+    h, wd = ctypes.c_int32(), ctypes.c_int32()
+    _check(_lib.ofdm_radar_coarse_shape(plan.handle, ctypes.byref(h), ctypes.byref(wd)), "ofdm_radar_coarse_shape")
+    return _check(_lib.ofdm_radar_coarse_map(plan.handle, _buf(Y, "c64", g, w, "Y"), _buf(X, "c64", g, w, "X"),
+                                             frames, _buf(x_out, "f32", frames * h.value * wd.value, w, "x_out"),
+                                             _stream(stream)), w)
 
 
 def ofdm_radar_process_learned(plan: Plan, theta, Y, X, frames, logit_threshold, max_candidates,
                                out_targets=None, n_targets=None, status=None, stream=None):
-    return _check(_lib.ofdm_radar_process_learned(plan.handle, _ptr(theta), _ptr(Y), _ptr(X), frames,
+    w = "ofdm_radar_process_learned"
+    frames = _frames(frames, w, plan.max_frames)
+    g = frames * plan.M * plan.N
+    return _check(_lib.ofdm_radar_process_learned(plan.handle, _buf(theta, "f32", ofdm_cnn_param_count(), w, "theta"),
+                                                  _buf(Y, "c64", g, w, "Y"), _buf(X, "c64", g, w, "X"), frames,
                                                   float(logit_threshold), int(max_candidates),
-                                                  _ptr(out_targets), _ptr(n_targets), _ptr(status),
-                                                  _stream(stream)), "ofdm_radar_process_learned")
+                                                  _buf(out_targets, "u8", frames * plan.max_targets * TARGET_BYTES,
+                                                       w, "out_targets"),
+                                                  _buf(n_targets, "i32", frames, w, "n_targets"),
+                                                  _buf(status, "i32", frames, w, "status"), _stream(stream)), w)
 
 
 def ofdm_cnn_param_count():
@@ -386,22 +471,31 @@ def ofdm_cnn_param_count():
 
 
 def ofdm_cnn_forward(theta, bf16, x, B, H, W, a1, a2, logits, stream=None):
-    return _check(_lib.ofdm_cnn_forward(_ptr(theta), int(bf16), _ptr(x), B, H, W, _ptr(a1), _ptr(a2),
-                                        _ptr(logits), _stream(stream)), "ofdm_cnn_forward")
+    w, c, a = "ofdm_cnn_forward", B * H * W, 16 * B * H * W
+    return _check(_lib.ofdm_cnn_forward(_buf(theta, "f32", ofdm_cnn_param_count(), w, "theta"), int(bf16),
+                                        _buf(x, "f32", c, w, "x"), B, H, W, _buf(a1, "f32", a, w, "a1"),
+                                        _buf(a2, "f32", a, w, "a2"), _buf(logits, "f32", c, w, "logits"),
+                                        _stream(stream)), w)
 
 
 def ofdm_cnn_backward(theta, bf16, x, a1, a2, glogits, B, H, W, ga1, ga2, gtheta, stream=None):
-    return _check(_lib.ofdm_cnn_backward(_ptr(theta), int(bf16), _ptr(x), _ptr(a1), _ptr(a2), _ptr(glogits),
-                                         B, H, W, _ptr(ga1), _ptr(ga2), _ptr(gtheta), _stream(stream)),
-                  "ofdm_cnn_backward")
+    w, c, a, n = "ofdm_cnn_backward", B * H * W, 16 * B * H * W, ofdm_cnn_param_count()
+    return _check(_lib.ofdm_cnn_backward(_buf(theta, "f32", n, w, "theta"), int(bf16), _buf(x, "f32", c, w, "x"),
+                                         _buf(a1, "f32", a, w, "a1"), _buf(a2, "f32", a, w, "a2"),
+                                         _buf(glogits, "f32", c, w, "glogits"), B, H, W,
+                                         _buf(ga1, "f32", a, w, "ga1"), _buf(ga2, "f32", a, w, "ga2"),
+                                         _buf(gtheta, "f32", n, w, "gtheta"), _stream(stream)), w)
 
 
 def ofdm_cnn_bce(logits, labels, n, pos_weight, loss, glogits, stream=None):
-    return _check(_lib.ofdm_cnn_bce(_ptr(logits), _ptr(labels), n, float(pos_weight), _ptr(loss),
-                                    _ptr(glogits), _stream(stream)), "ofdm_cnn_bce")
+    w = "ofdm_cnn_bce"
+    return _check(_lib.ofdm_cnn_bce(_buf(logits, "f32", n, w, "logits"), _buf(labels, "f32", n, w, "labels"), n,
+                                    float(pos_weight), _buf(loss, "f32", 1, w, "loss"),
+                                    _buf(glogits, "f32", n, w, "glogits"), _stream(stream)), w)
 
 
 def ofdm_cnn_adam(theta, grad, m, v, n, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
-    return _check(_lib.ofdm_cnn_adam(_ptr(theta), _ptr(grad), _ptr(m), _ptr(v), n, step, float(lr),
-                                     float(beta1), float(beta2), float(eps), _stream(stream)),
-                  "ofdm_cnn_adam")
+    w = "ofdm_cnn_adam"
+    return _check(_lib.ofdm_cnn_adam(_buf(theta, "f32", n, w, "theta"), _buf(grad, "f32", n, w, "grad"),
+                                     _buf(m, "f32", n, w, "m"), _buf(v, "f32", n, w, "v"), n, step, float(lr),
+                                     float(beta1), float(beta2), float(eps), _stream(stream)), w)

@@ -10,6 +10,7 @@ from oracle import ofdm_oracle as o
 
 MAP_TOL = 1e-5      # relative L2 of the FP32 path against FP64 (periodogram and strip)
 NEAR_TIE = 1e-5     # relative power gap under which two detections may swap
+PEAK_TOL = 1e-4     # relative error of one detected peak's power against FP64
 
 
 def rel_l2(a, b):
@@ -48,20 +49,36 @@ def stack_lk(arrs):
     return np.stack([syn.to_lk(a) for a in arrs])
 
 
-def check_detections_vs_fp64(gpu_rs, gpu_pw, det: o.Detection):
-    """Exact bin agreement with the FP64 oracle, except pairs of candidates
-    whose oracle powers are within NEAR_TIE (relative) of each other."""
+def check_detections_vs_fp64(gpu_rs, gpu_pw, det: o.Detection, P: np.ndarray):
+    """Exact bin agreement with the FP64 oracle up to near-ties.
+
+    gpu_rs: the GPU's (r, s) bins in its reported order; gpu_pw: their powers;
+    det: the oracle's detections on the FP64 map P ([r, c], c = s + M'/2).
+    The GPU must report as many targets as the oracle.  Where its i-th bin
+    differs from the oracle's, that bin must itself be a peak of the FP64 map
+    (no neighbour above it by more than NEAR_TIE) whose FP64 power lies
+    within NEAR_TIE of the oracle's i-th power: two candidates that FP32
+    cannot order.  Every reported power must match the FP64 power of its bin
+    to PEAK_TOL (relative, plus MAP_TOL of the strongest peak).  Returns the
+    number of swapped positions."""
     want = list(zip(det.r.tolist(), det.s.tolist()))
-    got = list(gpu_rs)
-    if got == want:
-        return 0
-    # allow swaps only among near-ties, including the first unreported one
-    pw = list(det.power) + ([det.next_power] if det.next_power else [])
+    got = [(int(r), int(s)) for r, s in gpu_rs]
+    assert len(got) == len(want), f"{len(got)} detections, oracle has {len(want)}"
+    assert len(set(got)) == len(got), f"repeated detection in {got}"
+    R, C = P.shape
+    top = float(det.power[0]) if len(want) else 0.0
     amb = 0
     for i, (g, w) in enumerate(zip(got, want)):
+        r, c = g[0] % R, (g[1] + C // 2) % C
+        pg = float(P[r, c])
         if g != w:
-            ref = pw[i]
-            close = [j for j, q in enumerate(pw) if abs(q - ref) <= NEAR_TIE * ref]
-            assert len(close) > 1, f"detection {i}: got {g}, oracle {want[i]} (no near-tie)"
+            ref = float(det.power[i])
+            assert abs(pg - ref) <= NEAR_TIE * ref, \
+                f"detection {i}: got {g} (P {pg:.6e}), oracle {w} (P {ref:.6e}): not a near-tie"
+            nb = max(float(P[(r + dr) % R, (c + dc) % C]) for dr in (-1, 0, 1) for dc in (-1, 0, 1)
+                     if (dr, dc) != (0, 0))
+            assert nb <= pg * (1 + NEAR_TIE), f"detection {i}: got {g}, not a peak of the FP64 map"
             amb += 1
+        assert abs(float(gpu_pw[i]) - pg) <= PEAK_TOL * pg + MAP_TOL * top, \
+            f"detection {i} at {g}: power {float(gpu_pw[i]):.6e}, FP64 {pg:.6e}"
     return amb

@@ -80,3 +80,25 @@ def test_batch_and_fps_reject_bad_input_before_any_launch(radar):
     assert lib.ofdm_fps_sft(None, None, None, 1, None, None, None, None, None) == -1
     assert lib.ofdm_radar_process_learned(None, None, None, None, 1, 0.0, 8, None, None, None, None) == -1
     assert radar.ofdm_cnn_param_count() == 16 * 9 + 16 + 16 * 16 * 9 + 16 + 16 * 9 + 1
+
+
+def test_binding_checks_buffers_before_calling_the_library(radar):
+    """dtype, contiguity, device and size are checked in the binding, so a
+    float32 or transposed view never reaches a kernel (no GPU needed: host
+    tensors are rejected for device arguments before any call)."""
+    import torch
+    p = radar.default_params(N=64, M=16, L_cp=8, max_targets=2)
+    good = torch.zeros((1, 16, 64), dtype=torch.complex64)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        radar.ofdm_radar_process_noalloc(p, good, good, 1)
+    with pytest.raises(TypeError, match="complex64"):
+        radar._buf(torch.zeros((1, 16, 64), dtype=torch.float32), "c64", 1024, "f", "Y")
+    with pytest.raises(ValueError, match="contiguous"):
+        radar._buf(torch.zeros((1, 64, 16), dtype=torch.complex64).transpose(1, 2), "c64", 1024, "f", "Y")
+    with pytest.raises(ValueError, match="needs 2048"):
+        radar._buf(good, "c64", 2048, "f", "Y", host=True)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        radar._chain_ptrs("f", 1, 64, 16, 64, 16, 2, good, good, None, None, None, None)
+    assert radar._buf(good, "c64", 1024, "f", "Y", host=True).value == good.data_ptr()
+    with pytest.raises(ValueError, match="frames"):
+        radar._frames(0, "f")

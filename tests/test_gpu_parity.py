@@ -113,7 +113,7 @@ def test_chain_matches_oracle(env, ci, frames):
         assert rel_l2(res["map"][i], ref["P"]) < MAP_TOL
         n = int(res["n"][i])
         rs = [(int(t["r"]), int(t["s"])) for t in res["tg"][i][:n]]
-        check_detections_vs_fp64(rs, res["tg"][i]["power"][:n], ref["det"])
+        check_detections_vs_fp64(rs, res["tg"][i]["power"][:n], ref["det"], ref["P"])
         # the detection step itself is exact on the GPU's own map (same FP32 decisions)
         det32 = o.detect(res["map"][i], p.detect_mode, p.max_targets)
         assert rs == list(zip(det32.r.tolist(), det32.s.tolist()))
@@ -133,7 +133,7 @@ def test_chain_full_batch_sampled(env):
         assert rel_l2(res["map"][i], ref["P"]) < MAP_TOL
         n = int(res["n"][i])
         rs = [(int(t["r"]), int(t["s"])) for t in res["tg"][i][:n]]
-        check_detections_vs_fp64(rs, res["tg"][i]["power"][:n], ref["det"])
+        check_detections_vs_fp64(rs, res["tg"][i]["power"][:n], ref["det"], ref["P"])
     # every frame finds its targets (one-bin tolerance for off-grid truth)
     hits = 0
     for i, (frm, _, _) in enumerate(fr):

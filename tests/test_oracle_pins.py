@@ -164,6 +164,113 @@ def test_point_target_window_closed_form(window):
     check_point_target_hann(window=window)
 
 
+# ---------------------------------------------------------------- range profile (Eq. (17), inner sum)
+def check_range_profile_point(window=o.WINDOW_HANN, N=64, M=16, rho=6, nu=3):
+    """A noiseless on-grid target survives DFT-CE unchanged, so H'[k, l] =
+    b e^{-j2pi k rho/N} e^{+j2pi l nu/M}.  With the periodic Hann window
+    w_k = 1/2 - (e^{+j2pi k/N} + e^{-j2pi k/N})/4 the range sum
+    sum_k w_k H'[k, l] e^{+j2pi k r/N} is N b e^{+j2pi l nu/M} times 1/2 at
+    r = rho, -1/4 at r = rho -+ 1 and 0 elsewhere (orthogonality of the
+    exponentials); Hamming gives 0.54 / -0.23; rect gives N at r = rho alone."""
+    b = 0.9 * np.exp(0.4j)
+    c0, c1 = {o.WINDOW_RECT: (1.0, 0.0), o.WINDOW_HANN: (0.5, -0.25),
+              o.WINDOW_HAMMING: (0.54, -0.23)}[window]
+    want = np.zeros((N, M), dtype=complex)
+    ramp = np.exp(2j * np.pi * np.arange(M) * nu / M)
+    want[rho] = c0 * N * b * ramp
+    want[(rho - 1) % N] += c1 * N * b * ramp
+    want[(rho + 1) % N] += c1 * N * b * ramp
+    # through the whole chain (ZC precoding, division, DFT-CE) ...
+    out = _noiseless_point(N, M, 16, rho, nu, b, 1, window)
+    assert np.allclose(out["g"], want, atol=1e-9 * N)
+    # ... and on the channel alone
+    g = o.range_profile(syn.channel([rho], [nu], [b], N, M), o.window(N, window))
+    assert np.allclose(g, want, atol=1e-9 * N)
+
+
+@pytest.mark.parametrize("window", [o.WINDOW_RECT, o.WINDOW_HANN, o.WINDOW_HAMMING])
+def test_range_profile_point_closed_form(window):
+    check_range_profile_point(window)
+
+
+def check_range_profile_then_doppler_is_periodogram(N=32, M=16, window=o.WINDOW_HANN):
+    """Eq. (17) is the range sum followed by the windowed Doppler sum: the
+    oracle's range profile, Doppler-summed term by term here, must give its
+    periodogram (centred columns, 1/(NM))."""
+    rng = np.random.default_rng(11)
+    Hd = rng.standard_normal((N, M)) + 1j * rng.standard_normal((N, M))
+    g = o.range_profile(Hd, o.window(N, window))
+    w_l = o.window(M, window)
+    P = o.periodogram(Hd, o.window(N, window), w_l)
+    want = np.zeros((N, M))
+    for r in range(N):
+        for c in range(M):
+            s = c - M // 2
+            acc = 0j
+            for l in range(M):
+                acc += w_l[l] * g[r, l] * np.exp(-2j * np.pi * ((l * s) % M) / M)
+            want[r, c] = abs(acc) ** 2 / (N * M)
+    assert np.allclose(P, want, rtol=1e-10, atol=1e-12 * want.max())
+
+
+@pytest.mark.parametrize("window", [o.WINDOW_RECT, o.WINDOW_HANN])
+def test_range_profile_then_doppler_is_periodogram(window):
+    check_range_profile_then_doppler_is_periodogram(window=window)
+
+
+# ---------------------------------------------------------------- coarse map of the learned proposal
+def check_coarse_map_point(window=o.WINDOW_HANN, N=64, M=64, L_cp=16, rho=6, nu_c=3):
+    """One noiseless on-grid target whose Doppler bin nu = 4 nu_c falls on the
+    coarse grid.  Its support rows carry amplitude alpha_j e^{+j2pi l nu/M};
+    over the first M/4 symbols that is e^{+j2pi l nu_c/(M/4)}, so the windowed
+    (M/4)-point DFT is alpha_j (M/4) beta(c) with beta the window's own DFT:
+    1 at c = nu_c for rect; 1/2 at nu_c and -1/4 at nu_c -+ 1 for Hann.  The
+    coarse cell is the maximum over each group of 4 workspace rows of
+    |alpha_j (M/4) beta(c)|^2, columns centred (c + M/8), x = log(1 + C/mean C)."""
+    b = 0.7 * np.exp(-1.1j)
+    Mc = M // 4
+    rows = o.support_rows(N, L_cp, window)
+    alpha = {o.WINDOW_RECT: {0: 1.0}, o.WINDOW_HANN: {0: 0.5, -1: -0.25, 1: -0.25}}[window]
+    beta = {o.WINDOW_RECT: {0: 1.0}, o.WINDOW_HANN: {0: 0.5, -1: -0.25, 1: -0.25}}[window]
+    ramp = np.exp(2j * np.pi * np.arange(M) * (4 * nu_c) / M)
+    g_rows = np.zeros((len(rows), M), dtype=complex)
+    for j, r in enumerate(rows):
+        d = (int(r) - rho + N // 2) % N - N // 2
+        if d in alpha:
+            g_rows[j] = alpha[d] * N * b * ramp
+    Hc = (len(rows) + 3) // 4
+    C = np.zeros((Hc, Mc))
+    for j, r in enumerate(rows):
+        d = (int(r) - rho + N // 2) % N - N // 2
+        if d not in alpha:
+            continue
+        for dc, bc in beta.items():
+            c = (nu_c + dc + Mc // 2) % Mc          # centred column
+            C[j // 4, c] = max(C[j // 4, c], abs(alpha[d] * N * b * Mc * bc) ** 2)
+    want = np.log1p(C / C.mean())
+    got = o.coarse_map(g_rows, window)
+    assert got.shape == (Hc, Mc)
+    assert np.allclose(got, want, atol=1e-12)
+
+
+@pytest.mark.parametrize("window", [o.WINDOW_RECT, o.WINDOW_HANN])
+def test_coarse_map_point_closed_form(window):
+    check_coarse_map_point(window)
+
+
+def test_coarse_map_rect_peak_value():
+    """Rect windows: the only non-zero coarse cell holds log(1 + Hc Mc)."""
+    N, M, L_cp, rho, nu_c = 64, 32, 16, 9, -2
+    Mc, rows = M // 4, o.support_rows(N, L_cp, o.WINDOW_RECT)
+    g = o.range_profile(syn.channel([rho], [4 * nu_c], [1.0], N, M), o.window(N, o.WINDOW_RECT))
+    x = o.coarse_map(g[rows], o.WINDOW_RECT)
+    Hc = (len(rows) + 3) // 4
+    peak = (rho // 4, nu_c + Mc // 2)
+    assert x[peak] == pytest.approx(math.log1p(Hc * Mc), rel=1e-12)
+    x[peak] = 0
+    assert np.max(np.abs(x)) < 1e-12
+
+
 def test_parseval():
     rng = np.random.default_rng(3)
     N, M = 32, 16
@@ -312,6 +419,10 @@ MUTATIONS = {
     "dft_ce_no_truncation": ("dft_ce", lambda f: (lambda H, L: f(H, H.shape[0]))),
     "dft_ce_extra_scale": ("dft_ce", lambda f: (lambda H, L: tuple(x / H.shape[0] for x in f(H, L)))),
     "window_symmetric": ("window", lambda f: (lambda n, k: f(n + 1, k)[:n] if k else f(n, k))),
+    "range_profile_no_window": ("range_profile",
+                                lambda f: (lambda Hd, w_k, N_pad=None: f(Hd, np.ones_like(w_k), N_pad))),
+    "coarse_map_no_window": ("coarse_map", lambda f: (lambda g, k: f(g, o.WINDOW_RECT))),
+    "coarse_map_unshifted": ("coarse_map", lambda f: (lambda g, k: np.roll(f(g, k), f(g, k).shape[1] // 2, axis=1))),
 }
 
 
@@ -321,7 +432,10 @@ def test_pins_catch_planted_mistakes(name, monkeypatch):
     monkeypatch.setattr(o, attr, wrap(getattr(o, attr)))
     checks = [lambda: check_zc_cazac(64, 3), lambda: check_zc_unitary(16, 3),
               check_dft_ce_identity, check_point_target_rect, check_point_target_hann,
-              lambda: test_dft_ce_keeps_on_grid_targets_in_cp()]
+              lambda: test_dft_ce_keeps_on_grid_targets_in_cp(),
+              lambda: check_range_profile_point(o.WINDOW_HANN),
+              lambda: check_range_profile_then_doppler_is_periodogram(),
+              lambda: check_coarse_map_point(o.WINDOW_HANN), lambda: check_coarse_map_point(o.WINDOW_RECT)]
     caught = 0
     for c in checks:
         try:
