@@ -40,9 +40,8 @@ BYTES_PER_FRAME = 20 * CFG.N * CFG.M           # Y + X (8NM each) + map (4NM)
 COLUMN_BYTES_PER_FRAME = 16 * CFG.N * CFG.M    # the column kernel reads Y and X
 
 
-# DRAM traffic of the column kernel from one ncu capture (profiles/
-# column_pipe_kernel_1024x256_64frames.md), valid only while its sources are
-# byte-identical to the captured ones.
+# DRAM traffic of the column kernel from one ncu capture of this workload,
+# valid only while its sources are byte-identical to the captured ones.
 TRAFFIC = {"bytes": 268.676096e6 + 6.363136e6,
            "sources": {"paper_2209_03883_gb300/csrc/column.cu": "a4b249c30005d74ba58b7d4bff5db3b3f778548d",
                        "paper_2209_03883_gb300/csrc/fft.cuh": "be6a0ab259f107f9f03afd0cdec7d675d6bb08b2"}}
@@ -91,7 +90,8 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        import tempfile
+        self.path = os.path.join(tempfile.gettempdir(), f"ofdm_bench_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
@@ -335,6 +335,107 @@ def extra_fps(radar, torch, dev, stream, steps, n_frames=32):
             "fps_sft": {"value": n_frames / (ms_f / 1e3), "unit": "frames/s", "ms_per_step": ms_f,
                         "iterations": I, "slices": T},
             "bins_agree_frames": f"{agree}/{n_frames}"}
+
+
+def extra_fps_ls(radar, torch, dev, stream, steps, n_frames=32):
+    """Plain LS estimation without precoding (zc_root = 0, L_cp = N) on 32
+    frames of 1024 x 1024, K = 8 on-grid, 5 dB: F = Y / X is cell-local, so
+    FPS-SFT reads only the sampled cells, while the periodogram (full
+    support, every row) reads and writes everything."""
+    N = M = 1024
+    cfg = syn.FrameConfig(N=N, M=M, L_cp=N, qam=16, zc_root=0, n_targets=8, on_grid=True, amp_db=(0.0, 0.0),
+                          snr_db=(5.0, 5.0), window=0, detect_k=8)
+    frames = [syn.draw_frame(cfg, 3000 + 700 + f) for f in range(n_frames)]
+    plan = radar.Plan(N=N, M=M, L_cp=N, zc_root=0, window=0, max_targets=8, max_frames=n_frames)
+    Ad = torch.from_numpy(np.stack([syn.to_lk(d.A) for d in frames])).to(dev)
+    Y = torch.from_numpy(np.stack([syn.to_lk(syn.received(d, d.A)) for d in frames])).to(dev)
+    rng = np.random.default_rng(3 * 1000 + 998)
+    T, I = 8, 4
+    sl = np.zeros((n_frames, I, 2 + 2 * T), dtype=np.int32)
+    sl[:, :, 0:2] = rng.integers(0, 512, size=(n_frames, I, 2)) * 2 + 1
+    sl[:, :, 2::2] = rng.integers(0, N, size=(n_frames, I, T))
+    sl[:, :, 3::2] = rng.integers(0, M, size=(n_frames, I, T))
+    sld = torch.from_numpy(sl).to(dev)
+    fp = radar.fps_default_params(iterations=I, offsets=T)
+    out = radar.alloc_outputs(plan, n_frames, dev)
+    tg2 = torch.zeros_like(out["targets"])
+    nt2 = torch.zeros_like(out["n_targets"])
+
+    def t_of(fn):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    ms_p = t_of(lambda: radar.ofdm_radar_process(plan, Y, Ad, n_frames, out["map"], out["targets"],
+                                                   out["n_targets"], out["status"], stream))
+    ms_f = t_of(lambda: radar.ofdm_fps_sft(plan, Y, Ad, n_frames, fp, sld, tg2, nt2, stream))
+    a = radar.targets_view(out["targets"], n_frames, 8)
+    b = radar.targets_view(tg2, n_frames, 8)
+    agree = sum(sorted((int(t["r"]), int(t["s"])) for t in a[f][:int(out["n_targets"][f])]) ==
+                sorted((int(t["r"]), int(t["s"])) for t in b[f][:int(nt2[f])]) for f in range(n_frames))
+    sampled = I * T * max(N, M)
+    plan.close()
+    return {"workload": "32 frames 1024x1024, no ZC precoding, plain LS (L_cp = N), K=8 on-grid, 5 dB, rect",
+            "periodogram": {"value": n_frames / (ms_p / 1e3), "unit": "frames/s", "ms_per_step": ms_p,
+                            "bytes_per_frame": 20 * N * M},
+            "fps_sft": {"value": n_frames / (ms_f / 1e3), "unit": "frames/s", "ms_per_step": ms_f,
+                        "cells_read_per_frame": sampled, "bytes_per_frame": 16 * sampled,
+                        "iterations": I, "slices": T},
+            "gain": ms_p / ms_f,
+            "bins_agree_frames": f"{agree}/{n_frames}"}
+
+
+def extra_tc(radar, torch, dev, stream, steps, Yd, Xd, params):
+    """The split-FP16 tensor-core column stage on the headline batch (same
+    inputs and outputs as the FP32 chain): step time, column-kernel time and
+    agreement of the detected bins with the FP32 chain."""
+    plan = radar.Plan(precision=radar.PREC_SPLIT_FP16, **params)
+    ref = radar.Plan(**params)
+    o1 = radar.alloc_outputs(plan, FRAMES, dev)
+    o2 = radar.alloc_outputs(ref, FRAMES, dev)
+
+    def step():
+        radar.ofdm_radar_process(plan, Yd, Xd, FRAMES, o1["map"], o1["targets"], o1["n_targets"], o1["status"],
+                                 stream)
+
+    for _ in range(3):
+        step()
+    radar.ofdm_radar_process(ref, Yd, Xd, FRAMES, o2["map"], o2["targets"], o2["n_targets"], o2["status"], stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    plan.timing_enable(True)
+    for _ in range(steps):
+        step()
+    torch.cuda.synchronize()
+    kt = plan.timing_read()
+    plan.timing_enable(False)
+    col = kt["column"][0] / max(kt["column"][1], 1)
+    peak, _ = load_peaks()
+    a = radar.targets_view(o1["targets"], FRAMES, plan.max_targets)
+    b = radar.targets_view(o2["targets"], FRAMES, ref.max_targets)
+    same = sum([(int(t["r"]), int(t["s"])) for t in a[f][:int(o1["n_targets"][f])]] ==
+               [(int(t["r"]), int(t["s"])) for t in b[f][:int(o2["n_targets"][f])]] for f in range(FRAMES))
+    m1, m2 = o1["map"].double(), o2["map"].double()
+    rel = float(((m1 - m2).norm() / m2.norm()).item())
+    plan.close()
+    ref.close()
+    return {"workload": WORKLOAD, "precision": "split fp16 (hi + lo, 3 products, fp32 accumulation in TMEM)",
+            "value": FRAMES / (ms / 1e3), "unit": "frames/s", "ms_per_step": ms,
+            "column_ms": col, "column_hbm_frac": COLUMN_BYTES_PER_FRAME * FRAMES / (col / 1e3) / 1e9 / peak,
+            "map_rel_l2_vs_fp32_chain": rel, "frames_with_same_bins_as_fp32": f"{same}/{FRAMES}"}
 
 
 def _hits(tv, nt, truth, M):
@@ -592,6 +693,16 @@ def run_ours(args):
             extra["sparse_fps_vs_periodogram"] = extra_fps(radar, torch, dev, stream, max(3, min(args.steps, 10)))
         except Exception as exc:
             extra["sparse_fps_vs_periodogram"] = {"error": str(exc)}
+        try:
+            extra["sparse_fps_ls_vs_periodogram"] = extra_fps_ls(radar, torch, dev, stream,
+                                                                 max(3, min(args.steps, 10)))
+        except Exception as exc:
+            extra["sparse_fps_ls_vs_periodogram"] = {"error": str(exc)}
+        try:
+            extra["tensor_core_split_fp16"] = extra_tc(radar, torch, dev, stream, max(3, min(args.steps, 10)), Yd, Xd,
+                                                       params)
+        except Exception as exc:
+            extra["tensor_core_split_fp16"] = {"error": str(exc)}
         try:
             extra["learned_vs_plain"] = extra_learned(radar, torch, dev, stream, max(3, min(args.steps, 10)))
         except Exception as exc:

@@ -17,8 +17,10 @@
  *   Calls are asynchronous on it; no output is valid before the caller syncs.
  * - Return value: OFDM_OK (0) or a negative OFDM_ERR_* code.  Invalid sizes
  *   or pointers are rejected before anything is launched.
- * - No entry point except ofdm_radar_plan_create and the *_host helpers
- *   allocates device memory.
+ * - No entry point allocates device memory except ofdm_radar_plan_create,
+ *   ofdm_radar_learned_prepare, the *_host helpers and the batch creation,
+ *   and, on their first use, the workspace of ofdm_fps_sft and the twiddle
+ *   table of ofdm_tx_amplifier.
  * - Per-frame `status` words carry OFDM_STATUS_* bits.
  */
 #ifndef OFDM_RADAR_H
@@ -42,21 +44,44 @@ enum {
 };
 
 enum { OFDM_WINDOW_RECT = 0, OFDM_WINDOW_HANN = 1, OFDM_WINDOW_HAMMING = 2 };
-enum { OFDM_DETECT_TOPK = 0, OFDM_DETECT_THRESHOLD = 1 };
-enum { OFDM_PREC_FP32 = 0, OFDM_PREC_SPLIT_BF16 = 1 };
+/* Detection (Eq. (18)): the max_targets strongest 8-neighbour local maxima
+ * (TOPK), those at or above the global threshold eta = -sigma^2 ln P_fa
+ * (THRESHOLD), or those at or above a locally estimated threshold (CFAR:
+ * alpha(n) times the mean of the n training cells around the cell, within
+ * cfar_guard + cfar_train rows and columns but outside the guard square, on
+ * support rows; alpha(n) = n (P_fa^(-1/n) - 1) gives P_fa exactly for
+ * exponential noise). */
+enum { OFDM_DETECT_TOPK = 0, OFDM_DETECT_THRESHOLD = 1, OFDM_DETECT_CFAR = 2 };
+/* Arithmetic of the two N-point DFTs of the column stage (the ZC transform
+ * and DFT-CE's inverse DFT):
+ *   OFDM_PREC_FP32        FP32 FFTs on the CUDA cores (any supported size);
+ *   OFDM_PREC_SPLIT_BF16  not built: BF16's 8-bit significand needs three
+ *                         pieces per operand (six products) for FP32-level
+ *                         accuracy, twice the products of split FP16;
+ *   OFDM_PREC_SPLIT_FP16  32-point DFT matrix products on the tensor cores
+ *                         with FP16 hi + lo operands (three products, FP32
+ *                         accumulation; about 2^-21 relative).  N = 1024,
+ *                         M a multiple of 4, L_cp <= 256, Y and X 16-byte
+ *                         aligned.  Everything after the column stage is the
+ *                         FP32 path's. */
+enum { OFDM_PREC_FP32 = 0, OFDM_PREC_SPLIT_BF16 = 1, OFDM_PREC_SPLIT_FP16 = 2 };
 
 enum {
   OFDM_STATUS_ZERO_X = 1u,     /* a precoded transmit cell was exactly 0; its F was set to 0 */
   OFDM_STATUS_NONFINITE = 2u,  /* a non-finite value reached the range profile */
   OFDM_STATUS_OVERFLOW = 4u,   /* threshold mode: more targets than max_targets */
-  OFDM_STATUS_FEW_PEAKS = 8u   /* top-K mode: fewer than max_targets local maxima */
+  OFDM_STATUS_FEW_PEAKS = 8u,  /* top-K mode: fewer than max_targets local maxima */
+  OFDM_STATUS_UNREFINED = 32u, /* an OFDM symbol had more ill-conditioned precoded cells than are
+                                  recomputed in double-float (64); the rest kept FP32 rounding */
+  OFDM_STATUS_TIMEOUT = 64u    /* a bounded wait inside a kernel ran out (the split-FP16 column kernel's
+                                  copy and tensor-core completions): this frame's outputs are invalid */
 };
 
 /* Parameters of one plan.  ofdm_radar_default_params fills the paper's
  * Table I physical constants and the defaults noted here. */
 typedef struct {
   int32_t N, M;          /* subcarriers, OFDM symbols; powers of two, N in [64, 4096], M in [16, 1024] */
-  int32_t N_pad, M_pad;  /* N', M' of Eq. (17); 0 -> N, M.  This build: N' = N, M' a power of 2 >= M */
+  int32_t N_pad, M_pad;  /* N', M' of Eq. (17); 0 -> N, M.  N' = N, 2N, 4N or 8N (<= 4096), M' a power of 2 >= M */
   int32_t L_cp;          /* DFT-CE taps kept (Eq. (21)), 1..N; L_cp == N is plain LS estimation */
   int32_t n_cp;          /* physical CP length for T_s in Eq. (19); 0 -> L_cp */
   int32_t zc_root;       /* ZC root r' of Sec. III-B (odd, so coprime to N^2); 0 -> no precoding */
@@ -70,6 +95,9 @@ typedef struct {
   float pfa;             /* false-alarm probability of Eq. (18), default 1e-2 */
   float noise_var;       /* per-cell noise power of the map; <= 0 -> estimate from the map */
   double fc_hz, df_hz;   /* carrier and subcarrier spacing (Table I: 77 GHz, 240 kHz) */
+  int32_t cfar_guard;    /* OFDM_DETECT_CFAR: guard cells on each side of the cell (default 1) */
+  int32_t cfar_train;    /* OFDM_DETECT_CFAR: training cells beyond the guard on each side (default 4);
+                            guard + train <= 8 */
 } ofdm_radar_params;
 
 /* One detection.  r = range bin 0..N'-1, s = Doppler bin -M'/2..M'/2-1,
@@ -288,6 +316,23 @@ int ofdm_cnn_bce(const float* logits, const float* labels, int32_t n, float pos_
 int ofdm_cnn_adam(float* theta, const float* grad, float* m, float* v, int32_t n, int32_t step, float lr,
                   float beta1, float beta2, float eps, void* stream);
 
+/* Transmit side of Sec. III-B: the PAPR (Eq. (25)) of each OFDM symbol's
+ * time signal and the share of its power that the power amplifier pushes
+ * out of the occupied band (adjacent-channel interference).
+ *   S     [frames][M][N] complex64: the transmitted frequency-domain grid
+ *         (X_p from ofdm_zc_precode, or the QAM grid without precoding)
+ *   oversample  L in {1, 2, 4, 8}, L N <= 4096: subcarrier k sits at bin k
+ *         (k < N/2) or k + (L-1) N of an L N-point grid; x = its inverse DFT
+ *   q     amplifier state level: |y| = |x| / sqrt(1 + (|x| / (x_bar 10^(q/10)))^2),
+ *         phase kept, x_bar the mean modulus of the symbol's samples (q = 2 in the paper)
+ *   papr  [frames][M] float32, max |x|^2 / mean |x|^2 (linear); may be NULL
+ *   aci   [frames][M] float32, power of DFT(y) outside the N occupied bins over
+ *         its total power; may be NULL
+ * The first call for a given L N builds that transform's twiddle table (a
+ * small device allocation). */
+int ofdm_tx_amplifier(ofdm_radar_plan* plan, const ofdm_c32* S, int32_t frames, int32_t oversample, float q,
+                      float* papr, float* aci, void* stream);
+
 /* Kernel launches made by the last successful call on this plan. */
 int ofdm_radar_last_launch_count(const ofdm_radar_plan* plan);
 
@@ -317,9 +362,10 @@ int ofdm_radar_timing_read(ofdm_radar_plan* plan, float* total_ms, int32_t* laun
  * requests return OFDM_ERR_UNSUPPORTED_SIZE before anything is launched.
  * The first call on a device looks up the array's address
  * (cudaGetSymbolAddress): make it before any stream capture.  Every call on
- * a device shares the array and leaves its contents behind; status words are
- * cleared by each call and tables are rebuilt on the caller's stream when the
- * parameters change.  Calls that overlap on the GPU race on the array.
+ * a device shares the array and leaves its contents behind; each call clears
+ * the status words and work counters it uses on the caller's stream first,
+ * and rebuilds the tables there when the parameters differ from the previous
+ * call's.  Calls that overlap on the GPU race on the array.
  * Calls no cudaMalloc/cudaFree. */
 int ofdm_radar_process_noalloc(const ofdm_radar_params* p, const ofdm_c32* Y, const ofdm_c32* X,
                                int32_t frames, float* out_map, ofdm_target* out_targets,

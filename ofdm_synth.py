@@ -12,7 +12,12 @@ X_p is passed in by the caller (the oracle's in tests, the library's own in
 the benchmark), so this module serves both sides without tying them.
 
 Frames are returned in the paper's orientation (N x M, [k, l]); `to_lk`
-gives the library's [l][k] complex64 layout.  Seeds follow
+gives the library's [l][k] complex64 layout.  The workloads' inputs are
+complex64, so the QAM grid A and the received grid Y are rounded to
+complex64-representable values here (held as complex128): the FP64 oracle
+and the library then consume the same numbers, and the comparison measures
+the chain's arithmetic, not the rounding of its inputs (which the LS division
+amplifies at near-zero precoded cells).  Seeds follow
 seed = 1000 * config_index + frame_index with numpy's PCG64.
 """
 from __future__ import annotations
@@ -145,7 +150,7 @@ def draw_frame(cfg: FrameConfig, seed: int, N: int | None = None, M: int | None 
     qam = qam or cfg.qam
     n_targets = cfg.n_targets if n_targets is None else n_targets
     rng = np.random.Generator(np.random.PCG64(seed))
-    A = qam_symbols(rng, (N, M), qam)
+    A = as_complex64_values(qam_symbols(rng, (N, M), qam))
     rho, nu, b = draw_targets(rng, n_targets, N, M, L_cp, cfg.on_grid, cfg.amp_db)
     snr = float(rng.uniform(*cfg.snr_db)) if cfg.snr_db[1] > cfg.snr_db[0] else cfg.snr_db[0]
     Z = awgn(rng, (N, M), snr) if noise else np.zeros((N, M), dtype=np.complex128)
@@ -153,9 +158,15 @@ def draw_frame(cfg: FrameConfig, seed: int, N: int | None = None, M: int | None 
                  snr_db=snr, seed=seed)
 
 
+def as_complex64_values(a: np.ndarray) -> np.ndarray:
+    """The nearest complex64 values, held as complex128."""
+    return np.asarray(a).astype(np.complex64).astype(np.complex128)
+
+
 def received(frame: Frame, Xp: np.ndarray) -> np.ndarray:
-    """Y = X_p * H + Z for the transmitted grid X_p chosen by the caller."""
-    return Xp * frame.H + frame.Z
+    """Y = X_p * H + Z for the transmitted grid X_p chosen by the caller,
+    rounded to complex64 values (the receiver's input type)."""
+    return as_complex64_values(Xp * frame.H + frame.Z)
 
 
 def to_lk(a: np.ndarray) -> np.ndarray:

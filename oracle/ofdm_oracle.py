@@ -38,7 +38,7 @@ import numpy as np
 C_LIGHT = 3.0e8  # speed of light used by the paper, Table I
 
 WINDOW_RECT, WINDOW_HANN, WINDOW_HAMMING = 0, 1, 2
-DETECT_TOPK, DETECT_THRESHOLD = 0, 1
+DETECT_TOPK, DETECT_THRESHOLD, DETECT_CFAR = 0, 1, 2
 
 STATUS_ZERO_X = 1      # a precoded transmit cell was exactly zero
 STATUS_NONFINITE = 2   # a non-finite input value was seen
@@ -284,6 +284,56 @@ def detect(P: np.ndarray, mode: int, max_targets: int, eta=None) -> Detection:
                      next_power=nxt, count=int(flat.size))
 
 
+def cfar_alpha(n_train: int, pfa: float) -> float:
+    """Cell-averaging CFAR multiplier: for a noise-only cell with exponential
+    power and n_train independent training cells of the same mean,
+    P[P > alpha * mean(training)] = (1 + alpha / n)^-n, which equals P_fa for
+    alpha = n (P_fa^(-1/n) - 1) (-> -ln P_fa, the fixed-sigma threshold of
+    Eq. (18), as n grows)."""
+    return n_train * (pfa ** (-1.0 / n_train) - 1.0)
+
+
+def cfar_detect(P: np.ndarray, rows: np.ndarray, pfa: float, guard: int, train: int, max_targets: int) -> Detection:
+    """Detection with a locally estimated noise level (reading F made local,
+    cell-averaging CFAR).  A cell of the support rows is a target when it is
+    an 8-neighbour local maximum (reading G) and P >= alpha(n) * mean of its
+    training cells: the cells within `guard + train` rows and columns of it
+    but outside the (2 guard + 1)^2 guard square, circular in both axes, that
+    lie on support rows (rows outside the DFT-CE support are zero by
+    construction and carry no noise).  Order and cap as in detect()."""
+    R, C = P.shape
+    on_support = np.zeros(R, dtype=bool)
+    on_support[rows] = True
+    lm = local_maxima(P)
+    w = guard + train
+    hits = []
+    for r in rows:
+        for c in range(C):
+            if not lm[r, c]:
+                continue
+            tot, n = 0.0, 0
+            for dr in range(-w, w + 1):
+                rr = (r + dr) % R
+                if not on_support[rr]:
+                    continue
+                for dc in range(-w, w + 1):
+                    if abs(dr) <= guard and abs(dc) <= guard:
+                        continue
+                    tot += float(P[rr, (c + dc) % C])
+                    n += 1
+            if n and P[r, c] >= cfar_alpha(n, pfa) * tot / n:
+                hits.append(r * C + c)
+    flat = np.array(sorted(hits), dtype=np.int64)
+    vals = P.ravel()[flat] if flat.size else np.zeros(0)
+    order = np.lexsort((flat, -vals.astype(np.float64)))
+    flat, vals = flat[order], vals[order]
+    status = STATUS_OVERFLOW if flat.size > max_targets else 0
+    nxt = float(vals[max_targets]) if flat.size > max_targets else 0.0
+    keep = flat[:max_targets]
+    return Detection(r=keep // C, s=keep % C - C // 2, power=vals[:max_targets], status=status,
+                     next_power=nxt, count=int(flat.size))
+
+
 def symbol_time(N: int, n_cp: int, df_hz: float) -> float:
     """T_s = T + T_cp = (N + N_cp) / (N df), with T = 1/df (Sec. II-B)."""
     return (N + n_cp) / (N * df_hz)
@@ -325,6 +375,8 @@ class Params:
     N_pad: int = 0
     M_pad: int = 0
     n_cp: int = 0              # physical CP length for T_s; 0 -> L_cp
+    cfar_guard: int = 1        # DETECT_CFAR: guard cells on each side
+    cfar_train: int = 4        # DETECT_CFAR: training cells beyond the guard on each side
     fc_hz: float = 77e9
     df_hz: float = 240e3
     extra: dict = field(default_factory=dict)
@@ -360,7 +412,10 @@ def process(Y: np.ndarray, A: np.ndarray, p: Params) -> dict:
     eta = None
     if p.detect_mode == DETECT_THRESHOLD:
         eta = threshold(P, rows, p.pfa, p.noise_var)
-    det = detect(P, p.detect_mode, p.max_targets, eta)
+    if p.detect_mode == DETECT_CFAR:
+        det = cfar_detect(P, rows, p.pfa, p.cfar_guard, p.cfar_train, p.max_targets)
+    else:
+        det = detect(P, p.detect_mode, p.max_targets, eta)
     if nzero:
         det.status |= STATUS_ZERO_X
     Ts = symbol_time(p.N, p.n_cp or p.L_cp, p.df_hz)
@@ -586,3 +641,55 @@ def papr(S: np.ndarray) -> np.ndarray:
     x = dft_matrix(S.shape[0]).conj() @ S
     p = np.abs(x) ** 2
     return p.max(axis=0) / p.mean(axis=0)
+
+
+# --------------------------------------------------------------------------
+# Transmit side: PAPR through a nonlinear power amplifier (Sec. III-B)
+# --------------------------------------------------------------------------
+def hpa(x: np.ndarray, q: float = 2.0) -> np.ndarray:
+    """Power amplifier of Sec. III-B: output modulus |x| / sqrt(1 + (|x| / (x_bar 10^(q/10)))^2)
+    with the input phase kept (AM/AM only).  Reading: x_bar, "the mean of x",
+    is the mean modulus of the symbol's time samples (the mean of the complex
+    samples is about zero for an OFDM symbol); q is the state level (2)."""
+    x = np.asarray(x, dtype=np.complex128)
+    a = np.abs(x)
+    sat = np.mean(a, axis=0, keepdims=True) * 10.0 ** (q / 10.0)
+    g = 1.0 / np.sqrt(1.0 + (a / sat) ** 2)
+    return x * g
+
+
+def oversampled_time(S: np.ndarray, L: int) -> np.ndarray:
+    """Time signal of each OFDM symbol (column of S) sampled L times per
+    subcarrier spacing: subcarrier k sits at frequency k (k < N/2) or k - N
+    (k >= N/2) of an L N-point grid, x[n] = sum_k S[k] e^{+j2pi f_k n / (L N)}
+    (Eq. (1) with oversampling; L = 1 is Eq. (1) itself)."""
+    S = np.asarray(S, dtype=np.complex128)
+    N = S.shape[0]
+    f = np.arange(N)
+    f = np.where(f < N // 2, f, f + (L - 1) * N)          # bins of the L N grid
+    Z = np.zeros((L * N,) + S.shape[1:], dtype=np.complex128)
+    Z[f] = S
+    return dft_matrix(L * N).conj() @ Z
+
+
+def aci_ratio(y: np.ndarray, N: int) -> np.ndarray:
+    """Share of the power of each oversampled symbol y (columns, L N samples)
+    that falls outside the N occupied bins: the adjacent-channel interference
+    that amplifier distortion creates (the spectrum study of Sec. III-B)."""
+    Y = dft_matrix(y.shape[0]) @ np.asarray(y, dtype=np.complex128)
+    LN = y.shape[0]
+    occ = np.zeros(LN, dtype=bool)
+    occ[:N // 2] = True
+    occ[LN - N // 2:] = True
+    p = np.abs(Y) ** 2
+    return p[~occ].sum(axis=0) / p.sum(axis=0)
+
+
+def tx_papr_aci(A: np.ndarray, zc_root: int, L: int = 4, q: float = 2.0, zc_q: int = 0):
+    """Per OFDM symbol: PAPR (Eq. (25)) of the oversampled time signal of the
+    transmitted grid (ZC-precoded when zc_root != 0) and the ACI ratio of the
+    same signal after the amplifier."""
+    Xp = zc_precode(A, zc_root, zc_q) if zc_root else np.asarray(A, dtype=np.complex128)
+    x = oversampled_time(Xp, L)
+    p = np.abs(x) ** 2
+    return p.max(axis=0) / p.mean(axis=0), aci_ratio(hpa(x, q), A.shape[0])

@@ -16,6 +16,7 @@
 // Both 1/N and N factors of Eqs. (20)/(22) and the range sum cancel.
 #include "fft.cuh"
 #include "internal.h"
+#include "refine.cuh"
 
 namespace ofdm {
 
@@ -70,57 +71,6 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return r;
 }
 
-// B_i = sum_k pre_k A_k exp(+2 pi i r' i k / N) in double-float by the whole
-// warp (lane handles k = lane, lane + 32, ...), rounded once to float.  Used
-// for precoded cells so small that the FP32 FFT's normwise rounding would be
-// amplified by the LS division (|X_p|^2 < tau * mean).
-template <int N>
-__device__ __noinline__ float2 refine_cell(const float2* __restrict__ x, int i, const ColumnArgs& a, int lane) {
-  cdf acc = {{0.f, 0.f}, {0.f, 0.f}};
-  for (int k = lane; k < N; k += 32) {
-    const cdf b = cdf_mulf(cdf_ld(a.pre_df + k), __ldg(x + k));
-    const unsigned m = ((unsigned)a.rprime * (unsigned)i * (unsigned)k) & (unsigned)(N - 1);
-    acc = cdf_add(acc, cdf_mul(b, cdf_ld(a.w_df + m)));
-  }
-#pragma unroll
-  for (int off = 16; off; off >>= 1) {
-    acc.re = df_add(acc.re, df_shfl_xor(acc.re, off));
-    acc.im = df_add(acc.im, df_shfl_xor(acc.im, off));
-  }
-  return make_float2(acc.re.hi + acc.re.lo, acc.im.hi + acc.im.lo);
-}
-
-// After the ZC FFT: find this warp's ill-conditioned cells and recompute them.
-// Thread t of a T-thread group holds positions i = t + T q.
-template <int N, int T, int E>
-__device__ __forceinline__ void refine_small_cells(float2* v, const float2* __restrict__ x, const ColumnArgs& a,
-                                                   int t, int lane) {
-  float s2 = 0.f;
-#pragma unroll
-  for (int q = 0; q < E; ++q) s2 += v[q].x * v[q].x + v[q].y * v[q].y;
-#pragma unroll
-  for (int off = 16; off; off >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, off);
-  const float thr = a.refine_tau * s2 * (1.f / (32.f * E));
-  unsigned flags = 0;
-#pragma unroll
-  for (int q = 0; q < E; ++q) flags |= (v[q].x * v[q].x + v[q].y * v[q].y < thr) ? (1u << q) : 0u;
-  unsigned pending = __ballot_sync(0xffffffffu, flags != 0);
-  while (pending) {
-    const int src = __ffs(pending) - 1;
-    const unsigned fm = __shfl_sync(0xffffffffu, flags, src);
-    const int q = __ffs(fm) - 1;
-    const int tsrc = __shfl_sync(0xffffffffu, t, src);
-    const float2 val = refine_cell<N>(x, tsrc + T * q, a, lane);
-    if (lane == src) {
-#pragma unroll
-      for (int qq = 0; qq < E; ++qq)
-        if (qq == q) v[qq] = val;
-      flags &= ~(1u << q);
-    }
-    pending = __ballot_sync(0xffffffffu, flags != 0);
-  }
-}
-
 // True if `pred` holds on any thread of the group (named barrier reduction;
 // every thread of the group must call it).
 template <int T>
@@ -135,16 +85,16 @@ __device__ __forceinline__ bool group_any(int group, bool pred) {
   return r != 0;
 }
 
-constexpr int kRefineList = 64;  // flagged cells refined per symbol (more stay FP32)
+constexpr int kRefineList = 64;  // flagged cells refined per symbol; more set OFDM_STATUS_UNREFINED
 
 // Group form of refine_small_cells for T > 32: the same cells (a warp-local
 // mean sets the threshold) are recomputed by all T threads of the group, each
 // summing N / T terms, so no warp idles at the group's next barrier while
 // another recomputes a cell alone.
 template <int N, int T, int E>
-__device__ __forceinline__ void refine_small_cells_group(float2* v, const float2* __restrict__ x, const ColumnArgs& a,
-                                                         int t, int lane, int group, int* cnt, int* list,
-                                                         cdf* part) {
+__device__ __forceinline__ uint32_t refine_small_cells_group(float2* v, const float2* __restrict__ x,
+                                                             const ColumnArgs& a, int t, int lane, int group,
+                                                             int* cnt, int* list, cdf* part) {
   float s2 = 0.f;
 #pragma unroll
   for (int q = 0; q < E; ++q) s2 += v[q].x * v[q].x + v[q].y * v[q].y;
@@ -154,13 +104,14 @@ __device__ __forceinline__ void refine_small_cells_group(float2* v, const float2
   unsigned flags = 0;
 #pragma unroll
   for (int q = 0; q < E; ++q) flags |= (v[q].x * v[q].x + v[q].y * v[q].y < thr) ? (1u << q) : 0u;
-  if (!group_any<T>(group, flags != 0)) return;
+  if (!group_any<T>(group, flags != 0)) return 0u;
   for (unsigned m = flags; m; m &= m - 1) {
     const int pos = atomicAdd(cnt, 1);
     if (pos < kRefineList) list[pos] = (t << 8) | (__ffs(m) - 1);
   }
   group_sync<T>(group);
-  const int n = min(*cnt, kRefineList);
+  const int n_flagged = *cnt;
+  const int n = min(n_flagged, kRefineList);
   for (int j = 0; j < n; ++j) {
     const int code = list[j], tt = code >> 8, qq = code & 255;
     const int i = tt + T * qq;
@@ -189,6 +140,8 @@ __device__ __forceinline__ void refine_small_cells_group(float2* v, const float2
     group_sync<T>(group);  // part[] is rewritten by the next cell
   }
   if (t == 0) *cnt = 0;    // the next symbol appends after its group_any barrier
+  // more flagged cells than the list holds: the rest stay FP32, and the frame says so
+  return n_flagged > kRefineList ? (uint32_t)OFDM_STATUS_UNREFINED : 0u;
 }
 
 // F_i = Y_i / X_p,i with X_p,i = post_i B_i / sqrt(N), B in v:
@@ -507,8 +460,8 @@ column_group_pipe_kernel(const float2* __restrict__ Y, const float2* __restrict_
       }
       group_fft<N, T, +1, C::SMEM_TABLES>(v, sa, tw, t, group);
       if (a.refine_tau > 0.f)
-        refine_small_cells_group<N, T, E>(v, X + row_off(sym), a, t, lane, group, &s_rcnt[group], s_rlist[group],
-                                          s_rpart[group]);
+        flags |= refine_small_cells_group<N, T, E>(v, X + row_off(sym), a, t, lane, group, &s_rcnt[group],
+                                                   s_rlist[group], s_rpart[group]);
       cp_async_wait<1>();                   // Y(sym)
       group_sync<T>(group);
       flags |= divide_precoded<T, E>(v, sy, true, a, t);
@@ -619,6 +572,9 @@ static cudaError_t launch_column_n(const float2* Y, const float2* X, float2* str
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if constexpr (N == 1024) {
+    if (a.tc_b) return launch_column_tc(Y, X, strip, wstatus, a, s, tickets);
+  }
   if constexpr (N <= 1024) {
     if (a.pipe_warps == 4) return launch_pipe<N, 4>(Y, X, strip, wstatus, a, s, tickets, sms, total);
     if constexpr (N == 1024) {

@@ -148,6 +148,30 @@ __device__ __forceinline__ float det_value(const float* base, const DetectArgs& 
   return base[((long)row << a.logMp) + c];
 }
 
+// CFAR test of the local maximum at input row ri (support-row index), column
+// c, power p: alpha(n) times the mean of the n training cells -- within
+// guard + train rows and columns, outside the guard square, on support rows
+// (circular when the support is the whole map) -- read from the detection's
+// input rows `base`.
+__device__ __noinline__ bool cfar_pass(const float* __restrict__ base, const DetectArgs& a, int ri, int c, float p) {
+  const int g = a.cfar_guard, w = g + a.cfar_train, Mp = a.Mp;
+  float sum = 0.f;
+  int n = 0;
+  for (int dr = -w; dr <= w; ++dr) {
+    int rj = ri + dr;
+    if (a.full) rj &= (a.rows - 1);
+    else if (rj < 0 || rj >= a.rows) continue;   // off the support: zero by construction, not noise
+    const float* rp = base + ((long)(a.compact ? rj : ((a.row0 + rj) & (a.Np - 1))) << a.logMp);
+    const bool in_guard_rows = dr >= -g && dr <= g;
+    for (int dc = -w; dc <= w; ++dc) {
+      if (in_guard_rows && dc >= -g && dc <= g) continue;
+      sum += __ldg(rp + ((c + dc) & (Mp - 1)));
+      ++n;
+    }
+  }
+  return n > 0 && p >= a.cfar_alpha[n] * (sum / (float)n);
+}
+
 // Block-wide bitonic sort of buf[0..n) (n a power of two), keys descending.
 __device__ void bitonic_desc(uint64_t* buf, int n) {
   for (int k = 2; k <= n; k <<= 1) {
@@ -232,7 +256,8 @@ __device__ __forceinline__ uint64_t warp_merge_lists(P src, int nlists, int K, i
 template <int LOGC>
 __device__ __forceinline__ void band_detect(float* tile, ofdm_target* __restrict__ out, int32_t* __restrict__ n_out,
                                             uint32_t* __restrict__ status, uint32_t* __restrict__ wstatus,
-                                            const DetectArgs& a, int band, int f, int t0, int tr) {
+                                            const DetectArgs& a, int band, int f, int t0, int tr,
+                                            const float* __restrict__ base) {
   constexpr int C = 1 << LOGC, NR = kCells >> LOGC;
   __shared__ uint64_t buf[kBandCap];
   __shared__ unsigned s_n, s_cnt;
@@ -241,6 +266,7 @@ __device__ __forceinline__ void band_detect(float* tile, ofdm_target* __restrict
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int K = a.K, Mp = a.Mp, logMp = a.logMp;
   const bool thr = a.mode == OFDM_DETECT_THRESHOLD;
+  const bool cfar = a.mode == OFDM_DETECT_CFAR;   // base holds the frame's input rows
   const float eta = thr ? (a.use_fixed_eta ? a.eta_fixed : a.eta[f]) : 0.f;
   if (tid == 0) { s_n = 0; s_cnt = 0; }
 
@@ -284,7 +310,8 @@ __device__ __forceinline__ void band_detect(float* tile, ofdm_target* __restrict
       const float nmax = fmaxf(up3, fmaxf(mid2, fmaxf(dc, fmaxf(dl, dr))));
       const float p = mc;
       // fmaxf skips NaN, so this is "no neighbour compares greater"
-      bool cand = i < tr && p > 0.f && !(nmax > p) && (!thr || p >= eta);
+      bool cand = i < tr && p > 0.f && !(nmax > p) && (!thr || p >= eta) &&
+                  (!cfar || cfar_pass(base, a, t0 + i, c, p));
       const uint32_t r = (rbase + (uint32_t)i) & (uint32_t)(a.Np - 1);
       if (cand && nmax == p) cand = !tie_lost(tile, logMp, a.Np, (int)r, i + 1, c, p);
       const uint64_t key =
@@ -395,7 +422,7 @@ __device__ __forceinline__ void band_detect(float* tile, ofdm_target* __restrict
       const unsigned total = atomicExch(a.counts + f, 0u);
       uint32_t st = wstatus ? wstatus[f] : 0u;
       if (a.mode == OFDM_DETECT_TOPK && total < (unsigned)K) st |= OFDM_STATUS_FEW_PEAKS;
-      if (a.mode == OFDM_DETECT_THRESHOLD && total > (unsigned)K) st |= OFDM_STATUS_OVERFLOW;
+      if (a.mode != OFDM_DETECT_TOPK && total > (unsigned)K) st |= OFDM_STATUS_OVERFLOW;
       if (status) status[g] = st;
       if (n_out) n_out[g] = nv;
       if (wstatus) wstatus[f] = 0u;  // ready for the next call
@@ -437,7 +464,7 @@ detect_band_kernel(const float* __restrict__ src, ofdm_target* __restrict__ out,
   }
   asm volatile("cp.async.commit_group;\n" ::: "memory");
   asm volatile("cp.async.wait_all;\n" ::: "memory");
-  band_detect<LOGC>(tile, out, n_out, status, wstatus, a, band, f, t0, tr);
+  band_detect<LOGC>(tile, out, n_out, status, wstatus, a, band, f, t0, tr, base);
 }
 
 // Fused Doppler stage and detection (top-K mode, 64 <= M' <= 256; frames
@@ -490,7 +517,7 @@ doppler_band_kernel(const float2* __restrict__ strip, float* __restrict__ map, o
       if (mrow) __stcs(mrow + c, p);
     }
   }
-  band_detect<LOGC>(tile, out, n_out, status, wstatus, a, band, f, t0, tr);
+  band_detect<LOGC>(tile, out, n_out, status, wstatus, a, band, f, t0, tr, nullptr);
 }
 
 __global__ void __launch_bounds__(1024) median_kernel(const float* __restrict__ src, DetectArgs a) {

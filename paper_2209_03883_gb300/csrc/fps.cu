@@ -1,17 +1,25 @@
 // fps.cu -- FPS-SFT (Sec. III-C): the sparse alternative to the 2D
-// periodogram, on the DFT-CE channel estimate H'.
+// periodogram, on the DFT-CE channel estimate H' (or, for plain LS
+// estimation without precoding, on F = Y / X itself).
 //
-// One CTA per frame runs every iteration (peeling needs the previous
-// iteration's result, so the frame stays on one SM):
-//   1. slice samples s_j[n] = H'[(a0 n + t0_j) mod N, (a1 n + t1_j) mod M]
-//      evaluated straight from the kept DFT-CE taps (the strip written by the
-//      column kernel with a rect stencil holds N h[n]):
-//      H'[k, l] = (1/N) sum_{n < L_cp} (N h[n, l]) e^{-2 pi i n k / N}  (Eq. (22));
-//   2. one warp per slice: Q-point DFT (Q = lcm(N, M) = max(N, M) here);
-//   3. removal of the frequencies already recovered from every slice;
-//   4. bin energy test against the median of the bin energies;
-//   5. ML decoding along each surviving bin's projection line with a
-//      coherence test (1-sparsity), amplitude from the coherent sum.
+// The slice positions of every iteration are inputs, so the samples and
+// their Q-point DFTs do not depend on what earlier iterations recover; only
+// the peeling and the decoding do.  The work is therefore split by what it
+// depends on:
+//   1. fps_sample_taps_kernel / fps_sample_direct_kernel (all frames, all
+//      iterations and slices at once, spread over the GPU):
+//        s_j[n] = H'[(a0 n + t0_j) mod N, (a1 n + t1_j) mod M],  n < Q
+//      from the kept DFT-CE taps of the strip (rect stencil, N h[n]):
+//        H'[k, l] = (1/N) sum_{n < L_cp} (N h[n, l]) e^{-2 pi i n k / N}  (Eq. (22)),
+//      one CTA per 8 columns l (every slice visits each column Q / M times),
+//      or, when F is cell-local (no ZC division to undo and L_cp = N), the
+//      sampled cells of Y and X alone: s = Y / X (Eq. (16)) -- the regime in
+//      which FPS-SFT reads a small fraction of the frame;
+//   2. fps_fft_kernel: the Q-point DFT of every slice (one warp each);
+//   3. fps_decode_kernel (one CTA per frame, iterations in order): removal of
+//      the recovered frequencies from every slice, bin energies, the median
+//      threshold, ML decoding along each surviving bin's projection line
+//      with the coherence (1-sparsity) test, and the recovered list.
 #include <float.h>
 
 #include "fft.cuh"
@@ -23,42 +31,124 @@ constexpr int kFpsThreads = 256;
 constexpr int kFpsMaxT = 8;        // slices per iteration
 constexpr int kFpsMaxRec = 64;     // recovered frequencies per frame
 constexpr int kFpsMaxCand = 256;   // candidate bins decoded per iteration
+constexpr int kFpsCols = 8;        // columns per CTA of the sampling kernel
 
 struct FpsRec { int f0, f1; float2 a; };
-
-template <int Q>
-struct FpsLayout {
-  static constexpr int SL = smem_elems(Q);  // float2 per slice (padded for the FFT exchange)
-};
 
 __device__ __forceinline__ float2 ptab_at(const float2* ptab, int m, int sign) {
   float2 w = ptab[m];
   if (sign < 0) w.y = -w.y;
   return w;
 }
+__device__ __forceinline__ int inv_mod_pow2(int a1, int M) {   // a1^{-1} mod M (a1 odd, M a power of two)
+  unsigned inv = 1u;
+  for (int k = 0; k < 5; ++k) inv = inv * (2u - (unsigned)a1 * inv);
+  return (int)(inv & (unsigned)(M - 1));
+}
 
+// ---------------------------------------------------------------- 1. samples from the taps
+// CTA = (8 consecutive columns, frame); warp w owns column l0 + w and loops
+// over its (iteration, slice, repeat) items, one per lane.
+__global__ void __launch_bounds__(kFpsThreads)
+fps_sample_taps_kernel(const float2* __restrict__ strip, const int32_t* __restrict__ slices,
+                       float2* __restrict__ S, FpsArgs a) {
+  extern __shared__ __align__(16) unsigned char fps_smem[];
+  float2* taps = reinterpret_cast<float2*>(fps_smem);   // [rows][kFpsCols]
+  const int f = blockIdx.y, l0 = blockIdx.x * kFpsCols;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int N = a.N, M = a.M, T = a.T, rows = a.rows, Q = a.Q;
+  const float2* g = strip + (size_t)f * rows * M;
+  for (int e = tid; e < rows * kFpsCols; e += kFpsThreads) {
+    const int n = e / kFpsCols, c = e % kFpsCols;
+    taps[e] = (l0 + c < M) ? g[(size_t)n * M + l0 + c] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  const int l = l0 + warp;
+  if (l >= M) return;
+  const int reps = Q / M;
+  const int items = a.iterations * T * reps;
+  for (int item = lane; item < items; item += 32) {
+    const int rep = item % reps, rest = item / reps;
+    const int j = rest % T, it = rest / T;
+    const int32_t* sp = slices + ((size_t)f * a.iterations + it) * (2 + 2 * T);
+    const int a0 = sp[0], a1 = sp[1], t0 = sp[2 + 2 * j], t1 = sp[3 + 2 * j];
+    const int n0 = (int)(((unsigned)inv_mod_pow2(a1, M) * (unsigned)((l - t1) & (M - 1))) & (unsigned)(M - 1));
+    const int n = n0 + M * rep;
+    const int k = (int)((((long)a0 * n + t0) % N + N) % N);
+    float2 acc = make_float2(0.f, 0.f);
+    for (int nn = 0; nn < rows; ++nn) {
+      const float4 w4 = __ldg(a.w_df + (int)(((unsigned)nn * (unsigned)k) & (unsigned)(N - 1)));
+      const float2 w = make_float2(w4.x, -w4.z);   // exp(-2 pi i nn k / N)
+      acc = cadd(acc, cmul(taps[nn * kFpsCols + warp], w));
+    }
+    S[(((size_t)f * a.iterations + it) * T + j) * Q + n] = cscale(acc, a.invN);
+  }
+}
+
+// ---------------------------------------------------------------- 1'. samples of F = Y / X
+// Thread per sample; the only bytes read are the sampled cells of Y and X.
+__global__ void __launch_bounds__(kFpsThreads)
+fps_sample_direct_kernel(const float2* __restrict__ Y, const float2* __restrict__ X,
+                         const int32_t* __restrict__ slices, float2* __restrict__ S,
+                         uint32_t* __restrict__ wstatus, FpsArgs a) {
+  const int N = a.N, M = a.M, T = a.T, Q = a.Q;
+  const long per_frame = (long)a.iterations * T * Q;
+  const long total = per_frame * a.frames;
+  for (long e = (long)blockIdx.x * kFpsThreads + threadIdx.x; e < total; e += (long)gridDim.x * kFpsThreads) {
+    const int f = (int)(e / per_frame);
+    const long r = e % per_frame;
+    const int n = (int)(r % Q);
+    const int j = (int)((r / Q) % T), it = (int)(r / ((long)Q * T));
+    const int32_t* sp = slices + ((size_t)f * a.iterations + it) * (2 + 2 * T);
+    const int k = (int)((((long)sp[0] * n + sp[2 + 2 * j]) % N + N) % N);
+    const int l = (int)((((long)sp[1] * n + sp[3 + 2 * j]) % M + M) % M);
+    const size_t cell = ((size_t)f * M + l) * N + k;
+    const float2 yv = __ldcs(Y + cell), xv = __ldcs(X + cell);
+    const float d2 = xv.x * xv.x + xv.y * xv.y;
+    if (d2 == 0.f) atomicOr(wstatus + f, (uint32_t)OFDM_STATUS_ZERO_X);
+    S[e] = d2 > 0.f ? cscale(cmulc(yv, xv), 1.f / d2) : make_float2(0.f, 0.f);
+  }
+}
+
+// ---------------------------------------------------------------- 2. slice DFTs
 template <int Q>
 __global__ void __launch_bounds__(kFpsThreads)
-fps_kernel(const float2* __restrict__ strip, const int32_t* __restrict__ slices, ofdm_target* __restrict__ out,
-           int32_t* __restrict__ n_out, uint32_t* __restrict__ wstatus, FpsArgs a) {
-  using Lay = FpsLayout<Q>;
+fps_fft_kernel(float2* __restrict__ S, long nslices, const float2* __restrict__ twQ) {
   extern __shared__ __align__(16) unsigned char fps_smem[];
-  float2* S = reinterpret_cast<float2*>(fps_smem);                 // T slices
-  float2* ptab = S + (size_t)kFpsMaxT * Lay::SL;                    // exp(+2 pi i m / Q)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float2* sm = reinterpret_cast<float2*>(fps_smem) + (size_t)warp * smem_elems(Q);
+  const long sl = (long)blockIdx.x * (kFpsThreads / 32) + warp;
+  if (sl >= nslices) return;
+  float2* s = S + sl * Q;
+  constexpr int E = Q / 32;
+  float2 v[E];
+#pragma unroll
+  for (int q = 0; q < E; ++q) v[q] = s[lane + 32 * q];
+  group_fft<Q, 32, -1>(v, sm, twQ, lane, 0);
+#pragma unroll
+  for (int q = 0; q < E; ++q) s[lane + 32 * q] = v[q];
+}
+
+// ---------------------------------------------------------------- 3. iterations of one frame
+template <int Q>
+__global__ void __launch_bounds__(kFpsThreads)
+fps_decode_kernel(const float2* __restrict__ Sg, const int32_t* __restrict__ slices, ofdm_target* __restrict__ out,
+                  int32_t* __restrict__ n_out, uint32_t* __restrict__ wstatus, FpsArgs a) {
+  extern __shared__ __align__(16) unsigned char fps_smem[];
+  float2* S = reinterpret_cast<float2*>(fps_smem);                 // T slices of this iteration
+  float2* ptab = S + (size_t)kFpsMaxT * Q;                          // exp(+2 pi i m / Q)
   float* E = reinterpret_cast<float*>(ptab + Q);                    // bin energy
   float* srt = E + Q;                                               // sorted copy
   FpsRec* rec = reinterpret_cast<FpsRec*>(srt + Q);                 // recovered list
   FpsRec* fnd = rec + kFpsMaxRec;                                   // found this iteration
   int* cand = reinterpret_cast<int*>(fnd + kFpsMaxCand);            // candidate bins
-  float2* taps = reinterpret_cast<float2*>(cand + kFpsMaxCand);     // [rows][CB] batch of tap columns
   __shared__ int s_nrec, s_ncand, s_nfnd;
   __shared__ float s_peak;
 
   const int f = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int N = a.N, M = a.M, T = a.T, rows = a.rows;
+  const int N = a.N, M = a.M, T = a.T;
   const int qn = Q / N, qm = Q / M;
-  const float2* g = strip + (size_t)f * rows * M;
 
   for (int m = tid; m < Q; m += kFpsThreads) {
     double s, c;
@@ -71,77 +161,30 @@ fps_kernel(const float2* __restrict__ strip, const int32_t* __restrict__ slices,
   for (int it = 0; it < a.iterations; ++it) {
     const int32_t* sp = slices + ((size_t)f * a.iterations + it) * (2 + 2 * T);
     const int a0 = sp[0], a1 = sp[1];
-    unsigned inv = 1u;  // a1^{-1} mod 2^32 by Newton's iteration (a1 odd), then mod M
-    for (int k = 0; k < 5; ++k) inv = inv * (2u - (unsigned)a1 * inv);
-    const int a1inv = (int)(inv & (unsigned)(M - 1));
-
-    // ---- 1. slice samples, CB tap columns at a time
-    for (int l0 = 0; l0 < M; l0 += a.CB) {
-      __syncthreads();
-      for (int e = tid; e < rows * a.CB; e += kFpsThreads) {
-        const int n = e / a.CB, cb = e % a.CB;
-        taps[e] = (l0 + cb < M) ? g[(size_t)n * M + l0 + cb] : make_float2(0.f, 0.f);
-      }
-      __syncthreads();
-      // items (column, slice, repeat) handled by quads of lanes
-      const int reps = Q / M;
-      const int items = a.CB * T * reps;
-      for (int it4 = tid >> 2; it4 < items; it4 += kFpsThreads >> 2) {
-        const int cb = it4 % a.CB, rest = it4 / a.CB;
-        const int j = rest % T, rep = rest / T;
-        const int l = l0 + cb;
-        if (l >= M) continue;
-        const int t0 = sp[2 + 2 * j], t1 = sp[3 + 2 * j];
-        const int n0 = (int)(((unsigned)a1inv * (unsigned)((l - t1) & (M - 1))) & (unsigned)(M - 1));
-        const int n = n0 + M * rep;
-        const int k = (int)(((long)a0 * n + t0) % N + N) % N;
-        float2 acc = make_float2(0.f, 0.f);
-        for (int nn = (tid & 3); nn < rows; nn += 4) {
-          const float4 w4 = __ldg(a.w_df + (int)(((unsigned)nn * (unsigned)k) & (unsigned)(N - 1)));
-          const float2 w = make_float2(w4.x, -w4.z);  // exp(-2 pi i nn k / N)
-          acc = cadd(acc, cmul(taps[nn * a.CB + cb], w));
-        }
-        const unsigned qmask = 0xfu << (lane & ~3);  // the four lanes of this item
-        acc.x += __shfl_xor_sync(qmask, acc.x, 1);
-        acc.y += __shfl_xor_sync(qmask, acc.y, 1);
-        acc.x += __shfl_xor_sync(qmask, acc.x, 2);
-        acc.y += __shfl_xor_sync(qmask, acc.y, 2);
-        if ((tid & 3) == 0) S[(size_t)j * Lay::SL + n] = cscale(acc, a.invN);
+    const int a1inv = inv_mod_pow2(a1, M);
+    const float4* src = reinterpret_cast<const float4*>(Sg + ((size_t)f * a.iterations + it) * T * Q);
+    for (int e = tid; e < T * Q / 2; e += kFpsThreads) reinterpret_cast<float4*>(S)[e] = src[e];
+    __syncthreads();
+    // ---- remove the recovered frequencies (serial per slice: bins may coincide)
+    if (tid < T) {
+      const int j = tid;
+      float2* sj = S + (size_t)j * Q;
+      const int t0 = sp[2 + 2 * j], t1 = sp[3 + 2 * j];
+      for (int r = 0; r < s_nrec; ++r) {
+        const int f0 = rec[r].f0, f1 = rec[r].f1;
+        const int m = (int)(((long)a0 * f0 * qn + (long)a1 * f1 * qm) % Q);
+        const int ph = (int)(((long)f0 * t0 * qn + (long)f1 * t1 * qm) % Q);
+        const float2 c = cscale(cmul(rec[r].a, ptab_at(ptab, ph, +1)), (float)Q * a.invNM);
+        sj[m] = csub(sj[m], c);
       }
     }
     __syncthreads();
 
-    // ---- 2. Q-point DFT of each slice (warp j), natural order in and out
-    for (int j = warp; j < T; j += kFpsThreads / 32) {
-      float2* sj = S + (size_t)j * Lay::SL;
-      constexpr int E2 = Q / 32;
-      float2 v[E2];
-#pragma unroll
-      for (int q = 0; q < E2; ++q) v[q] = sj[lane + 32 * q];
-      group_fft<Q, 32, -1>(v, sj, a.twQ, lane, 0);
-      __syncwarp();
-#pragma unroll
-      for (int q = 0; q < E2; ++q) sj[lane + 32 * q] = v[q];
-      __syncwarp();
-      // ---- 3. remove the recovered frequencies (serial per slice: bins may coincide)
-      if (lane == 0) {
-        const int t0 = sp[2 + 2 * j], t1 = sp[3 + 2 * j];
-        for (int r = 0; r < s_nrec; ++r) {
-          const int f0 = rec[r].f0, f1 = rec[r].f1;
-          const int m = (int)(((long)a0 * f0 * qn + (long)a1 * f1 * qm) % Q);
-          const int ph = (int)(((long)f0 * t0 * qn + (long)f1 * t1 * qm) % Q);
-          const float2 c = cscale(cmul(rec[r].a, ptab_at(ptab, ph, +1)), (float)Q * a.invNM);
-          sj[m] = csub(sj[m], c);
-        }
-      }
-    }
-    __syncthreads();
-
-    // ---- 4. bin energies, median threshold, running peak
+    // ---- bin energies, median threshold, running peak
     for (int m = tid; m < Q; m += kFpsThreads) {
       float e = 0.f;
       for (int j = 0; j < T; ++j) {
-        const float2 v = S[(size_t)j * Lay::SL + m];
+        const float2 v = S[(size_t)j * Q + m];
         e += v.x * v.x + v.y * v.y;
       }
       E[m] = e / (float)T;
@@ -176,7 +219,7 @@ fps_kernel(const float2* __restrict__ strip, const int32_t* __restrict__ slices,
     const int ncand = min(s_ncand, kFpsMaxCand);
     if (ncand == 0) break;  // nothing above the noise: done (uniform: shared value)
 
-    // ---- 5. ML decoding along each candidate bin's line (one warp per bin)
+    // ---- ML decoding along each candidate bin's line (one warp per bin)
     for (int ci = warp; ci < ncand; ci += kFpsThreads / 32) {
       const int m = cand[ci];
       float best = -1.f;
@@ -190,7 +233,7 @@ fps_kernel(const float2* __restrict__ strip, const int32_t* __restrict__ slices,
         for (int j = 0; j < T; ++j) {
           const int t0 = sp[2 + 2 * j], t1 = sp[3 + 2 * j];
           const int ph = (int)(((long)f0 * t0 * qn + (long)f1 * t1 * qm) % Q);
-          acc = cadd(acc, cmul(S[(size_t)j * Lay::SL + m], ptab_at(ptab, ph, -1)));
+          acc = cadd(acc, cmul(S[(size_t)j * Q + m], ptab_at(ptab, ph, -1)));
         }
         const float mag = acc.x * acc.x + acc.y * acc.y;
         if (mag > best) { best = mag; bf0 = f0; bf1 = f1; bacc = acc; }
@@ -209,7 +252,7 @@ fps_kernel(const float2* __restrict__ strip, const int32_t* __restrict__ slices,
       if (lane == 0 && bf0 >= 0) {
         float sumabs = 0.f;
         for (int j = 0; j < T; ++j) {
-          const float2 v = S[(size_t)j * Lay::SL + m];
+          const float2 v = S[(size_t)j * Q + m];
           sumabs += sqrtf(v.x * v.x + v.y * v.y);
         }
         if (sqrtf(best) >= a.coherence_min * sumabs) {
@@ -277,28 +320,58 @@ fps_kernel(const float2* __restrict__ strip, const int32_t* __restrict__ slices,
   }
 }
 
+size_t fps_workspace_elems(int frames, int iterations, int T, int Q) {
+  return (size_t)frames * iterations * T * Q;
+}
+
 template <int Q>
-static cudaError_t launch_fps_q(const float2* strip, const int32_t* slices, ofdm_target* out, int32_t* n_out,
-                                uint32_t* wstatus, const FpsArgs& a, cudaStream_t s) {
-  const size_t smem = (size_t)kFpsMaxT * FpsLayout<Q>::SL * sizeof(float2) + Q * sizeof(float2) +
-                      2 * Q * sizeof(float) + (kFpsMaxRec + kFpsMaxCand) * sizeof(FpsRec) +
-                      kFpsMaxCand * sizeof(int) + (size_t)a.rows * a.CB * sizeof(float2);
-  cudaError_t e = cudaFuncSetAttribute(fps_kernel<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+static cudaError_t launch_fps_q(const float2* strip, const float2* Y, const float2* X, const int32_t* slices,
+                                float2* S, ofdm_target* out, int32_t* n_out, uint32_t* wstatus, const FpsArgs& a,
+                                cudaStream_t s, int* launches) {
+  cudaError_t e;
+  if (a.direct) {
+    const long total = (long)a.frames * a.iterations * a.T * Q;
+    long blocks = (total + kFpsThreads - 1) / kFpsThreads;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    fps_sample_direct_kernel<<<(unsigned)blocks, kFpsThreads, 0, s>>>(Y, X, slices, S, wstatus, a);
+  } else {
+    const size_t smem = (size_t)a.rows * kFpsCols * sizeof(float2);
+    e = cudaFuncSetAttribute(fps_sample_taps_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((a.M + kFpsCols - 1) / kFpsCols), (unsigned)a.frames);
+    fps_sample_taps_kernel<<<grid, kFpsThreads, smem, s>>>(strip, slices, S, a);
+  }
+  ++*launches;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  {
+    const long nsl = (long)a.frames * a.iterations * a.T;
+    const size_t smem = (size_t)(kFpsThreads / 32) * smem_elems(Q) * sizeof(float2);
+    e = cudaFuncSetAttribute(fps_fft_kernel<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const long blocks = (nsl + kFpsThreads / 32 - 1) / (kFpsThreads / 32);
+    fps_fft_kernel<Q><<<(unsigned)blocks, kFpsThreads, smem, s>>>(S, nsl, a.twQ);
+    ++*launches;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  const size_t smem = (size_t)kFpsMaxT * Q * sizeof(float2) + Q * sizeof(float2) + 2 * Q * sizeof(float) +
+                      (kFpsMaxRec + kFpsMaxCand) * sizeof(FpsRec) + kFpsMaxCand * sizeof(int);
+  e = cudaFuncSetAttribute(fps_decode_kernel<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  fps_kernel<Q><<<a.frames, kFpsThreads, smem, s>>>(strip, slices, out, n_out, wstatus, a);
+  fps_decode_kernel<Q><<<a.frames, kFpsThreads, smem, s>>>(S, slices, out, n_out, wstatus, a);
+  ++*launches;
   return cudaGetLastError();
 }
 
-cudaError_t launch_fps(int Q, const float2* strip, const int32_t* slices, ofdm_target* out, int32_t* n_out,
-                       uint32_t* wstatus, const FpsArgs& a, cudaStream_t s, int* launches) {
-  ++*launches;
+cudaError_t launch_fps(int Q, const float2* strip, const float2* Y, const float2* X, const int32_t* slices,
+                       float2* S, ofdm_target* out, int32_t* n_out, uint32_t* wstatus, const FpsArgs& a,
+                       cudaStream_t s, int* launches) {
   switch (Q) {
-    case 64: return launch_fps_q<64>(strip, slices, out, n_out, wstatus, a, s);
-    case 128: return launch_fps_q<128>(strip, slices, out, n_out, wstatus, a, s);
-    case 256: return launch_fps_q<256>(strip, slices, out, n_out, wstatus, a, s);
-    case 512: return launch_fps_q<512>(strip, slices, out, n_out, wstatus, a, s);
-    case 1024: return launch_fps_q<1024>(strip, slices, out, n_out, wstatus, a, s);
-    default: --*launches; return cudaErrorInvalidValue;
+    case 64: return launch_fps_q<64>(strip, Y, X, slices, S, out, n_out, wstatus, a, s, launches);
+    case 128: return launch_fps_q<128>(strip, Y, X, slices, S, out, n_out, wstatus, a, s, launches);
+    case 256: return launch_fps_q<256>(strip, Y, X, slices, S, out, n_out, wstatus, a, s, launches);
+    case 512: return launch_fps_q<512>(strip, Y, X, slices, S, out, n_out, wstatus, a, s, launches);
+    case 1024: return launch_fps_q<1024>(strip, Y, X, slices, S, out, n_out, wstatus, a, s, launches);
+    default: return cudaErrorInvalidValue;
   }
 }
 

@@ -30,6 +30,11 @@ struct ColumnArgs {
   int pipe_warps;                // pipelined kernel variant: 0 = most warps that fit, 4 = 4 warps per CTA,
                                  // 2 = groups of N / 16 threads, 16 points each (N >= 1024, needs tw_group)
   const float2* tw_group = nullptr;  // N >= 1024: pass twiddles for 16 points per thread, or null
+  // Split-FP16 tensor-core form (N = 1024): the 32-point DFT operand tables
+  // (hi and lo halves, tc_table_bytes() each) and the 32 x 32 inter-stage
+  // twiddles exp(+2 pi i n1 k2 / 1024) / 32.  Null: the FP32 kernels.
+  const uint4* tc_b = nullptr;
+  const float2* tc_t12 = nullptr;
 };
 
 struct ZctArgs {
@@ -69,6 +74,9 @@ struct DetectArgs {
   unsigned* counts;               // [frames] candidates found
   float* eta;                     // [frames] threshold from the median pre-pass
   int bands, band_rows;           // set by detect_bands()
+  // CFAR mode: guard and training half-widths and alpha(n) for n training cells (host-built table)
+  int cfar_guard = 0, cfar_train = 0;
+  const float* cfar_alpha = nullptr;
   // optional: the detection launch also zeroes map rows [z0, z0 + nz) of each frame
   float* zmap = nullptr;          // the map, or null (no zeroing)
   const long long* zmap_off = nullptr;  // per-frame float offset of the map, or null (f * zframe)
@@ -93,7 +101,8 @@ inline void detect_bands(int rows, int Mp, int* band_rows, int* bands) {
 // *tickets receives how far the launch advances a.work_ctr (symbols + warps
 // for the pipelined kernel, 0 otherwise); the caller adds it to work_base.
 struct FpsArgs {
-  int N, M, T, rows, CB, iterations, frames, K, max_recover;
+  int N, M, Q, T, rows, iterations, frames, K, max_recover;
+  int direct;                       // 1: samples are Y / X at the sampled cells (F is cell-local)
   float invN, invNM, NMoverQ;       // 1/N, 1/(N M), N M / Q
   float median_factor;             // bin threshold = median energy * (-ln pfa) / ln 2
   float dynamic_range, coherence_min;
@@ -118,8 +127,42 @@ cudaError_t launch_refine(const float2* strip, const float* logits, ofdm_target*
 cudaError_t cnn_forward(const float* th, int bf16, const float* x, int B, int H, int W, float* a1, float* a2,
                         float* z, cudaStream_t s);
 
-cudaError_t launch_fps(int Q, const float2* strip, const int32_t* slices, ofdm_target* out, int32_t* n_out,
-                       uint32_t* wstatus, const FpsArgs& a, cudaStream_t s, int* launches);
+// FPS-SFT: sampling (from the strip's taps, or from Y and X when a.direct),
+// slice DFTs into the workspace S (fps_workspace_elems float2), decoding.
+size_t fps_workspace_elems(int frames, int iterations, int T, int Q);
+cudaError_t launch_fps(int Q, const float2* strip, const float2* Y, const float2* X, const int32_t* slices,
+                       float2* S, ofdm_target* out, int32_t* n_out, uint32_t* wstatus, const FpsArgs& a,
+                       cudaStream_t s, int* launches);
+
+// Range transform on a zero-padded grid N' > N (range_pad.cu).
+struct PadArgs {
+  int M, L_cp, frames;
+  const float* wk;         // [N] window over k
+  const float2* twN;       // N-point pass twiddles for N / pad_threads(N') points per thread
+  const float2* twP;       // N'-point pass twiddles for N' / pad_threads(N') points per thread
+};
+int pad_threads(int NP);
+cudaError_t launch_range_pad(int N, int NP, const float2* taps, float2* strip, const PadArgs& a, cudaStream_t s,
+                             int* launches);
+
+// Transmit side (tx.cu): PAPR and amplifier out-of-band power per symbol.
+struct TxArgs {
+  int N, M, frames;
+  float sat_factor;        // 10^(q/10): amplifier saturation / mean modulus
+  const float2* tw;        // LN-point pass twiddles for tx_points_per_thread(LN) points per thread
+};
+int tx_points_per_thread(int LN);
+cudaError_t launch_tx(int LN, const float2* S, float* papr, float* aci, const TxArgs& a, cudaStream_t s,
+                      int* launches);
+
+// Tensor-core column kernel (N = 1024, M % 4 == 0, L_cp <= 256, 16-byte
+// aligned Y, X and frame offsets; the caller checks these).
+cudaError_t launch_column_tc(const float2* Y, const float2* X, float2* strip, uint32_t* wstatus, const ColumnArgs& a,
+                             cudaStream_t s, unsigned long long* tickets);
+// Host tables of the tensor-core form: `b` receives the hi and lo operand
+// images (2 * tc_table_bytes() bytes), `t12` the 1024 inter-stage twiddles.
+size_t tc_table_bytes();
+void build_tc_tables(unsigned char* b, float2* t12);
 
 cudaError_t launch_column(int N, const float2* Y, const float2* X, float2* strip, uint32_t* wstatus,
                           const ColumnArgs& a, cudaStream_t s, int* launches,
@@ -137,7 +180,7 @@ cudaError_t launch_detect(const float* pow, ofdm_target* out, int32_t* n_out, ui
 // any): the power strip is not written.  For M' >= 512 the fused kernel needs
 // too many registers per thread and the two kernels were measured faster.
 inline bool doppler_detect_fusable(const DetectArgs& a, int Mp) {
-  return a.mode == OFDM_DETECT_TOPK && Mp >= 64 && Mp <= 256 && a.compact;
+  return a.mode == OFDM_DETECT_TOPK && Mp >= 64 && Mp <= 256 && a.compact;   // (CFAR reads its own input rows)
 }
 cudaError_t launch_doppler_detect(int Mp, const float2* strip, float* map, ofdm_target* out, int32_t* n_out,
                                   uint32_t* status, uint32_t* wstatus, const DetectArgs& a, const DopplerArgs& d,

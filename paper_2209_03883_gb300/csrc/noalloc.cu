@@ -7,9 +7,12 @@
 // passes every input and output buffer.
 //
 // The array is shared by every call on a device and keeps the last call's
-// contents: the per-frame status words are cleared at the start of each
-// call, and the tables are regenerated (by a kernel on the caller's stream)
-// whenever the parameters differ from the previous call's on that device.
+// contents: the per-frame status words, the column kernel's ticket counter
+// and the detection's per-frame tickets and counts are cleared on the
+// caller's stream at the start of each call, so no call depends on what an
+// earlier one left behind, and the tables are regenerated (by a kernel on the
+// caller's stream) whenever the parameters differ from the previous call's on
+// that device.
 // Calls that overlap on the GPU -- on two streams, or from two host threads
 // -- race on the array.  The first call on a device looks up the array's
 // device address with cudaGetSymbolAddress; make that first call before any
@@ -138,6 +141,7 @@ int validate(const ofdm_radar_params& p) {
   if (p.L_cp < 1 || p.L_cp > N || p.n_cp < 0) return OFDM_ERR_INVALID_ARG;
   if (p.zc_root < 0 || (p.zc_root > 0 && (p.zc_root % 2) == 0)) return OFDM_ERR_INVALID_ARG;
   if (p.window < OFDM_WINDOW_RECT || p.window > OFDM_WINDOW_HAMMING) return OFDM_ERR_INVALID_ARG;
+  if (p.detect_mode == OFDM_DETECT_CFAR) return OFDM_ERR_UNSUPPORTED_SIZE;   // no alpha table in the array
   if (p.detect_mode != OFDM_DETECT_TOPK && p.detect_mode != OFDM_DETECT_THRESHOLD) return OFDM_ERR_INVALID_ARG;
   if (p.max_targets < 1 || p.max_targets > 32) return OFDM_ERR_INVALID_ARG;
   if (p.precision != OFDM_PREC_FP32) return OFDM_ERR_UNSUPPORTED_SIZE;
@@ -155,7 +159,6 @@ struct DeviceState {
   bool ready = false;
   unsigned char* base = nullptr;  // device address of g_noalloc_scratch
   bool have_tables = false;
-  unsigned long long ctr_base = 0;  // the counter starts at zero: the array is zero-initialised
   ofdm_radar_params tables_for;   // parameters the tables in the array were built for
 };
 constexpr int kMaxDevices = 64;
@@ -183,7 +186,8 @@ extern "C" int ofdm_radar_process_noalloc(const ofdm_radar_params* pin, const of
   const int full = (p.L_cp + spread >= N) ? 1 : 0;
   const int rows = full ? N : p.L_cp + spread;
   const int row0 = (full || !spread) ? 0 : N - 1;
-  if (frames < 1 || frames > kNoallocMaxFrames) return OFDM_ERR_INVALID_ARG;
+  if (frames < 1) return OFDM_ERR_INVALID_ARG;
+  if (frames > kNoallocMaxFrames) return OFDM_ERR_UNSUPPORTED_SIZE;  // beyond the fixed scratch array
   const long cells = (long)frames * rows * (Mp > M ? Mp : M);
   if (cells > kNoallocMaxCells) return OFDM_ERR_UNSUPPORTED_SIZE;  // beyond the fixed scratch array
 
@@ -218,7 +222,14 @@ extern "C" int ofdm_radar_process_noalloc(const ofdm_radar_params* pin, const of
   }
   unsigned char* b = st.base;
   uint32_t* wstatus = reinterpret_cast<uint32_t*>(b + kOffStatus);
-  e = cudaMemsetAsync(wstatus, 0, (size_t)frames * sizeof(uint32_t), s);  // status starts at zero
+  // Everything a kernel of this call counts or accumulates starts at zero:
+  // status words, the column kernel's symbol tickets, and the detection's
+  // per-frame tickets and candidate counts.
+  e = cudaMemsetAsync(wstatus, 0, (size_t)frames * sizeof(uint32_t), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b + kOffCtr, 0, sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b + kOffDetTick, 0, (size_t)frames * sizeof(unsigned), s);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(b + kOffDetTick + kNoallocMaxFrames * sizeof(unsigned), 0, (size_t)frames * sizeof(unsigned), s);
   if (e != cudaSuccess) return OFDM_ERR_CUDA;
   float2* strip = reinterpret_cast<float2*>(b + kOffStrip);
   float* pow = reinterpret_cast<float*>(b + kOffPow);
@@ -244,7 +255,7 @@ extern "C" int ofdm_radar_process_noalloc(const ofdm_radar_params* pin, const of
   ca.pre_df = reinterpret_cast<float4*>(b + kOffDf);
   ca.w_df = ca.pre_df + N;
   ca.work_ctr = reinterpret_cast<unsigned long long*>(b + kOffCtr);
-  ca.work_base = st.ctr_base;
+  ca.work_base = 0;                  // the counter was cleared above
   ca.frame_off = nullptr;
   ca.pipe_warps = 0;
 
@@ -263,8 +274,8 @@ extern "C" int ofdm_radar_process_noalloc(const ofdm_radar_params* pin, const of
   ta.out_idx = nullptr;
   ta.frame_mask = nullptr;
   ta.part_keys = reinterpret_cast<uint64_t*>(b + kOffDetKeys);
-  ta.tickets = reinterpret_cast<unsigned*>(b + kOffDetTick);   // zero-initialised with the array,
-  ta.counts = ta.tickets + kNoallocMaxFrames;                   // reset by every frame's last CTA
+  ta.tickets = reinterpret_cast<unsigned*>(b + kOffDetTick);   // cleared above for this call's frames
+  ta.counts = ta.tickets + kNoallocMaxFrames;
   ta.eta = reinterpret_cast<float*>(b + kOffEta);
   ta.frame_stride = (long)rows * Mp; ta.frames = frames; ta.mode = p.detect_mode; ta.K = p.max_targets;
   ta.use_fixed_eta = p.noise_var > 0.f ? 1 : 0;
@@ -278,7 +289,6 @@ extern "C" int ofdm_radar_process_noalloc(const ofdm_radar_params* pin, const of
   unsigned long long tk = 0;
   e = launch_column(N, reinterpret_cast<const float2*>(Y), reinterpret_cast<const float2*>(X), strip, wstatus, ca,
                     s, &launches, &tk);
-  st.ctr_base += tk;
   if (out_map && rows < N) {  // the detection launch zeroes the rows outside the support
     ta.zmap = out_map;
     ta.zframe = (long)N * Mp;

@@ -28,6 +28,17 @@ struct ofdm_radar_plan {
   float2 *pre, *post, *pre_conj, *post_conj, *twN, *twM;
   float2* twG = nullptr;       // N >= 1024: twiddles for 16 points per thread (groups of N / 16 threads)
   float4* d_df = nullptr;      // double-float pre-chirp [N] and roots of unity [N]
+  unsigned char* d_tc = nullptr;  // split-FP16 form: DFT-32 operand images (hi, lo) and inter-stage twiddles
+  float2* d_fps = nullptr;        // FPS-SFT slice workspace (allocated by the first ofdm_fps_sft call)
+  size_t fps_elems = 0;
+  float2* d_twL = nullptr;        // ofdm_tx_amplifier: L N-point pass twiddles (first call per L N)
+  int twL_n = 0;
+  // range zero padding N' > N: kept taps [max_frames][L_cp][M], window over k and the two transforms' twiddles
+  float2* d_taps = nullptr;
+  float2* d_padtab = nullptr;
+  float2 *twPN = nullptr, *twPP = nullptr;
+  float* d_wk = nullptr;
+  float* d_alpha = nullptr;       // CFAR: alpha(n) = n (P_fa^(-1/n) - 1), n = 0 .. 17^2
   float* d_wl = nullptr;
   float2* d_strip = nullptr;   // [max_frames][rows][M]
   float* d_pow = nullptr;      // [max_frames][rows][M']
@@ -76,7 +87,10 @@ namespace {
 // are recomputed in double-float (about 1e-4 of the cells for a ZC-precoded
 // QAM grid), which keeps the FP32 chain's error near FP32 rounding even when
 // the LS division meets a near-zero precoded cell.
-constexpr float kRefineTau = 1e-4f;
+#ifndef OFDM_REFINE_TAU
+#define OFDM_REFINE_TAU 1e-4f
+#endif
+constexpr float kRefineTau = OFDM_REFINE_TAU;
 constexpr int kMaxTimed = 4096;
 constexpr int kKinds = 8;  // column, zero_rows, doppler, detect, zct, coarse, cnn, refine
 enum { K_COLUMN = 0, K_ZERO = 1, K_DOPPLER = 2, K_DETECT = 3, K_ZCT = 4, K_COARSE = 5, K_CNN = 6, K_REFINE = 7 };
@@ -165,6 +179,8 @@ void ofdm_radar_default_params(ofdm_radar_params* p) {
   p->zc_root = 1;
   p->window = OFDM_WINDOW_HANN;
   p->detect_mode = OFDM_DETECT_TOPK;
+  p->cfar_guard = 1;
+  p->cfar_train = 4;
   p->max_targets = 8;
   p->max_frames = 1;
   p->precision = OFDM_PREC_FP32;
@@ -190,6 +206,13 @@ void ofdm_radar_plan_destroy(ofdm_radar_plan* plan) {
   if (!plan) return;
   cudaFree(plan->d_tables);
   cudaFree(plan->d_df);
+  cudaFree(plan->d_tc);
+  cudaFree(plan->d_fps);
+  cudaFree(plan->d_twL);
+  cudaFree(plan->d_taps);
+  cudaFree(plan->d_padtab);
+  cudaFree(plan->d_wk);
+  cudaFree(plan->d_alpha);
   cudaFree(plan->d_wl);
   cudaFree(plan->d_strip);
   cudaFree(plan->d_pow);
@@ -236,16 +259,30 @@ int ofdm_radar_plan_create(const ofdm_radar_params* pin, ofdm_radar_plan** out) 
   const int Np = p.N_pad ? p.N_pad : N, Mp = p.M_pad ? p.M_pad : M;
   if (!is_pow2(N) || N < 64 || N > 4096) return OFDM_ERR_UNSUPPORTED_SIZE;
   if (!is_pow2(M) || M < 16 || M > 1024) return OFDM_ERR_UNSUPPORTED_SIZE;
-  if (Np != N) return OFDM_ERR_UNSUPPORTED_SIZE;  // range zero-padding is not built
+  // range zero padding: N' = 2N, 4N or 8N, at most 4096
+  if (Np != N && (!is_pow2(Np) || Np < 2 * N || Np > 8 * N || Np > 4096)) return OFDM_ERR_UNSUPPORTED_SIZE;
   if (!is_pow2(Mp) || Mp < M || Mp > 1024) return OFDM_ERR_UNSUPPORTED_SIZE;
   if (p.L_cp < 1 || p.L_cp > N) return OFDM_ERR_INVALID_ARG;
   if (p.n_cp < 0) return OFDM_ERR_INVALID_ARG;
   if (p.zc_root < 0 || (p.zc_root > 0 && (p.zc_root % 2) == 0)) return OFDM_ERR_INVALID_ARG;
   if (p.window < OFDM_WINDOW_RECT || p.window > OFDM_WINDOW_HAMMING) return OFDM_ERR_INVALID_ARG;
-  if (p.detect_mode != OFDM_DETECT_TOPK && p.detect_mode != OFDM_DETECT_THRESHOLD) return OFDM_ERR_INVALID_ARG;
+  if (p.detect_mode != OFDM_DETECT_TOPK && p.detect_mode != OFDM_DETECT_THRESHOLD && p.detect_mode != OFDM_DETECT_CFAR)
+    return OFDM_ERR_INVALID_ARG;
+  if (p.detect_mode == OFDM_DETECT_CFAR &&
+      (p.cfar_guard < 0 || p.cfar_train < 1 || p.cfar_guard + p.cfar_train > 8))
+    return OFDM_ERR_INVALID_ARG;
   if (p.max_targets < 1 || p.max_targets > 32) return OFDM_ERR_INVALID_ARG;
   if (p.max_frames < 1) return OFDM_ERR_INVALID_ARG;
-  if (p.precision != OFDM_PREC_FP32) return OFDM_ERR_UNSUPPORTED_SIZE;
+  if (p.precision != OFDM_PREC_FP32 && p.precision != OFDM_PREC_SPLIT_BF16 && p.precision != OFDM_PREC_SPLIT_FP16)
+    return OFDM_ERR_INVALID_ARG;
+  if (p.precision == OFDM_PREC_SPLIT_BF16) return OFDM_ERR_UNSUPPORTED_SIZE;   // not built
+  if (p.precision == OFDM_PREC_SPLIT_FP16) {
+    // the tensor-core column kernel: 1024 = 32 x 32, tiles of 4 symbols,
+    // taps n < 256 from the last stage, and a support narrower than N
+    // (rows up to L_cp itself with a Hann / Hamming window: L_cp <= 255)
+    const int spread_tc = p.window == OFDM_WINDOW_RECT ? 0 : 1;
+    if (N != 1024 || Np != N || M % 4 || p.L_cp + spread_tc > 256) return OFDM_ERR_UNSUPPORTED_SIZE;
+  }
   if (!(p.pfa > 0.f && p.pfa < 1.f)) return OFDM_ERR_INVALID_ARG;
   if (!(p.fc_hz > 0.0 && p.df_hz > 0.0)) return OFDM_ERR_INVALID_ARG;
 
@@ -256,13 +293,15 @@ int ofdm_radar_plan_create(const ofdm_radar_params* pin, ofdm_radar_plan** out) 
   // Support rows: taps n < L_cp (Eq. (21)); a periodic Hann/Hamming window
   // over k spreads each tap to r - 1 and r + 1 (circular).
   const int spread = p.window == OFDM_WINDOW_RECT ? 0 : 2;
-  if (p.L_cp + spread >= N) {
+  if (Np > N) {   // on a padded grid every range row carries signal (range_pad.cu)
+    pl->rows = Np; pl->row0 = 0; pl->full = 1;
+  } else if (p.L_cp + spread >= N) {
     pl->rows = N; pl->row0 = 0; pl->full = 1;
   } else {
     pl->rows = p.L_cp + spread; pl->row0 = spread ? N - 1 : 0; pl->full = 0;
   }
-  pl->nz = N - pl->rows;
-  pl->z0 = (pl->row0 + pl->rows) % N;
+  pl->nz = Np - pl->rows;
+  pl->z0 = (pl->row0 + pl->rows) % Np;
   if (p.window == OFDM_WINDOW_HANN) { pl->c0 = 0.5f; pl->c1 = -0.25f; }
   else if (p.window == OFDM_WINDOW_HAMMING) { pl->c0 = 0.54f; pl->c1 = -0.23f; }
   else { pl->c0 = 1.f; pl->c1 = 0.f; }
@@ -317,6 +356,19 @@ int ofdm_radar_plan_create(const ofdm_radar_params* pin, ofdm_radar_plan** out) 
   } else {
     build_twiddles(twM, Mp, Mp / 32);
   }
+  std::vector<float2> twPN, twPP;
+  std::vector<float> wk;
+  if (Np > N) {
+    const int T = ofdm::pad_threads(Np);
+    build_twiddles(twPN, N, N / T);
+    build_twiddles(twPP, Np, Np / T);
+    wk.resize(N);
+    for (int k = 0; k < N; ++k) {
+      const double c = cos(2.0 * M_PI * k / N);
+      wk[k] = p.window == OFDM_WINDOW_HANN ? (float)(0.5 - 0.5 * c)
+            : p.window == OFDM_WINDOW_HAMMING ? (float)(0.54 - 0.46 * c) : 1.f;
+    }
+  }
   std::vector<float> wl(M);
   for (int l = 0; l < M; ++l) {
     const double c = cos(2.0 * M_PI * l / M);
@@ -339,6 +391,13 @@ int ofdm_radar_plan_create(const ofdm_radar_params* pin, ofdm_radar_plan** out) 
   if (e == cudaSuccess) e = dalloc(&pl->d_detkeys, (size_t)p.max_frames * pl->det_bands * 32);
   if (e == cudaSuccess) e = dalloc(&pl->d_dettick, 2 * (size_t)p.max_frames);
   if (e == cudaSuccess) e = dalloc(&pl->d_eta, (size_t)p.max_frames);
+  const size_t tc_bytes = 2 * ofdm::tc_table_bytes() + 1024 * sizeof(float2);
+  if (e == cudaSuccess && p.precision == OFDM_PREC_SPLIT_FP16) e = dalloc(&pl->d_tc, tc_bytes);
+  if (e == cudaSuccess && Np > N) e = dalloc(&pl->d_taps, (size_t)p.max_frames * p.L_cp * M);
+  if (e == cudaSuccess && Np > N) e = dalloc(&pl->d_padtab, twPN.size() + twPP.size());
+  if (e == cudaSuccess && Np > N) e = dalloc(&pl->d_wk, (size_t)N);
+  constexpr int kAlphaN = 17 * 17 + 1;
+  if (e == cudaSuccess && p.detect_mode == OFDM_DETECT_CFAR) e = dalloc(&pl->d_alpha, (size_t)kAlphaN);
   if (e != cudaSuccess) {
     ofdm_radar_plan_destroy(pl);
     cudaGetLastError();
@@ -366,6 +425,24 @@ int ofdm_radar_plan_create(const ofdm_radar_params* pin, ofdm_radar_plan** out) 
   if (e == cudaSuccess) e = cudaMemset(pl->d_wstatus, 0, (size_t)p.max_frames * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemset(pl->d_ctr, 0, 5 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(pl->d_dettick, 0, 2 * (size_t)p.max_frames * sizeof(unsigned));
+  if (e == cudaSuccess && pl->d_alpha) {
+    float alpha[kAlphaN];
+    alpha[0] = 0.f;
+    for (int n = 1; n < kAlphaN; ++n) alpha[n] = (float)(n * (pow((double)p.pfa, -1.0 / n) - 1.0));
+    e = cudaMemcpy(pl->d_alpha, alpha, sizeof(alpha), cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess && pl->d_padtab) {
+    pl->twPN = pl->d_padtab;
+    pl->twPP = pl->d_padtab + twPN.size();
+    e = cudaMemcpy(pl->twPN, twPN.data(), twPN.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(pl->twPP, twPP.data(), twPP.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(pl->d_wk, wk.data(), N * sizeof(float), cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess && pl->d_tc) {
+    std::vector<unsigned char> tc(tc_bytes);
+    ofdm::build_tc_tables(tc.data(), reinterpret_cast<float2*>(tc.data() + 2 * ofdm::tc_table_bytes()));
+    e = cudaMemcpy(pl->d_tc, tc.data(), tc_bytes, cudaMemcpyHostToDevice);
+  }
   if (e != cudaSuccess) {
     ofdm_radar_plan_destroy(pl);
     return cuda_fail(e);
@@ -377,7 +454,7 @@ int ofdm_radar_plan_create(const ofdm_radar_params* pin, ofdm_radar_plan** out) 
 int ofdm_radar_support_rows(const ofdm_radar_plan* plan, int32_t* rows) {
   if (!plan) return OFDM_ERR_INVALID_ARG;
   if (rows)
-    for (int i = 0; i < plan->rows; ++i) rows[i] = (plan->row0 + i) % plan->p.N;
+    for (int i = 0; i < plan->rows; ++i) rows[i] = (plan->row0 + i) % plan->Np;
   return plan->rows;
 }
 
@@ -450,7 +527,24 @@ ColumnArgs column_args(const ofdm_radar_plan* pl, int frames) {
   a.frame_off = nullptr;
   a.pipe_warps = pl->twG ? 2 : 0;   // N >= 1024: groups of N / 16 threads (measured faster), else the widest CTA
   a.tw_group = pl->twG;
+  if (pl->Np > pl->p.N) {   // the kept taps N h[n] (rect stencil) for the padded range transform
+    a.rows = pl->p.L_cp;
+    a.row0 = 0;
+    a.full = pl->p.L_cp >= pl->p.N ? 1 : 0;
+    a.c0 = 1.f;
+    a.c1 = 0.f;
+  }
+  if (pl->d_tc) {
+    a.tc_b = reinterpret_cast<const uint4*>(pl->d_tc);
+    a.tc_t12 = reinterpret_cast<const float2*>(pl->d_tc + 2 * ofdm::tc_table_bytes());
+  }
   return a;
+}
+
+// The split-FP16 column kernel moves Y and X rows with bulk copies, which
+// need 16-byte aligned addresses.
+bool tc_misaligned(const ofdm_radar_plan* pl, const void* Y, const void* X) {
+  return pl->d_tc && (((uintptr_t)Y | (uintptr_t)X) & 15u);
 }
 
 DopplerArgs doppler_args(const ofdm_radar_plan* pl, int frames) {
@@ -501,6 +595,9 @@ DetectArgs detect_args(const ofdm_radar_plan* pl, int frames, int compact) {
   const double Ts = (double)(p.N + ncp) / ((double)p.N * p.df_hz);
   a.dd = (float)(c / (2.0 * pl->Np * p.df_hz));
   a.dv = (float)(c / (2.0 * p.fc_hz * pl->Mp * Ts));
+  a.cfar_guard = p.cfar_guard;
+  a.cfar_train = p.cfar_train;
+  a.cfar_alpha = pl->d_alpha;
   return a;
 }
 
@@ -521,15 +618,33 @@ int finish(ofdm_radar_plan* pl, int launches, cudaError_t e) {
   return OFDM_OK;
 }
 
+// Steps a1-a5 into `strip` ([frames][rows][M]): the column kernel, followed
+// on a padded range grid by the full N'-row range transform of the kept taps.
+cudaError_t run_column(ofdm_radar_plan* pl, const float2* Y, const float2* X, int frames, float2* strip,
+                       cudaStream_t s, int* launches) {
+  unsigned long long tk = 0;
+  const bool padded = pl->Np > pl->p.N;
+  cudaError_t e = ofdm::launch_column(pl->p.N, Y, X, padded ? pl->d_taps : strip, pl->d_wstatus,
+                                      column_args(pl, frames), s, launches, &tk);
+  pl->ctr_base[pl->ctr_slot] += tk;
+  if (e != cudaSuccess || !padded) return e;
+  ofdm::PadArgs pa;
+  pa.M = pl->p.M;
+  pa.L_cp = pl->p.L_cp;
+  pa.frames = frames;
+  pa.wk = pl->d_wk;
+  pa.twN = pl->twPN;
+  pa.twP = pl->twPP;
+  return ofdm::launch_range_pad(pl->p.N, pl->Np, pl->d_taps, strip, pa, s, launches);
+}
+
 // The chain on device buffers; shared by the device and host entry points.
 cudaError_t run_chain(ofdm_radar_plan* pl, const float2* Y, const float2* X, int frames, float* map,
                       ofdm_target* tg, int32_t* nt, uint32_t* st, cudaStream_t s, int* launches) {
   cudaError_t e;
   {
     ScopedTimer tm(pl, s, K_COLUMN);
-    unsigned long long tk = 0;
-    e = ofdm::launch_column(pl->p.N, Y, X, pl->d_strip, pl->d_wstatus, column_args(pl, frames), s, launches, &tk);
-    pl->ctr_base[pl->ctr_slot] += tk;
+    e = run_column(pl, Y, X, frames, pl->d_strip, s, launches);
   }
   if (e != cudaSuccess) return e;
   DetectArgs ta = detect_args(pl, frames, 1);
@@ -555,7 +670,7 @@ extern "C" {
 int ofdm_radar_process(ofdm_radar_plan* pl, const ofdm_c32* Y, const ofdm_c32* X, int32_t frames,
                        float* out_map, ofdm_target* out_targets, int32_t* n_targets, uint32_t* status,
                        void* stream) {
-  if (!pl || !Y || !X || bad_frames(pl, frames)) return OFDM_ERR_INVALID_ARG;
+  if (!pl || !Y || !X || bad_frames(pl, frames) || tc_misaligned(pl, Y, X)) return OFDM_ERR_INVALID_ARG;
   int launches = 0;
   cudaError_t e = run_chain(pl, (const float2*)Y, (const float2*)X, frames, out_map, out_targets, n_targets,
                             status, (cudaStream_t)stream, &launches);
@@ -586,12 +701,12 @@ int ofdm_zc_precode(ofdm_radar_plan* pl, const ofdm_c32* in, ofdm_c32* out, int3
 
 int ofdm_radar_range_profile(ofdm_radar_plan* pl, const ofdm_c32* Y, const ofdm_c32* X, int32_t frames,
                              ofdm_c32* strip, void* stream) {
-  if (!pl || !Y || !X || !strip || bad_frames(pl, frames)) return OFDM_ERR_INVALID_ARG;
+  if (!pl || !Y || !X || !strip || bad_frames(pl, frames) || tc_misaligned(pl, Y, X) ||
+      tc_misaligned(pl, strip, strip))
+    return OFDM_ERR_INVALID_ARG;
   int launches = 0;
-  unsigned long long tk = 0;
-  cudaError_t e = ofdm::launch_column(pl->p.N, (const float2*)Y, (const float2*)X, (float2*)strip,
-                                      pl->d_wstatus, column_args(pl, frames), (cudaStream_t)stream, &launches, &tk);
-  pl->ctr_base[pl->ctr_slot] += tk;
+  cudaError_t e = run_column(pl, (const float2*)Y, (const float2*)X, frames, (float2*)strip, (cudaStream_t)stream,
+                             &launches);
   // the status words of this call are not reported; clear them
   if (e == cudaSuccess)
     e = cudaMemsetAsync(pl->d_wstatus, 0, (size_t)frames * sizeof(uint32_t), (cudaStream_t)stream);
@@ -710,34 +825,56 @@ void ofdm_fps_default_params(ofdm_fps_params* fp) {
 int ofdm_fps_sft(ofdm_radar_plan* pl, const ofdm_c32* Y, const ofdm_c32* X, int32_t frames,
                  const ofdm_fps_params* fp, const int32_t* slices, ofdm_target* out_targets,
                  int32_t* n_targets, void* stream) {
-  if (!pl || !Y || !X || !fp || !slices || bad_frames(pl, frames)) return OFDM_ERR_INVALID_ARG;
+  if (!pl || !Y || !X || !fp || !slices || bad_frames(pl, frames) || tc_misaligned(pl, Y, X))
+    return OFDM_ERR_INVALID_ARG;
   const ofdm_radar_params& p = pl->p;
   const int N = p.N, M = p.M, Q = N > M ? N : M;
-  if (Q > 1024 || pl->Mp != M) return OFDM_ERR_UNSUPPORTED_SIZE;
+  if (Q > 1024 || pl->Mp != M || pl->Np != N) return OFDM_ERR_UNSUPPORTED_SIZE;
   if (fp->iterations < 1 || fp->iterations > 16 || fp->offsets < 3 || fp->offsets > 8 ||
       fp->max_recover < 1 || fp->max_recover > 64 || !(fp->bin_pfa > 0.f && fp->bin_pfa < 1.f) ||
       !(fp->coherence_min >= 0.f && fp->coherence_min <= 1.f) || !(fp->dynamic_range >= 0.f))
     return OFDM_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  // Column pass with a rect stencil: the strip then holds the kept taps N h[n].
-  ColumnArgs ca = column_args(pl, frames);
-  ca.rows = p.L_cp;
-  ca.row0 = 0;
-  ca.full = p.L_cp >= N ? 1 : 0;
-  ca.c0 = 1.f;
-  ca.c1 = 0.f;
+  // Slice workspace for max_frames frames of this (iterations, offsets).
+  const size_t need = ofdm::fps_workspace_elems(p.max_frames, fp->iterations, fp->offsets, Q);
+  if (need > pl->fps_elems) {
+    cudaError_t ea = cudaStreamSynchronize(s);   // the old workspace may still be in use
+    if (ea != cudaSuccess) return cuda_fail(ea);
+    cudaFree(pl->d_fps);
+    pl->d_fps = nullptr;
+    pl->fps_elems = 0;
+    ea = dalloc(&pl->d_fps, need);
+    if (ea != cudaSuccess) {
+      cudaGetLastError();
+      return ea == cudaErrorMemoryAllocation ? OFDM_ERR_NO_MEMORY : cuda_fail(ea);
+    }
+    pl->fps_elems = need;
+  }
+  // F is cell-local when there is no precoding to undo and DFT-CE keeps every
+  // tap (plain LS estimation): the samples then read only the sampled cells.
+  const bool direct = (p.zc_root == 0 || p.x_is_precoded) && p.L_cp >= N;
   int launches = 0;
-  unsigned long long tk = 0;
-  cudaError_t e = ofdm::launch_column(N, (const float2*)Y, (const float2*)X, pl->d_strip, pl->d_wstatus, ca, s,
-                                      &launches, &tk);
-  pl->ctr_base[pl->ctr_slot] += tk;
+  cudaError_t e = cudaSuccess;
+  if (direct) {
+    e = cudaMemsetAsync(pl->d_wstatus, 0, (size_t)frames * sizeof(uint32_t), s);
+  } else {
+    // Column pass with a rect stencil: the strip then holds the kept taps N h[n].
+    ColumnArgs ca = column_args(pl, frames);
+    ca.rows = p.L_cp;
+    ca.row0 = 0;
+    ca.full = p.L_cp >= N ? 1 : 0;
+    ca.c0 = 1.f;
+    ca.c1 = 0.f;
+    unsigned long long tk = 0;
+    e = ofdm::launch_column(N, (const float2*)Y, (const float2*)X, pl->d_strip, pl->d_wstatus, ca, s, &launches,
+                            &tk);
+    pl->ctr_base[pl->ctr_slot] += tk;
+  }
   if (e != cudaSuccess) return finish(pl, launches, e);
   ofdm::FpsArgs a;
-  a.N = N; a.M = M; a.T = fp->offsets; a.rows = p.L_cp; a.iterations = fp->iterations; a.frames = frames;
+  a.N = N; a.M = M; a.Q = Q; a.T = fp->offsets; a.rows = p.L_cp; a.iterations = fp->iterations; a.frames = frames;
   a.K = p.max_targets; a.max_recover = fp->max_recover;
-  a.CB = 4096 / p.L_cp;
-  if (a.CB < 1) a.CB = 1;
-  if (a.CB > 32) a.CB = 32;
+  a.direct = direct ? 1 : 0;
   a.invN = (float)(1.0 / N);
   a.invNM = (float)(1.0 / ((double)N * M));
   a.NMoverQ = (float)((double)N * M / Q);
@@ -749,7 +886,43 @@ int ofdm_fps_sft(ofdm_radar_plan* pl, const ofdm_c32* Y, const ofdm_c32* X, int3
   a.dv = d.dv;
   a.w_df = pl->d_df + N;
   a.twQ = (Q == N) ? pl->twN : pl->twM;
-  e = ofdm::launch_fps(Q, pl->d_strip, slices, out_targets, n_targets, pl->d_wstatus, a, s, &launches);
+  e = ofdm::launch_fps(Q, pl->d_strip, (const float2*)Y, (const float2*)X, slices, pl->d_fps, out_targets, n_targets,
+                       pl->d_wstatus, a, s, &launches);
+  return finish(pl, launches, e);
+}
+
+int ofdm_tx_amplifier(ofdm_radar_plan* pl, const ofdm_c32* S, int32_t frames, int32_t oversample, float q,
+                      float* papr, float* aci, void* stream) {
+  if (!pl || !S || bad_frames(pl, frames) || !(q > -100.f && q < 100.f)) return OFDM_ERR_INVALID_ARG;
+  const int N = pl->p.N, LN = N * oversample;
+  if (oversample < 1 || oversample > 8 || (oversample & (oversample - 1)) || LN > 4096)
+    return OFDM_ERR_UNSUPPORTED_SIZE;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (pl->twL_n != LN) {   // twiddles of the L N-point transforms, built once per size
+    std::vector<float2> tw;
+    build_twiddles(tw, LN, ofdm::tx_points_per_thread(LN));
+    cudaError_t e = cudaStreamSynchronize(s);   // the previous table may still be in use
+    if (e == cudaSuccess) {
+      cudaFree(pl->d_twL);
+      pl->d_twL = nullptr;
+      pl->twL_n = 0;
+      e = dalloc(&pl->d_twL, tw.size());
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(pl->d_twL, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return e == cudaErrorMemoryAllocation ? OFDM_ERR_NO_MEMORY : cuda_fail(e);
+    }
+    pl->twL_n = LN;
+  }
+  ofdm::TxArgs a;
+  a.N = N;
+  a.M = pl->p.M;
+  a.frames = frames;
+  a.sat_factor = (float)pow(10.0, (double)q / 10.0);
+  a.tw = pl->d_twL;
+  int launches = 0;
+  cudaError_t e = ofdm::launch_tx(LN, (const float2*)S, papr, aci, a, s, &launches);
   return finish(pl, launches, e);
 }
 
@@ -1086,7 +1259,7 @@ int ofdm_radar_coarse_shape(const ofdm_radar_plan* pl, int32_t* h, int32_t* w) {
 
 int ofdm_radar_coarse_map(ofdm_radar_plan* pl, const ofdm_c32* Y, const ofdm_c32* X, int32_t frames, float* x_out,
                           void* stream) {
-  if (!pl || !Y || !X || !pl->d_cpow || bad_frames(pl, frames)) return OFDM_ERR_INVALID_ARG;
+  if (!pl || !Y || !X || !pl->d_cpow || bad_frames(pl, frames) || tc_misaligned(pl, Y, X)) return OFDM_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   int launches = 0;
   unsigned long long tk = 0;
@@ -1104,7 +1277,8 @@ int ofdm_radar_coarse_map(ofdm_radar_plan* pl, const ofdm_c32* Y, const ofdm_c32
 int ofdm_radar_process_learned(ofdm_radar_plan* pl, const float* theta, const ofdm_c32* Y, const ofdm_c32* X,
                                int32_t frames, float zthr, int32_t cap, ofdm_target* out, int32_t* nt,
                                uint32_t* st, void* stream) {
-  if (!pl || !theta || !Y || !X || !pl->d_cpow || bad_frames(pl, frames) || cap < 1 || cap > 256)
+  if (!pl || !theta || !Y || !X || !pl->d_cpow || bad_frames(pl, frames) || cap < 1 || cap > 256 ||
+      tc_misaligned(pl, Y, X))
     return OFDM_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   int launches = 0;

@@ -13,15 +13,17 @@ import os
 import re
 
 PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(PKG, "libofdm_radar.so")
+# OFDM_RADAR_LIB may name another build of the same library (same ABI).
+LIB_PATH = os.environ.get("OFDM_RADAR_LIB") or os.path.join(PKG, "libofdm_radar.so")
 HEADER = os.path.join(os.path.dirname(PKG), "include", "ofdm_radar.h")
 
 OFDM_OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "UNSUPPORTED_SIZE", -3: "CUDA", -4: "TIMEOUT", -5: "NO_MEMORY"}
 WINDOW_RECT, WINDOW_HANN, WINDOW_HAMMING = 0, 1, 2
-DETECT_TOPK, DETECT_THRESHOLD = 0, 1
-PREC_FP32, PREC_SPLIT_BF16 = 0, 1
+DETECT_TOPK, DETECT_THRESHOLD, DETECT_CFAR = 0, 1, 2
+PREC_FP32, PREC_SPLIT_BF16, PREC_SPLIT_FP16 = 0, 1, 2
 STATUS_ZERO_X, STATUS_NONFINITE, STATUS_OVERFLOW, STATUS_FEW_PEAKS = 1, 2, 4, 8
+STATUS_UNREFINED, STATUS_TIMEOUT = 32, 64
 
 
 class Params(ctypes.Structure):
@@ -33,7 +35,8 @@ class Params(ctypes.Structure):
                 ("detect_mode", ctypes.c_int32), ("max_targets", ctypes.c_int32),
                 ("max_frames", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("pfa", ctypes.c_float), ("noise_var", ctypes.c_float),
-                ("fc_hz", ctypes.c_double), ("df_hz", ctypes.c_double)]
+                ("fc_hz", ctypes.c_double), ("df_hz", ctypes.c_double),
+                ("cfar_guard", ctypes.c_int32), ("cfar_train", ctypes.c_int32)]
 
 
 class Target(ctypes.Structure):
@@ -92,6 +95,8 @@ def _load():
     lib.ofdm_fps_default_params.restype = None
     lib.ofdm_fps_sft.argtypes = [vp, vp, vp, i32, P(FpsParams), vp, vp, vp, vp]
     lib.ofdm_fps_sft.restype = ctypes.c_int
+    lib.ofdm_tx_amplifier.argtypes = [vp, vp, i32, i32, ctypes.c_float, vp, vp, vp]
+    lib.ofdm_tx_amplifier.restype = ctypes.c_int
     lib.ofdm_radar_batch_create.argtypes = [P(Params), vp, i32, ctypes.c_uint32, P(vp)]
     lib.ofdm_radar_batch_create.restype = ctypes.c_int
     lib.ofdm_radar_batch_process.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
@@ -182,9 +187,11 @@ def _buf(t, kind, need, where, name, host=False):
 
 
 def _frames(frames, where, cap=None):
+    """The frame count, rejected (as the library does, INVALID_ARG) outside
+    [1, cap] before any buffer is looked at."""
     frames = int(frames)
     if frames < 1 or (cap is not None and frames > cap):
-        raise ValueError(f"{where}: frames = {frames} outside [1, {cap}]")
+        raise OfdmError(-1, f"{where}: frames = {frames} outside [1, {cap}]")
     return frames
 
 
@@ -283,10 +290,14 @@ def ofdm_radar_process_noalloc(params: Params, Y, X, frames, out_map=None, out_t
     """The chain without any device allocation (no plan; fixed in-library scratch)."""
     w = "ofdm_radar_process_noalloc"
     frames = _frames(frames, w)
-    ptrs = _chain_ptrs(w, frames, params.N, params.M, params.N_pad or params.N, params.M_pad or params.M,
-                       params.max_targets, Y, X, out_map, out_targets, n_targets, status)
-    # Y and X are checked for one frame: the library rejects frame counts
-    # beyond its fixed array before it reads them.
+    # Requests beyond the library's fixed array are rejected by the library
+    # before it reads anything; the buffers are checked for what it accepts.
+    N, M, Mp = params.N, params.M, params.M_pad or params.M
+    spread = 0 if params.window == WINDOW_RECT else 2
+    rows = N if params.L_cp + spread >= N else params.L_cp + spread
+    checked = frames if frames <= 4096 and frames * rows * max(M, Mp) <= (1 << 20) else 1
+    ptrs = _chain_ptrs(w, checked, N, M, params.N_pad or N, Mp, params.max_targets, Y, X, out_map, out_targets,
+                       n_targets, status)
     return _check(_lib.ofdm_radar_process_noalloc(ctypes.byref(params), ptrs[0], ptrs[1], frames, *ptrs[2:],
                                                   _stream(stream)), w)
 
@@ -499,3 +510,15 @@ def ofdm_cnn_adam(theta, grad, m, v, n, step, lr, beta1=0.9, beta2=0.999, eps=1e
     return _check(_lib.ofdm_cnn_adam(_buf(theta, "f32", n, w, "theta"), _buf(grad, "f32", n, w, "grad"),
                                      _buf(m, "f32", n, w, "m"), _buf(v, "f32", n, w, "v"), n, step, float(lr),
                                      float(beta1), float(beta2), float(eps), _stream(stream)), w)
+
+
+# ------------------------------------------------------------- transmit side
+def ofdm_tx_amplifier(plan: Plan, S, frames, oversample=4, q=2.0, papr=None, aci=None, stream=None):
+    """PAPR and amplifier out-of-band power of each OFDM symbol of the
+    transmitted grid S ([frames][M][N] complex64): papr, aci [frames][M] float32."""
+    w = "ofdm_tx_amplifier"
+    frames = _frames(frames, w, plan.max_frames)
+    n = frames * plan.M
+    return _check(_lib.ofdm_tx_amplifier(plan.handle, _buf(S, "c64", n * plan.N, w, "S"), frames, int(oversample),
+                                         float(q), _buf(papr, "f32", n, w, "papr"), _buf(aci, "f32", n, w, "aci"),
+                                         _stream(stream)), w)

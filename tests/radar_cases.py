@@ -31,7 +31,7 @@ def plan_kwargs(p: o.Params, frames: int) -> dict:
                 zc_root=p.zc_root, zc_q=p.zc_q, x_is_precoded=int(p.x_is_precoded),
                 window=p.window, detect_mode=p.detect_mode, max_targets=p.max_targets,
                 max_frames=frames, pfa=p.pfa, noise_var=p.noise_var, fc_hz=p.fc_hz,
-                df_hz=p.df_hz)
+                df_hz=p.df_hz, cfar_guard=p.cfar_guard, cfar_train=p.cfar_train)
 
 
 def make_frames(ci: int, frames: int, cfg: syn.FrameConfig | None = None, **draw_kw):
@@ -49,17 +49,18 @@ def stack_lk(arrs):
     return np.stack([syn.to_lk(a) for a in arrs])
 
 
-def check_detections_vs_fp64(gpu_rs, gpu_pw, det: o.Detection, P: np.ndarray):
+def check_detections_vs_fp64(gpu_rs, gpu_pw, det: o.Detection, P: np.ndarray, near_tie: float = NEAR_TIE,
+                             peak_tol: float = PEAK_TOL, map_tol: float = MAP_TOL):
     """Exact bin agreement with the FP64 oracle up to near-ties.
 
     gpu_rs: the GPU's (r, s) bins in its reported order; gpu_pw: their powers;
     det: the oracle's detections on the FP64 map P ([r, c], c = s + M'/2).
     The GPU must report as many targets as the oracle.  Where its i-th bin
     differs from the oracle's, that bin must itself be a peak of the FP64 map
-    (no neighbour above it by more than NEAR_TIE) whose FP64 power lies
-    within NEAR_TIE of the oracle's i-th power: two candidates that FP32
+    (no neighbour above it by more than near_tie) whose FP64 power lies
+    within near_tie of the oracle's i-th power: two candidates that FP32
     cannot order.  Every reported power must match the FP64 power of its bin
-    to PEAK_TOL (relative, plus MAP_TOL of the strongest peak).  Returns the
+    to peak_tol (relative, plus map_tol of the strongest peak).  Returns the
     number of swapped positions."""
     want = list(zip(det.r.tolist(), det.s.tolist()))
     got = [(int(r), int(s)) for r, s in gpu_rs]
@@ -73,12 +74,12 @@ def check_detections_vs_fp64(gpu_rs, gpu_pw, det: o.Detection, P: np.ndarray):
         pg = float(P[r, c])
         if g != w:
             ref = float(det.power[i])
-            assert abs(pg - ref) <= NEAR_TIE * ref, \
+            assert abs(pg - ref) <= near_tie * ref, \
                 f"detection {i}: got {g} (P {pg:.6e}), oracle {w} (P {ref:.6e}): not a near-tie"
             nb = max(float(P[(r + dr) % R, (c + dc) % C]) for dr in (-1, 0, 1) for dc in (-1, 0, 1)
                      if (dr, dc) != (0, 0))
-            assert nb <= pg * (1 + NEAR_TIE), f"detection {i}: got {g}, not a peak of the FP64 map"
+            assert nb <= pg * (1 + near_tie), f"detection {i}: got {g}, not a peak of the FP64 map"
             amb += 1
-        assert abs(float(gpu_pw[i]) - pg) <= PEAK_TOL * pg + MAP_TOL * top, \
+        assert abs(float(gpu_pw[i]) - pg) <= peak_tol * pg + map_tol * top, \
             f"detection {i} at {g}: power {float(gpu_pw[i]):.6e}, FP64 {pg:.6e}"
     return amb

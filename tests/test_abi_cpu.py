@@ -24,7 +24,7 @@ def test_exports_every_declared_function(radar):
 
 
 def test_struct_layouts(radar):
-    assert ctypes.sizeof(radar.Params) == 16 * 4 + 2 * 8
+    assert ctypes.sizeof(radar.Params) == 16 * 4 + 2 * 8 + 2 * 4
     assert ctypes.sizeof(radar.Target) == 20
 
 
@@ -46,7 +46,9 @@ BAD = [
     (dict(N=1024, M=256, L_cp=128, max_targets=33), -1),
     (dict(N=1024, M=256, L_cp=128, max_frames=0), -1),
     (dict(N=1024, M=256, L_cp=128, pfa=0.0), -1),
-    (dict(N=1024, M=256, L_cp=128, N_pad=2048), -2),  # range padding not built
+    (dict(N=1024, M=256, L_cp=128, N_pad=3072), -2),  # range padding: a power of two
+    (dict(N=1024, M=256, L_cp=128, N_pad=8192), -2),  # range padding: N' <= 4096
+    (dict(N=256, M=64, L_cp=32, N_pad=4096), -2),     # range padding: at most 8 N
     (dict(N=1024, M=256, L_cp=128, M_pad=200), -2),
 ]
 
@@ -100,5 +102,22 @@ def test_binding_checks_buffers_before_calling_the_library(radar):
     with pytest.raises(ValueError, match="CUDA tensor"):
         radar._chain_ptrs("f", 1, 64, 16, 64, 16, 2, good, good, None, None, None, None)
     assert radar._buf(good, "c64", 1024, "f", "Y", host=True).value == good.data_ptr()
-    with pytest.raises(ValueError, match="frames"):
+    with pytest.raises(radar.OfdmError) as ei:
         radar._frames(0, "f")
+    assert ei.value.code == -1
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(N=2048, M=256, L_cp=128, precision=2), -2),   # split FP16: N = 1024 only
+    (dict(N=1024, M=256, L_cp=256, precision=2), -2),   # Hann: rows up to L_cp need L_cp <= 255
+    (dict(N=1024, M=256, L_cp=300, window=0, precision=2), -2),
+    (dict(N=1024, M=256, L_cp=128, precision=1), -2),   # split BF16: not built
+    (dict(N=1024, M=256, L_cp=128, precision=7), -1),
+    (dict(N=1024, M=256, L_cp=128, detect_mode=2, cfar_guard=4, cfar_train=5), -1),   # guard + train <= 8
+    (dict(N=1024, M=256, L_cp=128, detect_mode=2, cfar_train=0), -1),
+    (dict(N=1024, M=256, L_cp=128, detect_mode=3), -1),
+])
+def test_precision_limits(radar, kw, code):
+    with pytest.raises(radar.OfdmError) as ei:
+        radar.Plan(**kw)
+    assert ei.value.code == code

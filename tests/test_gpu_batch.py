@@ -4,7 +4,7 @@ import pytest
 
 import ofdm_synth as syn
 from oracle import ofdm_oracle as o
-from radar_cases import MAP_TOL, rel_l2
+from radar_cases import MAP_TOL, check_detections_vs_fp64, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -74,12 +74,15 @@ def test_batch_matches_oracle_and_graph_replays(env):
     groups = b.groups()
     assert sum(g[3] for g in groups) == 24 and len(groups) > 1
     assert all(g[4] in (0, 4) for g in groups if g[0] <= 1024)
-    for f in (0, 5, 11, 23):
+    for f in range(24):   # every frame of the batch
         N, M, L, d, Y = frames[f]
         p = o.Params(N=N, M=M, L_cp=L, zc_root=1, window=1, max_targets=16)
         ref = o.process(Y, d.A, p)
         got = mp[descs[f][4]:descs[f][4] + N * M].reshape(N, M)
-        assert rel_l2(got, ref["P"]) < MAP_TOL
+        assert rel_l2(got, ref["P"]) < MAP_TOL, f"frame {f}"
+        n = int(nt[f])
+        check_detections_vs_fp64([(int(t["r"]), int(t["s"])) for t in tv[f][:n]], tv[f]["power"][:n],
+                                 ref["det"], ref["P"])
         det32 = o.detect(got, o.DETECT_TOPK, 16)
         n = int(nt[f])
         assert [(int(t["r"]), int(t["s"])) for t in tv[f][:n]] == list(zip(det32.r.tolist(), det32.s.tolist()))

@@ -102,6 +102,36 @@ def test_fps_rejects_bad_params(env):
     p = o.Params(N=64, M=16, L_cp=16)
     plan = radar.Plan(**plan_kwargs(p, 1))
     Y = torch.zeros((1, 16, 64), dtype=torch.complex64, device=dev)
-    sl = torch.zeros((1, 4, 18), dtype=torch.int32, device=dev)
+    sl = torch.zeros((1, 4, 20), dtype=torch.int32, device=dev)   # room for 9 offsets: the library rejects them
     with pytest.raises(radar.OfdmError):
         radar.ofdm_fps_sft(plan, Y, Y, 1, radar.fps_default_params(offsets=9), sl)
+
+
+def test_fps_ls_estimation_reads_sampled_cells(env):
+    """Plain LS estimation without precoding (zc_root = 0, L_cp = N): F = Y / X
+    is cell-local, so the slices come straight from the sampled cells of Y and
+    X (no column pass).  1024 x 1024, K = 8 on-grid, 5 dB: the GPU recovers
+    exactly what the oracle's FPS-SFT recovers on F, and that equals the
+    periodogram's top 8."""
+    radar, torch, dev = env
+    N = M = 1024
+    cfg = syn.FrameConfig(N=N, M=M, L_cp=N, qam=16, zc_root=0, n_targets=8, on_grid=True, amp_db=(0.0, 0.0),
+                          snr_db=(5.0, 5.0), window=0, detect_k=8)
+    frames = 2
+    frs = [syn.draw_frame(cfg, 3500 + f) for f in range(frames)]
+    Ys = [syn.received(d, d.A) for d in frs]
+    p = o.Params(N=N, M=M, L_cp=N, zc_root=0, window=0, max_targets=8)
+    T, I = 8, 4
+    slices = draw_slices(37, frames, I, T, N, M)
+    fp = radar.fps_default_params(iterations=I, offsets=T)
+    tv, nt = run_fps(env, p, Ys, [d.A for d in frs], slices, fp)
+    ofp = o.FpsParams(iterations=I, offsets=T)
+    for i, d in enumerate(frs):
+        F, _ = o.ls_divide(Ys[i], d.A)
+        want = o.fps_targets(o.fps_sft(F, as_oracle_slices(slices[i], T), ofp), N, M, 8)
+        n = int(nt[i])
+        got = [(int(t["r"]), int(t["s"])) for t in tv[i][:n]]
+        assert got == [(r, s) for _, _, r, s in want]
+        assert np.allclose(tv[i]["power"][:n], [w[0] for w in want], rtol=1e-3)
+        ref = o.process(Ys[i], d.A, p)
+        assert sorted(got) == sorted(zip(ref["det"].r.tolist(), ref["det"].s.tolist()))

@@ -71,7 +71,7 @@ def oracle_strip(p, Y, A):
 def test_zc_precode_forward_inverse(env, N, M, r, q):
     radar, torch, dev = env
     rng = np.random.default_rng(N + r)
-    A = syn.qam_symbols(rng, (N, M), 16)
+    A = syn.as_complex64_values(syn.qam_symbols(rng, (N, M), 16))
     p = o.Params(N=N, M=M, L_cp=N // 8, zc_root=r, zc_q=q)
     plan = radar.Plan(**plan_kwargs(p, 1))
     Ad = to_dev(torch, dev, syn.to_lk(A)[None])
@@ -121,16 +121,15 @@ def test_chain_matches_oracle(env, ci, frames):
         assert int(res["status"][i]) == det32.status
 
 
-def test_chain_full_batch_sampled(env):
-    """The benchmark's launch: 64 frames of 1024 x 256 in one call; frames
-    0, 31 and 63 are checked in full against the oracle."""
+def test_chain_full_batch_every_frame(env):
+    """The benchmark's launch: 64 frames of 1024 x 256 in one call, every
+    frame checked in full against the oracle (map and detections)."""
     cfg, fr = make_frames(2, 64)
     p = oracle_params(cfg)
     res = run_chain(env, p, [f[2] for f in fr], [f[0].A for f in fr])
-    for i in (0, 31, 63):
-        frm, Xp, Y = fr[i]
+    for i, (frm, Xp, Y) in enumerate(fr):
         ref = o.process(Y, frm.A, p)
-        assert rel_l2(res["map"][i], ref["P"]) < MAP_TOL
+        assert rel_l2(res["map"][i], ref["P"]) < MAP_TOL, f"frame {i}"
         n = int(res["n"][i])
         rs = [(int(t["r"]), int(t["s"])) for t in res["tg"][i][:n]]
         check_detections_vs_fp64(rs, res["tg"][i]["power"][:n], ref["det"], ref["P"])
@@ -142,6 +141,21 @@ def test_chain_full_batch_sampled(env):
         for rho, nu in zip(frm.rho, frm.nu):
             hits += any(abs(r - rho) <= 1.0 and abs(((s - nu) + 128) % 256 - 128) <= 1.0 for r, s in got)
     assert hits >= 0.8 * 5 * 64
+
+
+@pytest.mark.slow
+def test_largest_workload_full_frame(env):
+    """One whole 4096 x 1024 frame (L_cp = 512, 32 off-grid targets) through
+    the chain: map and detections against the oracle."""
+    cfg, fr = make_frames(5, 1)
+    p = oracle_params(cfg)
+    frm, Xp, Y = fr[0]
+    res = run_chain(env, p, [Y], [frm.A])
+    ref = o.process(Y, frm.A, p)
+    assert rel_l2(res["map"][0], ref["P"]) < MAP_TOL
+    n = int(res["n"][0])
+    rs = [(int(t["r"]), int(t["s"])) for t in res["tg"][0][:n]]
+    check_detections_vs_fp64(rs, res["tg"][0]["power"][:n], ref["det"], ref["P"])
 
 
 def test_largest_workload_sampled(env):
@@ -257,7 +271,7 @@ def test_zero_and_nonfinite_cells_flagged(env):
 def test_noiseless_point_target_lands_on_its_bin(env):
     N, M = 1024, 256
     rng = np.random.default_rng(11)
-    A = syn.qam_symbols(rng, (N, M), 16)
+    A = syn.as_complex64_values(syn.qam_symbols(rng, (N, M), 16))
     Xp = o.zc_precode(A, 1)
     H = syn.channel([37.0], [-21.0], [1.0], N, M)
     p = o.Params(N=N, M=M, L_cp=128, window=o.WINDOW_HANN, max_targets=1)
@@ -365,3 +379,89 @@ def test_detection_statistics_against_truth(env):
     assert hits >= 0.85 * n_true
     assert np.sqrt(np.mean(np.square(errs_d))) < 0.45 * dd
     assert np.sqrt(np.mean(np.square(errs_v))) < 0.45 * dv
+
+
+# ------------------------------------------------------------------ range zero padding N' > N (Eq. (17))
+PAD_CASES = [
+    ("64_to_128_rect", dict(N=64, M=16, L_cp=8, N_pad=128, window=o.WINDOW_RECT)),
+    ("128_to_512_hann", dict(N=128, M=32, L_cp=16, N_pad=512, window=o.WINDOW_HANN)),
+    ("256_to_512_hamming_doppler_pad", dict(N=256, M=64, L_cp=32, N_pad=512, M_pad=128, window=o.WINDOW_HAMMING)),
+    ("1024_to_2048_hann", dict(N=1024, M=64, L_cp=128, N_pad=2048, window=o.WINDOW_HANN)),
+    ("512_to_4096_hann", dict(N=512, M=16, L_cp=64, N_pad=4096, window=o.WINDOW_HANN)),
+]
+
+
+@pytest.mark.parametrize("name,kw", PAD_CASES, ids=[c[0] for c in PAD_CASES])
+def test_range_zero_padding(env, name, kw):
+    """A padded range grid interpolates between bins, so every one of the N'
+    rows carries signal: the strip (all N' rows), the map and the detections
+    against the oracle's Eq. (17) with N' > N."""
+    radar, torch, dev = env
+    base = syn.FrameConfig(N=kw["N"], M=kw["M"], L_cp=kw["L_cp"], qam=16, zc_root=1, n_targets=3, on_grid=False,
+                           amp_db=(-6.0, 0.0), snr_db=(0.0, 0.0), window=kw["window"], detect_k=4)
+    fr = []
+    for f in range(2):
+        d = syn.draw_frame(base, 8100 + f)
+        Xp = o.zc_precode(d.A, 1)
+        fr.append((d, Xp, syn.received(d, Xp)))
+    p = o.Params(N=kw["N"], M=kw["M"], L_cp=kw["L_cp"], zc_root=1, window=kw["window"], max_targets=4,
+                 N_pad=kw["N_pad"], M_pad=kw.get("M_pad", 0))
+    rows, strip = gpu_strip(env, p, [f[2] for f in fr], [f[0].A for f in fr])
+    assert rows == list(range(kw["N_pad"]))
+    res = run_chain(env, p, [f[2] for f in fr], [f[0].A for f in fr])
+    for i, (frm, Xp, Y) in enumerate(fr):
+        ref = o.process(Y, frm.A, p)
+        g = o.range_profile(ref["Hd"], o.window(p.N, p.window), p.N_pad)
+        assert rel_l2(strip[i], g) < MAP_TOL
+        assert rel_l2(res["map"][i], ref["P"]) < MAP_TOL
+        n = int(res["n"][i])
+        rs = [(int(t["r"]), int(t["s"])) for t in res["tg"][i][:n]]
+        check_detections_vs_fp64(rs, res["tg"][i]["power"][:n], ref["det"], ref["P"])
+
+
+# ------------------------------------------------------------------ CFAR detection (reading F, local noise level)
+def _cfar_ratio(P, rows, r, c, guard, train, pfa):
+    """P / (alpha(n) mean of the training cells) of one cell, in FP64."""
+    R, C = P.shape
+    on = np.zeros(R, dtype=bool)
+    on[rows] = True
+    w = guard + train
+    tr = [P[(r + dr) % R, (c + dc) % C] for dr in range(-w, w + 1) for dc in range(-w, w + 1)
+          if on[(r + dr) % R] and not (abs(dr) <= guard and abs(dc) <= guard)]
+    return float(P[r, c]) / (o.cfar_alpha(len(tr), pfa) * float(np.mean(tr)))
+
+
+@pytest.mark.parametrize("N,M,L,window,full", [(1024, 256, 128, o.WINDOW_HANN, False),
+                                               (256, 64, 256, o.WINDOW_RECT, True)])
+def test_cfar_detection(env, N, M, L, window, full):
+    """CFAR mode: the map against the FP64 oracle, and the detections exactly
+    those of the oracle's CFAR rule applied to the GPU's own map, except cells
+    whose statistic lies within 1e-4 of the threshold (FP32 training sums)."""
+    base = syn.FrameConfig(N=N, M=M, L_cp=L, qam=16, zc_root=1, n_targets=4, on_grid=False, amp_db=(-10.0, 0.0),
+                           snr_db=(-5.0, -5.0), window=window, detect_k=16)
+    fr = []
+    for f in range(2):
+        d = syn.draw_frame(base, 8500 + f)
+        Xp = o.zc_precode(d.A, 1)
+        fr.append((d, Xp, syn.received(d, Xp)))
+    p = o.Params(N=N, M=M, L_cp=L, zc_root=1, window=window, max_targets=32, detect_mode=o.DETECT_CFAR, pfa=1e-6,
+                 cfar_guard=1, cfar_train=3)
+    res = run_chain(env, p, [f[2] for f in fr], [f[0].A for f in fr])
+    rows = o.support_rows(N, L, window)
+    assert (len(rows) == N) == full
+    for i, (frm, Xp, Y) in enumerate(fr):
+        ref = o.process(Y, frm.A, p)
+        assert rel_l2(res["map"][i], ref["P"]) < MAP_TOL
+        P32 = res["map"][i].astype(np.float64)
+        want = o.cfar_detect(P32, rows, p.pfa, p.cfar_guard, p.cfar_train, p.max_targets)
+        n = int(res["n"][i])
+        assert want.count <= p.max_targets   # every detection is reported
+        got = {(int(t["r"]), int(t["s"])) for t in res["tg"][i][:n]}
+        exp = set(zip(want.r.tolist(), want.s.tolist()))
+        for (r, s) in got ^ exp:
+            ratio = _cfar_ratio(P32, rows, r, s + M // 2, p.cfar_guard, p.cfar_train, p.pfa)
+            assert abs(ratio - 1.0) < 1e-4, f"({r}, {s}) decided differently, statistic {ratio}"
+        # the strong targets are found (one-bin tolerance for off-grid truth)
+        for rho, nu, b in zip(frm.rho, frm.nu, frm.b):
+            if abs(b) ** 2 > 0.3:
+                assert any(abs(r - rho) <= 1.0 and abs(((s - nu) + M // 2) % M - M // 2) <= 1.0 for r, s in got)

@@ -602,3 +602,111 @@ def test_zc_precoding_lowers_papr():
     p1 = 10 * np.log10(o.papr(o.zc_precode(A, 1)))
     assert np.median(p1) < np.median(p0) - 3.0
     assert np.quantile(p1, 0.99) < np.quantile(p0, 0.5)
+
+
+# ---------------------------------------------------------------- amplifier and spectrum (Sec. III-B)
+def test_hpa_limits():
+    """Small inputs pass linearly; large ones saturate at x_bar 10^(q/10);
+    the phase is kept."""
+    x = np.ones((10001, 1), complex)
+    x[0, 0] = 1e-6 * np.exp(0.3j)
+    x[-1, 0] = 1e12 * np.exp(-2.0j)
+    y = o.hpa(x, q=2.0)
+    sat = np.mean(np.abs(x)) * 10 ** 0.2
+    assert abs(y[0, 0] - x[0, 0]) < 1e-9 * abs(x[0, 0])
+    assert abs(abs(y[-1, 0]) - sat) < 1e-6 * sat
+    assert np.allclose(np.angle(y), np.angle(x))
+    # f(a) = a / sqrt(1 + (a/s)^2) at a = s gives s / sqrt(2)
+    z = np.full((4, 1), 3.0 + 0j)
+    assert np.allclose(np.abs(o.hpa(z, 0.0)), 3.0 / np.sqrt(2.0))
+
+
+def test_oversampled_time_matches_direct_sum():
+    rng = np.random.default_rng(4)
+    N, L = 8, 3
+    S = rng.standard_normal((N, 2)) + 1j * rng.standard_normal((N, 2))
+    x = o.oversampled_time(S, L)
+    for n in range(L * N):
+        for c in range(2):
+            want = sum(S[k, c] * np.exp(2j * np.pi * (k if k < N // 2 else k - N) * n / (L * N)) for k in range(N))
+            assert abs(x[n, c] - want) < 1e-9
+    assert np.allclose(o.oversampled_time(S, 1), o.dft_matrix(N).conj() @ S)
+
+
+def test_aci_closed_forms():
+    """A single subcarrier has a constant-modulus time signal: the amplifier
+    only scales it, so nothing leaks out of band; any signal without the
+    amplifier has zero out-of-band power; a clipped two-tone signal leaks."""
+    N, L = 16, 4
+    one = np.zeros((N, 1), complex)
+    one[3] = 1.0
+    x = o.oversampled_time(one, L)
+    assert o.aci_ratio(o.hpa(x), N)[0] < 1e-20
+    rng = np.random.default_rng(2)
+    S = rng.standard_normal((N, 3)) + 1j * rng.standard_normal((N, 3))
+    assert np.all(o.aci_ratio(o.oversampled_time(S, L), N) < 1e-20)
+    two = np.zeros((N, 1), complex)
+    two[1] = two[5] = 1.0
+    assert o.aci_ratio(o.hpa(o.oversampled_time(two, L), 0.0), N)[0] > 1e-4
+
+
+def test_zc_precoding_lowers_amplifier_leakage():
+    """The paper's claim (Sec. III-B): with ZC precoding the amplifier adds less
+    adjacent-channel interference (statistical, 128 subcarriers)."""
+    rng = np.random.default_rng(9)
+    A = syn.qam_symbols(rng, (128, 64), 16)
+    p0, a0 = o.tx_papr_aci(A, 0)
+    p1, a1 = o.tx_papr_aci(A, 1)
+    assert np.median(p1) < np.median(p0)
+    assert np.median(a1) < np.median(a0)
+
+
+# ---------------------------------------------------------------- CFAR detection (reading F, local noise level)
+def test_cfar_alpha_gives_pfa_exactly():
+    """For exponential noise, P[P > alpha * mean of n training cells] has the
+    closed form (1 + alpha/n)^-n; alpha is chosen so that it equals P_fa."""
+    for n in (8, 24, 112):
+        for pfa in (1e-2, 1e-4):
+            a = o.cfar_alpha(n, pfa)
+            assert (1 + a / n) ** (-n) == pytest.approx(pfa, rel=1e-12)
+    assert o.cfar_alpha(10 ** 6, 1e-2) == pytest.approx(-math.log(1e-2), rel=1e-5)
+
+
+def test_cfar_false_alarm_rate_on_noise():
+    """Monte-Carlo check of the closed form on an exponential-noise map: the
+    fraction of cells above the CFAR threshold matches P_fa (local maxima and
+    all); a strong on-grid peak is always detected."""
+    rng = np.random.default_rng(5)
+    R, C = 64, 64
+    P = rng.exponential(1.0, size=(R, C))
+    pfa = 0.05
+    rows = np.arange(R)
+    g, t = 1, 4
+    exceed = 0
+    w = g + t
+    for r in range(R):
+        for c in range(C):
+            tr = [P[(r + dr) % R, (c + dc) % C] for dr in range(-w, w + 1) for dc in range(-w, w + 1)
+                  if not (abs(dr) <= g and abs(dc) <= g)]
+            exceed += P[r, c] >= o.cfar_alpha(len(tr), pfa) * np.mean(tr)
+    assert abs(exceed / (R * C) - pfa) < 4 * math.sqrt(pfa * (1 - pfa) / (R * C)) + 0.01
+    P[20, 30] = 100.0
+    det = o.cfar_detect(P, rows, pfa, g, t, 64)
+    assert (20, 30 - C // 2) in set(zip(det.r.tolist(), det.s.tolist()))
+
+
+def test_cfar_bruteforce_tiny_and_support_edge():
+    """Hand-built 6 x 8 map, support rows 0..3: the training mean of a peak
+    next to the support edge uses only support rows."""
+    P = np.full((6, 8), 1.0)
+    P[4:] = 0.0                       # outside the support
+    P[3, 2] = 50.0
+    P[1, 6] = 5.0
+    det = o.cfar_detect(P, np.arange(4), 0.1, 0, 1, 4)
+    # (3, 2): training = 8 neighbours minus the 3 on row 4 (off support) -> 5 cells of 1
+    a5 = o.cfar_alpha(5, 0.1)
+    assert 50.0 >= a5 * 1.0
+    # (1, 6): 8 training cells of 1 -> alpha(8) = 8 (10^(1/8) - 1) ~ 2.68 < 5
+    got = set(zip(det.r.tolist(), det.s.tolist()))
+    assert got == {(3, 2 - 4), (1, 6 - 4)}
+    assert list(det.power) == [50.0, 5.0]
