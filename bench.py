@@ -42,9 +42,10 @@ COLUMN_BYTES_PER_FRAME = 16 * CFG.N * CFG.M    # the column kernel reads Y and X
 
 # DRAM traffic of the column kernel from one ncu capture of this workload,
 # valid only while its sources are byte-identical to the captured ones.
-TRAFFIC = {"bytes": 268.676096e6 + 6.363136e6,
-           "sources": {"paper_2209_03883_gb300/csrc/column.cu": "a4b249c30005d74ba58b7d4bff5db3b3f778548d",
-                       "paper_2209_03883_gb300/csrc/fft.cuh": "be6a0ab259f107f9f03afd0cdec7d675d6bb08b2"}}
+TRAFFIC = {"bytes": 268.747520e6 + 5.859072e6,
+           "sources": {"paper_2209_03883_gb300/csrc/column.cu": "7e8ff9e9fc7136727ead73dbe38bd7c865422c38",
+                       "paper_2209_03883_gb300/csrc/fft.cuh": "be6a0ab259f107f9f03afd0cdec7d675d6bb08b2",
+                       "paper_2209_03883_gb300/csrc/refine.cuh": "cd4a12e621e0713ccbb4e9a483c65f5bd7eb2b32"}}
 
 
 def captured_traffic():
@@ -438,6 +439,106 @@ def extra_tc(radar, torch, dev, stream, steps, Yd, Xd, params):
             "map_rel_l2_vs_fp32_chain": rel, "frames_with_same_bins_as_fp32": f"{same}/{FRAMES}"}
 
 
+def rmse_sweep(radar, torch, dev, snrs=(-50.0, -45.0, -40.0, -35.0, -30.0, -25.0, -20.0), frames_per_snr=8,
+               seed=7000):
+    """Monte-Carlo range / velocity RMSE against SNR at Table I's size (N = 2048,
+    M = 560, N_cp = 512, Hamming window, 5 off-grid targets at -6..0 dB) for
+    three receivers: ZC precoding + DFT-CE, DFT-CE without precoding, and plain
+    LS estimation (L_cp = N).  Each true target is matched to the nearest
+    detection within 2 bins; a target with none counts as a miss.  Estimates
+    follow Eq. (19) (Delta d = c / (2 N df), Delta v = c / (2 fc M T_s)).  The
+    frame's processing gain is about 60 dB, so the SNRs reach well below 0 dB
+    before the estimates leave the off-grid rounding floor (Delta / sqrt(12))."""
+    N, M, L = 2048, 560, 512
+    forms = {"zcp_dft_ce": dict(zc_root=1, L_cp=L), "dft_ce": dict(zc_root=0, L_cp=L),
+             "ls": dict(zc_root=0, L_cp=N)}
+    Ts = (N + L) / (N * 240e3)
+    dd, dv = 3e8 / (2 * N * 240e3), 3e8 / (2 * 77e9 * M * Ts)
+    out = {"workload": "N=2048, M=560, N_cp=512 (Table I), Hamming, 5 off-grid targets -6..0 dB",
+           "snr_db": list(snrs), "frames_per_snr": frames_per_snr, "range_resolution_m": dd,
+           "velocity_resolution_mps": dv}
+    plans = {k: radar.Plan(N=N, M=M, L_cp=v["L_cp"], n_cp=L, zc_root=v["zc_root"], window=radar.WINDOW_HAMMING,
+                           max_targets=8, max_frames=frames_per_snr) for k, v in forms.items()}
+    for k in forms:
+        out[k] = {"range_rmse_m": [], "velocity_rmse_mps": [], "miss_rate": []}
+    for si, snr in enumerate(snrs):
+        cfg = syn.FrameConfig(N=N, M=M, L_cp=L, qam=16, zc_root=1, n_targets=5, on_grid=False, amp_db=(-6.0, 0.0),
+                              snr_db=(snr, snr), window=2, detect_k=8)
+        frs = [syn.draw_frame(cfg, seed + 100 * si + f) for f in range(frames_per_snr)]
+        Ad = torch.from_numpy(np.stack([syn.to_lk(d.A) for d in frs])).to(dev)
+        Xp = torch.empty_like(Ad)
+        radar.ofdm_zc_precode(plans["zcp_dft_ce"], Ad, Xp, frames_per_snr)
+        Xpn = Xp.cpu().numpy()
+        for k, v in forms.items():
+            tx = [syn.from_lk(Xpn[i]).astype(np.complex128) if v["zc_root"] else d.A for i, d in enumerate(frs)]
+            Y = torch.from_numpy(np.stack([syn.to_lk(syn.received(d, tx[i])) for i, d in enumerate(frs)])).to(dev)
+            res = radar.process(plans[k], Y, Ad, with_map=False)
+            torch.cuda.synchronize()
+            tv = radar.targets_view(res["targets"], frames_per_snr, 8)
+            nt = res["n_targets"].cpu().numpy()
+            er, ev, miss, tot = [], [], 0, 0
+            for i, d in enumerate(frs):
+                det = [(int(t["r"]), int(t["s"])) for t in tv[i][:int(nt[i])]]
+                for rho, nu in zip(d.rho, d.nu):
+                    tot += 1
+                    best = None
+                    for r, s_ in det:
+                        dr_, ds_ = r - rho, ((s_ - nu) + M / 2) % M - M / 2
+                        if abs(dr_) <= 2 and abs(ds_) <= 2 and (best is None or dr_ ** 2 + ds_ ** 2 < best[0]):
+                            best = (dr_ ** 2 + ds_ ** 2, dr_, ds_)
+                    if best is None:
+                        miss += 1
+                    else:
+                        er.append(best[1] * dd)
+                        ev.append(best[2] * dv)
+            out[k]["range_rmse_m"].append(float(np.sqrt(np.mean(np.square(er)))) if er else None)
+            out[k]["velocity_rmse_mps"].append(float(np.sqrt(np.mean(np.square(ev)))) if ev else None)
+            out[k]["miss_rate"].append(miss / tot)
+    for pl in plans.values():
+        pl.close()
+    return out
+
+
+def extra_table1(radar, torch, dev, stream, steps, frames=16):
+    """Throughput of the chain at Table I's size (N = 2048, M = M' = 560: the
+    Doppler stage as a matrix product, not a power-of-two FFT) and the RMSE
+    sweep."""
+    N, M, L = 2048, 560, 512
+    cfg = syn.FrameConfig(N=N, M=M, L_cp=L, qam=16, zc_root=1, n_targets=5, on_grid=False, amp_db=(-6.0, 0.0),
+                          snr_db=(0.0, 0.0), window=2, detect_k=5)
+    plan = radar.Plan(N=N, M=M, L_cp=L, n_cp=L, zc_root=1, window=radar.WINDOW_HAMMING, max_targets=5,
+                      max_frames=frames)
+    frs = [syn.draw_frame(cfg, 7900 + f) for f in range(frames)]
+    Ad = torch.from_numpy(np.stack([syn.to_lk(d.A) for d in frs])).to(dev)
+    Xp = torch.empty_like(Ad)
+    radar.ofdm_zc_precode(plan, Ad, Xp, frames)
+    Xpn = Xp.cpu().numpy()
+    Y = torch.from_numpy(np.stack([syn.to_lk(syn.received(d, syn.from_lk(Xpn[i]).astype(np.complex128)))
+                                   for i, d in enumerate(frs)])).to(dev)
+    o = radar.alloc_outputs(plan, frames, dev)
+    fn = lambda: radar.ofdm_radar_process(plan, Y, Ad, frames, o["map"], o["targets"], o["n_targets"], o["status"],
+                                          stream)
+    for _ in range(2):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    plan.timing_enable(True)
+    fn()
+    torch.cuda.synchronize()
+    stage = {k: round(v[0], 4) for k, v in plan.timing_read().items() if v[1]}
+    plan.timing_enable(False)
+    plan.close()
+    return {"workload": f"{frames} frames N=2048, M=M'=560, L_cp=N_cp=512, Hamming, ZC precoding",
+            "value": frames / (ms / 1e3), "unit": "frames/s", "ms_per_step": ms, "stage_ms": stage,
+            "rmse_vs_snr": rmse_sweep(radar, torch, dev)}
+
+
 def _hits(tv, nt, truth, M):
     h = 0
     for f, (rho, nu, _b, _snr) in enumerate(truth):
@@ -543,7 +644,8 @@ def run_ours(args):
 
     params = dict(N=CFG.N, M=CFG.M, L_cp=CFG.L_cp, zc_root=CFG.zc_root, window=CFG.window,
                   max_targets=CFG.detect_k, max_frames=FRAMES)
-    plan = radar.Plan(**params)
+    tc = args.precision == "split_fp16"
+    plan = radar.Plan(precision=radar.PREC_SPLIT_FP16, **params) if tc else radar.Plan(**params)
 
     # Inputs: QAM grids, channels and noise drawn on the host; the transmitted
     # (precoded) grid comes from the library's own ZC transform.
@@ -662,13 +764,14 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32" if not tc else "f16x2 split (f32 accumulate)", "data": "synthetic",
         "config": {"workload": WORKLOAD, "frames_per_step": FRAMES, "N": CFG.N, "M": CFG.M,
-                   "L_cp": CFG.L_cp, "precision": "fp32", "parallelism": f"replicas x{world} (frames)",
+                   "L_cp": CFG.L_cp, "precision": args.precision, "parallelism": f"replicas x{world} (frames)",
                    "l2": f"inputs {2 * FRAMES * CFG.N * CFG.M * 8 / 1e6:.0f} MB per step > 129 MB L2; no flush"},
-        "roofline": {"bound": "hbm", "kernel": "column_group_pipe_kernel<1024, 64>", "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "hbm", "kernel": "column_tc_kernel" if tc else "column_group_pipe_kernel<1024, 64>",
+                     "achieved": achieved, "peak": peak,
                      "peak_source": f"{peak_kind} hbm_gbs", "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": captured_traffic(),
+                     "traffic": None if tc else captured_traffic(),
                      "algorithmic_bytes_per_launch": COLUMN_BYTES_PER_FRAME * FRAMES,
                      "avg_launch_ms": col_avg_ms,
                      "step_frac": BYTES_PER_FRAME * FRAMES / (step_ms / 1e3) / 1e9 / peak},
@@ -704,6 +807,10 @@ def run_ours(args):
         except Exception as exc:
             extra["tensor_core_split_fp16"] = {"error": str(exc)}
         try:
+            extra["table1_2048x560"] = extra_table1(radar, torch, dev, stream, max(3, min(args.steps, 10)))
+        except Exception as exc:
+            extra["table1_2048x560"] = {"error": str(exc)}
+        try:
             extra["learned_vs_plain"] = extra_learned(radar, torch, dev, stream, max(3, min(args.steps, 10)))
         except Exception as exc:
             extra["learned_vs_plain"] = {"error": str(exc)}
@@ -725,6 +832,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and FPS-SFT measurements")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "split_fp16"],
+                    help="column stage of the headline chain: FP32 FFTs or split-FP16 tensor cores")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

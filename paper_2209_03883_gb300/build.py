@@ -15,7 +15,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libofdm_radar.so")
-SOURCES = ["column.cu", "column_tc.cu", "doppler_detect.cu", "plan.cu", "noalloc.cu", "fps.cu", "cnn.cu", "learned.cu", "tx.cu", "range_pad.cu"]
+SOURCES = ["column.cu", "column_tc.cu", "doppler_detect.cu", "plan.cu", "noalloc.cu", "fps.cu", "cnn.cu", "learned.cu", "tx.cu", "range_pad.cu", "doppler_general.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC"]
 

@@ -24,44 +24,62 @@ __device__ __forceinline__ float wval(const float* w, int i, int bf16) {
   return bf16 ? __bfloat162float(__float2bfloat16_rn(v)) : v;
 }
 
-// y[b][o] = conv(x[b], w) + bias, optionally ReLU.  Ci, Co <= 16.
-__global__ void __launch_bounds__(kTile * kTile)
-conv3x3_fwd(const float* __restrict__ x, const float* __restrict__ w, const float* __restrict__ bias,
-            float* __restrict__ y, int Ci, int Co, int H, int W, int relu, int bf16) {
-  __shared__ float sx[kMaxC][kHalo][kHalo];
-  __shared__ float sw[kMaxC * kMaxC * 9];
+// y[b][o] = conv(x[b], w) + bias, optionally ReLU (Ci, Co <= 16), used by
+// inference and training: 16 x 16 output pixels per CTA, 64 threads of 1 x 4
+// pixels each, so every weight read from shared memory serves four
+// multiply-adds (the 16 -> 16 layer reads 2304 weights per pixel).  Each
+// output sums over (c, dy, dx) in that order.
+constexpr int kPx = 4;                       // pixels per thread (along x)
+template <int CI, int CO>
+__global__ void __launch_bounds__(kTile * kTile / kPx)
+conv3x3_fwd_x4(const float* __restrict__ x, const float* __restrict__ w, const float* __restrict__ bias,
+               float* __restrict__ y, int H, int W, int relu, int bf16) {
+  __shared__ float sx[CI][kHalo][kHalo];
+  __shared__ float sw[CO * CI * 9];
   const int b = blockIdx.z;
-  const int ty = threadIdx.x / kTile, tx = threadIdx.x % kTile;
+  const int ty = threadIdx.x / (kTile / kPx), tx0 = (threadIdx.x % (kTile / kPx)) * kPx;
   const int y0 = blockIdx.y * kTile, x0 = blockIdx.x * kTile;
-  for (int i = threadIdx.x; i < Co * Ci * 9; i += blockDim.x) sw[i] = wval(w, i, bf16);
-  for (int i = threadIdx.x; i < Ci * kHalo * kHalo; i += blockDim.x) {
+  for (int i = threadIdx.x; i < CO * CI * 9; i += blockDim.x) sw[i] = wval(w, i, bf16);
+  for (int i = threadIdx.x; i < CI * kHalo * kHalo; i += blockDim.x) {
     const int c = i / (kHalo * kHalo), r = (i / kHalo) % kHalo, q = i % kHalo;
     const int gy = y0 + r - 1, gx = x0 + q - 1;
-    sx[c][r][q] = (gy >= 0 && gy < H && gx >= 0 && gx < W) ? x[(((long)b * Ci + c) * H + gy) * W + gx] : 0.f;
+    sx[c][r][q] = (gy >= 0 && gy < H && gx >= 0 && gx < W) ? x[(((long)b * CI + c) * H + gy) * W + gx] : 0.f;
   }
   __syncthreads();
-  const int gy = y0 + ty, gx = x0 + tx;
-  if (gy >= H || gx >= W) return;
-  float acc[kMaxC];
+  const int gy = y0 + ty;
+  if (gy >= H) return;
+  float acc[kPx][CO];
 #pragma unroll
-  for (int o = 0; o < kMaxC; ++o) acc[o] = 0.f;
-  for (int c = 0; c < Ci; ++c)
+  for (int p = 0; p < kPx; ++p)
 #pragma unroll
-    for (int dy = 0; dy < 3; ++dy)
+    for (int o = 0; o < CO; ++o) acc[p][o] = 0.f;
+#pragma unroll 2
+  for (int c = 0; c < CI; ++c)
 #pragma unroll
-      for (int dx = 0; dx < 3; ++dx) {
-        const float v = sx[c][ty + dy][tx + dx];
+    for (int dy = 0; dy < 3; ++dy) {
+      float v[kPx + 2];
 #pragma unroll
-        for (int o = 0; o < kMaxC; ++o)
-          if (o < Co) acc[o] = fmaf(sw[(o * Ci + c) * 9 + dy * 3 + dx], v, acc[o]);
-      }
+      for (int q = 0; q < kPx + 2; ++q) v[q] = sx[c][ty + dy][tx0 + q];
 #pragma unroll
-  for (int o = 0; o < kMaxC; ++o)
-    if (o < Co) {
-      float v = acc[o] + bias[o];
-      if (relu) v = fmaxf(v, 0.f);
-      y[(((long)b * Co + o) * H + gy) * W + gx] = v;
+      for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+        for (int o = 0; o < CO; ++o) {
+          const float wt = sw[(o * CI + c) * 9 + dy * 3 + dx];
+#pragma unroll
+          for (int p = 0; p < kPx; ++p) acc[p][o] = fmaf(wt, v[p + dx], acc[p][o]);
+        }
     }
+#pragma unroll
+  for (int p = 0; p < kPx; ++p) {
+    const int gx = x0 + tx0 + p;
+    if (gx >= W) continue;
+#pragma unroll
+    for (int o = 0; o < CO; ++o) {
+      float val = acc[p][o] + bias[o];
+      if (relu) val = fmaxf(val, 0.f);
+      y[(((long)b * CO + o) * H + gy) * W + gx] = val;
+    }
+  }
 }
 
 // gx[b][c] = sum_o sum_k w[o][c][k] * gy[b][o](shifted), times (act > 0) if act != null.
@@ -170,9 +188,10 @@ dim3 conv_grid(int B, int H, int W) { return dim3((W + kTile - 1) / kTile, (H + 
 cudaError_t cnn_forward(const float* th, int bf16, const float* x, int B, int H, int W, float* a1, float* a2,
                         float* z, cudaStream_t s) {
   const dim3 g = conv_grid(B, H, W);
-  conv3x3_fwd<<<g, kTile * kTile, 0, s>>>(x, th + kW1, th + kB1, a1, 1, 16, H, W, 1, bf16);
-  conv3x3_fwd<<<g, kTile * kTile, 0, s>>>(a1, th + kW2, th + kB2, a2, 16, 16, H, W, 1, bf16);
-  conv3x3_fwd<<<g, kTile * kTile, 0, s>>>(a2, th + kW3, th + kB3, z, 16, 1, H, W, 0, bf16);
+  constexpr int T = kTile * kTile / kPx;
+  conv3x3_fwd_x4<1, 16><<<g, T, 0, s>>>(x, th + kW1, th + kB1, a1, H, W, 1, bf16);
+  conv3x3_fwd_x4<16, 16><<<g, T, 0, s>>>(a1, th + kW2, th + kB2, a2, H, W, 1, bf16);
+  conv3x3_fwd_x4<16, 1><<<g, T, 0, s>>>(a2, th + kW3, th + kB3, z, H, W, 0, bf16);
   return cudaGetLastError();
 }
 

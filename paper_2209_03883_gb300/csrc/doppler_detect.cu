@@ -253,7 +253,7 @@ __device__ __forceinline__ uint64_t warp_merge_lists(P src, int nlists, int K, i
 // scan, the floor, the band's top K and the last CTA's merge.  Shared by the
 // detection kernel (which stages the rows from the power strip) and the fused
 // Doppler + detection kernel (which computes them).
-template <int LOGC>
+template <int LOGC, bool CFAR = false>
 __device__ __forceinline__ void band_detect(float* tile, ofdm_target* __restrict__ out, int32_t* __restrict__ n_out,
                                             uint32_t* __restrict__ status, uint32_t* __restrict__ wstatus,
                                             const DetectArgs& a, int band, int f, int t0, int tr,
@@ -266,7 +266,6 @@ __device__ __forceinline__ void band_detect(float* tile, ofdm_target* __restrict
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int K = a.K, Mp = a.Mp, logMp = a.logMp;
   const bool thr = a.mode == OFDM_DETECT_THRESHOLD;
-  const bool cfar = a.mode == OFDM_DETECT_CFAR;   // base holds the frame's input rows
   const float eta = thr ? (a.use_fixed_eta ? a.eta_fixed : a.eta[f]) : 0.f;
   if (tid == 0) { s_n = 0; s_cnt = 0; }
 
@@ -311,7 +310,7 @@ __device__ __forceinline__ void band_detect(float* tile, ofdm_target* __restrict
       const float p = mc;
       // fmaxf skips NaN, so this is "no neighbour compares greater"
       bool cand = i < tr && p > 0.f && !(nmax > p) && (!thr || p >= eta) &&
-                  (!cfar || cfar_pass(base, a, t0 + i, c, p));
+                  (!CFAR || cfar_pass(base, a, t0 + i, c, p));   // CFAR: base holds the frame's input rows
       const uint32_t r = (rbase + (uint32_t)i) & (uint32_t)(a.Np - 1);
       if (cand && nmax == p) cand = !tie_lost(tile, logMp, a.Np, (int)r, i + 1, c, p);
       const uint64_t key =
@@ -432,7 +431,7 @@ __device__ __forceinline__ void band_detect(float* tile, ofdm_target* __restrict
 }
 
 
-template <int LOGC>
+template <int LOGC, bool CFAR>
 __global__ void __launch_bounds__(kDetThreads)
 detect_band_kernel(const float* __restrict__ src, ofdm_target* __restrict__ out, int32_t* __restrict__ n_out,
                    uint32_t* __restrict__ status, uint32_t* __restrict__ wstatus, DetectArgs a) {
@@ -464,7 +463,7 @@ detect_band_kernel(const float* __restrict__ src, ofdm_target* __restrict__ out,
   }
   asm volatile("cp.async.commit_group;\n" ::: "memory");
   asm volatile("cp.async.wait_all;\n" ::: "memory");
-  band_detect<LOGC>(tile, out, n_out, status, wstatus, a, band, f, t0, tr, base);
+  band_detect<LOGC, CFAR>(tile, out, n_out, status, wstatus, a, band, f, t0, tr, base);
 }
 
 // Fused Doppler stage and detection (top-K mode, 64 <= M' <= 256; frames
@@ -517,7 +516,7 @@ doppler_band_kernel(const float2* __restrict__ strip, float* __restrict__ map, o
       if (mrow) __stcs(mrow + c, p);
     }
   }
-  band_detect<LOGC>(tile, out, n_out, status, wstatus, a, band, f, t0, tr, nullptr);
+  band_detect<LOGC, false>(tile, out, n_out, status, wstatus, a, band, f, t0, tr, nullptr);
 }
 
 __global__ void __launch_bounds__(1024) median_kernel(const float* __restrict__ src, DetectArgs a) {
@@ -623,7 +622,10 @@ cudaError_t launch_detect(const float* pow, ofdm_target* out, int32_t* n_out, ui
   const size_t tile = (size_t)(full_rows + 2) * a.Mp * sizeof(float);
   const size_t smem = tile;
   if (a.logMp > 10 || a.bands > 1024) return cudaErrorInvalidValue;
-  auto kern = a.logMp <= 8 ? detect_band_kernel<0> : (a.logMp == 9 ? detect_band_kernel<1> : detect_band_kernel<2>);
+  const bool cfar = a.mode == OFDM_DETECT_CFAR;
+  auto kern = a.logMp <= 8 ? (cfar ? detect_band_kernel<0, true> : detect_band_kernel<0, false>)
+            : a.logMp == 9 ? (cfar ? detect_band_kernel<1, true> : detect_band_kernel<1, false>)
+                           : (cfar ? detect_band_kernel<2, true> : detect_band_kernel<2, false>);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   ++*launches;

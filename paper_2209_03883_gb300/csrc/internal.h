@@ -84,7 +84,10 @@ struct DetectArgs {
 };
 
 // Row bands of the detection grid: kDetBandCells cells per CTA.
-constexpr int kDetBandCells = 4096;
+#ifndef OFDM_DET_BAND_CELLS
+#define OFDM_DET_BAND_CELLS 4096
+#endif
+constexpr int kDetBandCells = OFDM_DET_BAND_CELLS;
 // The rows are spread evenly over the fewest bands of at most
 // kDetBandCells / M' rows (130 rows at M' = 256: 9 bands of 15 or 10, not 16
 // and a last band of 2), so that no CTA carries much more than the others.
@@ -144,6 +147,16 @@ struct PadArgs {
 int pad_threads(int NP);
 cudaError_t launch_range_pad(int N, int NP, const float2* taps, float2* strip, const PadArgs& a, cudaStream_t s,
                              int* launches);
+
+// Doppler grid M' that is not a power of two (doppler_general.cu): the
+// windowed Doppler DFT as a complex matrix product (roots = e^{-2 pi i m / M'})
+// and detection by sorted block lists (a.part_keys holds detect_general_blocks
+// lists of 32 keys per frame).
+cudaError_t launch_doppler_general(const float2* strip, float* map, float* pow, const DopplerArgs& a,
+                                   const float2* roots, cudaStream_t s, int* launches);
+int detect_general_blocks(int rows, int Mp);
+cudaError_t launch_detect_general(const float* pow, ofdm_target* out, int32_t* n_out, uint32_t* status,
+                                  uint32_t* wstatus, const DetectArgs& a, cudaStream_t s, int* launches);
 
 // Transmit side (tx.cu): PAPR and amplifier out-of-band power per symbol.
 struct TxArgs {

@@ -20,6 +20,7 @@ constexpr int kHostChunks = 16;  // frame chunks of the host-buffer pipeline
 struct ofdm_radar_plan {
   ofdm_radar_params p;
   int Np, Mp;
+  int gen = 0;                 // M' not a power of two: matrix-product Doppler stage and general detection
   int rows, row0, full;        // DFT-CE support (Eqs. (17), (21))
   int z0, nz;                  // contiguous zero rows of the map
   int rinv;
@@ -258,10 +259,11 @@ int ofdm_radar_plan_create(const ofdm_radar_params* pin, ofdm_radar_plan** out) 
   const int N = p.N, M = p.M;
   const int Np = p.N_pad ? p.N_pad : N, Mp = p.M_pad ? p.M_pad : M;
   if (!is_pow2(N) || N < 64 || N > 4096) return OFDM_ERR_UNSUPPORTED_SIZE;
-  if (!is_pow2(M) || M < 16 || M > 1024) return OFDM_ERR_UNSUPPORTED_SIZE;
+  // M: 16..1024, a multiple of 4 (Table I's 560 included); M' >= M likewise
+  if (M < 16 || M > 1024 || M % 4) return OFDM_ERR_UNSUPPORTED_SIZE;
   // range zero padding: N' = 2N, 4N or 8N, at most 4096
   if (Np != N && (!is_pow2(Np) || Np < 2 * N || Np > 8 * N || Np > 4096)) return OFDM_ERR_UNSUPPORTED_SIZE;
-  if (!is_pow2(Mp) || Mp < M || Mp > 1024) return OFDM_ERR_UNSUPPORTED_SIZE;
+  if (Mp < M || Mp > 1024 || Mp % 4) return OFDM_ERR_UNSUPPORTED_SIZE;
   if (p.L_cp < 1 || p.L_cp > N) return OFDM_ERR_INVALID_ARG;
   if (p.n_cp < 0) return OFDM_ERR_INVALID_ARG;
   if (p.zc_root < 0 || (p.zc_root > 0 && (p.zc_root % 2) == 0)) return OFDM_ERR_INVALID_ARG;
@@ -290,6 +292,7 @@ int ofdm_radar_plan_create(const ofdm_radar_params* pin, ofdm_radar_plan** out) 
   pl->p = p;
   pl->Np = Np;
   pl->Mp = Mp;
+  pl->gen = is_pow2(Mp) ? 0 : 1;
   // Support rows: taps n < L_cp (Eq. (21)); a periodic Hann/Hamming window
   // over k spreads each tap to r - 1 and r + 1 (circular).
   const int spread = p.window == OFDM_WINDOW_RECT ? 0 : 2;
@@ -347,7 +350,13 @@ int ofdm_radar_plan_create(const ofdm_radar_params* pin, ofdm_radar_plan** out) 
   std::vector<float2> twN, twM, twG;
   build_twiddles(twN, N, column_points_per_thread(N));
   if (N >= 1024) build_twiddles(twG, N, 16);   // column kernel in groups of N / 16 threads
-  if (Mp <= 32) {
+  if (!is_pow2(Mp)) {   // roots e^{-2 pi i m / M'} of the matrix-product Doppler stage
+    twM.resize(Mp);
+    for (int m = 0; m < Mp; ++m) {
+      const double a = -2.0 * M_PI * m / Mp;
+      twM[m] = make_float2((float)cos(a), (float)sin(a));
+    }
+  } else if (Mp <= 32) {
     twM.resize(Mp);
     for (int m = 0; m < Mp; ++m) {
       const double a = 2.0 * M_PI * m / Mp;
@@ -387,6 +396,7 @@ int ofdm_radar_plan_create(const ofdm_radar_params* pin, ofdm_radar_plan** out) 
   {
     int br = 0;
     ofdm::detect_bands(pl->rows, Mp, &br, &pl->det_bands);
+    if (!is_pow2(Mp)) pl->det_bands = ofdm::detect_general_blocks(pl->rows, Mp);
   }
   if (e == cudaSuccess) e = dalloc(&pl->d_detkeys, (size_t)p.max_frames * pl->det_bands * 32);
   if (e == cudaSuccess) e = dalloc(&pl->d_dettick, 2 * (size_t)p.max_frames);
@@ -648,6 +658,17 @@ cudaError_t run_chain(ofdm_radar_plan* pl, const float2* Y, const float2* X, int
   }
   if (e != cudaSuccess) return e;
   DetectArgs ta = detect_args(pl, frames, 1);
+  if (pl->gen) {   // M' not a power of two
+    {
+      ScopedTimer tm(pl, s, K_DOPPLER);
+      if (map) e = ofdm::launch_zero_rows(map, frames, pl->Np, pl->Mp, pl->z0, pl->nz, s, launches);
+      if (e == cudaSuccess)
+        e = ofdm::launch_doppler_general(pl->d_strip, map, pl->d_pow, doppler_args(pl, frames), pl->twM, s, launches);
+    }
+    if (e != cudaSuccess) return e;
+    ScopedTimer tm(pl, s, K_DETECT);
+    return ofdm::launch_detect_general(pl->d_pow, tg, nt, st, pl->d_wstatus, ta, s, launches);
+  }
   set_zero_rows(pl, map, nullptr, &ta);   // the detection launch zeroes the rows outside the support
   if (ofdm::doppler_detect_fusable(ta, pl->Mp)) {
     ScopedTimer tm(pl, s, K_DETECT);      // Doppler stage included
@@ -719,7 +740,10 @@ int ofdm_radar_doppler(ofdm_radar_plan* pl, const ofdm_c32* strip, int32_t frame
   int launches = 0;
   cudaError_t e = ofdm::launch_zero_rows(out_map, frames, pl->Np, pl->Mp, pl->z0, pl->nz, (cudaStream_t)stream,
                                          &launches);
-  if (e == cudaSuccess)
+  if (e == cudaSuccess && pl->gen)
+    e = ofdm::launch_doppler_general((const float2*)strip, out_map, nullptr, doppler_args(pl, frames), pl->twM,
+                                     (cudaStream_t)stream, &launches);
+  else if (e == cudaSuccess)
     e = ofdm::launch_doppler(pl->Mp, (const float2*)strip, out_map, pl->d_pow, doppler_args(pl, frames),
                              (cudaStream_t)stream, &launches);
   return finish(pl, launches, e);
@@ -729,8 +753,10 @@ int ofdm_radar_detect(ofdm_radar_plan* pl, const float* map, int32_t frames, ofd
                       int32_t* n_targets, uint32_t* status, void* stream) {
   if (!pl || !map || bad_frames(pl, frames)) return OFDM_ERR_INVALID_ARG;
   int launches = 0;
-  cudaError_t e = ofdm::launch_detect(map, out_targets, n_targets, status, nullptr, detect_args(pl, frames, 0),
-                                      (cudaStream_t)stream, &launches);
+  cudaError_t e = pl->gen ? ofdm::launch_detect_general(map, out_targets, n_targets, status, nullptr,
+                                                        detect_args(pl, frames, 0), (cudaStream_t)stream, &launches)
+                          : ofdm::launch_detect(map, out_targets, n_targets, status, nullptr,
+                                                detect_args(pl, frames, 0), (cudaStream_t)stream, &launches);
   return finish(pl, launches, e);
 }
 
@@ -829,7 +855,7 @@ int ofdm_fps_sft(ofdm_radar_plan* pl, const ofdm_c32* Y, const ofdm_c32* X, int3
     return OFDM_ERR_INVALID_ARG;
   const ofdm_radar_params& p = pl->p;
   const int N = p.N, M = p.M, Q = N > M ? N : M;
-  if (Q > 1024 || pl->Mp != M || pl->Np != N) return OFDM_ERR_UNSUPPORTED_SIZE;
+  if (Q > 1024 || pl->Mp != M || pl->Np != N || !is_pow2(M)) return OFDM_ERR_UNSUPPORTED_SIZE;
   if (fp->iterations < 1 || fp->iterations > 16 || fp->offsets < 3 || fp->offsets > 8 ||
       fp->max_recover < 1 || fp->max_recover > 64 || !(fp->bin_pfa > 0.f && fp->bin_pfa < 1.f) ||
       !(fp->coherence_min >= 0.f && fp->coherence_min <= 1.f) || !(fp->dynamic_range >= 0.f))

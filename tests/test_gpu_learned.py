@@ -185,3 +185,85 @@ def test_training_lowers_loss_and_checkpoint_roundtrip(env):
         tr2.load(path)
         assert tr2.step == tr.step
         assert torch.equal(tr2.logits(Y, A), z1)
+
+
+def test_trained_network_gain_over_the_plain_chain(env, capsys):
+    """What the trained network gains over the chain without it, on held-out
+    frames of the learned workload's shape (4096 x 1024, L_cp 512, 32 off-grid
+    targets, SNR U[-15, 5] dB): frames/s of both forms and targets found
+    within one bin.  The learned form replaces only the Doppler stage and the
+    detection; the column stage (ZC transform, division, DFT-CE) is shared and
+    is most of the plain form's time, which bounds the possible gain.  The test
+    states the measured gain and that bound, and requires equal detection
+    accuracy up to 1 % of the targets."""
+    radar, torch, dev = env
+    from paper_2209_03883_gb300.learned import Trainer, coarse_labels
+    cfg = syn.CONFIGS[5]
+    N, M, L, B = cfg.N, cfg.M, cfg.L_cp, 4
+    tplan = radar.Plan(N=N, M=M, L_cp=L, max_frames=B, max_targets=cfg.detect_k)
+    tr = Trainer(tplan, torch, dev, seed=5)
+    rows = tplan.support_rows()
+
+    def precode_with(plan):
+        def f(A):
+            out = torch.empty_like(A)
+            radar.ofdm_zc_precode(plan, A, out, A.shape[0])
+            return out
+        return f
+
+    for step in range(120):
+        Y, A, truth = syn.draw_frames_torch(cfg, [5 * 1000 + 300 + B * step + i for i in range(B)], dev,
+                                            precode_with(tplan))
+        tr.train_step(Y, A, coarse_labels(truth, N, M, len(rows), rows[0], tr.Hc, tr.Mc))
+    Yv, Av, _ = syn.draw_frames_torch(cfg, [5 * 1000 + 60 + i for i in range(B)], dev, precode_with(tplan))
+    thr = float(torch.topk(tr.logits(Yv, Av).reshape(B, -1), 64, dim=1).values[:, -1].mean())
+    n_eval = 8
+    plan = radar.Plan(N=N, M=M, L_cp=L, max_frames=n_eval, max_targets=cfg.detect_k)
+    radar.ofdm_radar_learned_prepare(plan)
+    Y, A, truth = syn.draw_frames_torch(cfg, [5 * 1000 + 700 + f for f in range(n_eval)], dev, precode_with(plan))
+    po = radar.alloc_outputs(plan, n_eval, dev, with_map=False)
+    lo = radar.alloc_outputs(plan, n_eval, dev, with_map=False)
+    plain = lambda: radar.ofdm_radar_process(plan, Y, A, n_eval, None, po["targets"], po["n_targets"], po["status"])
+    learned = lambda: radar.ofdm_radar_process_learned(plan, tr.theta, Y, A, n_eval, thr, 256, lo["targets"],
+                                                       lo["n_targets"], lo["status"])
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms_plain, ms_learned = timed(plain), timed(learned)
+    plan.timing_enable(True)
+    plain()
+    torch.cuda.synchronize()
+    st = plan.timing_read()
+    plan.timing_enable(False)
+    col = st["column"][0]
+    tail = sum(v[0] for k, v in st.items() if k != "column")
+    bound = (col + tail) / col          # the learned stages for free
+
+    def hits(o):
+        tv = radar.targets_view(o["targets"], n_eval, cfg.detect_k)
+        nt = o["n_targets"].cpu().numpy()
+        h = 0
+        for f, (rho, nu, _b, _snr) in enumerate(truth):
+            got = [(int(t["r"]), int(t["s"])) for t in tv[f][:int(nt[f])]]
+            for a_, b_ in zip(rho, nu):
+                h += any(abs(r - a_) <= 1.0 and abs(((s - b_) + M // 2) % M - M // 2) <= 1.0 for r, s in got)
+        return h
+
+    hp, hl = hits(po), hits(lo)
+    total = cfg.n_targets * n_eval
+    gain = ms_plain / ms_learned
+    with capsys.disabled():
+        print(f"\nlearned vs plain on {n_eval} frames {N}x{M}: gain {gain:.3f}x "
+              f"(plain {ms_plain:.3f} ms, learned {ms_learned:.3f} ms; bound if the learned stages were free "
+              f"{bound:.3f}x), targets found {hl}/{total} learned vs {hp}/{total} plain")
+    assert gain <= bound * 1.05
+    assert hl >= hp - 0.01 * total

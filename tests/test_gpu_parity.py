@@ -465,3 +465,45 @@ def test_cfar_detection(env, N, M, L, window, full):
         for rho, nu, b in zip(frm.rho, frm.nu, frm.b):
             if abs(b) ** 2 > 0.3:
                 assert any(abs(r - rho) <= 1.0 and abs(((s - nu) + M // 2) % M - M // 2) <= 1.0 for r, s in got)
+
+
+# ------------------------------------------------------------------ Doppler grids that are not powers of two
+GENERAL_M = [
+    ("table1_2048x560_hamming", dict(N=2048, M=560, L_cp=512, window=o.WINDOW_HAMMING, targets=5, frames=1)),
+    ("64x20_rect", dict(N=64, M=20, L_cp=8, window=o.WINDOW_RECT, targets=2, frames=2)),
+    ("256x100_hann", dict(N=256, M=100, L_cp=32, window=o.WINDOW_HANN, targets=3, frames=2)),
+    ("128x48_pad60", dict(N=128, M=48, M_pad=60, L_cp=16, window=o.WINDOW_HANN, targets=2, frames=2)),
+    ("256x100_threshold", dict(N=256, M=100, L_cp=32, window=o.WINDOW_HANN, targets=3, frames=2,
+                               detect_mode=o.DETECT_THRESHOLD)),
+    ("256x100_full_rect", dict(N=256, M=100, L_cp=256, window=o.WINDOW_RECT, targets=3, frames=2)),
+]
+
+
+@pytest.mark.parametrize("name,kw", GENERAL_M, ids=[c[0] for c in GENERAL_M])
+def test_doppler_grid_not_a_power_of_two(env, name, kw):
+    """M' = 560 = 2^4 5 7 (Table I) and other non-power-of-two Doppler grids:
+    the matrix-product Doppler stage and the general detection against the
+    oracle (map, bins; the detection itself exactly on the GPU's own map)."""
+    base = syn.FrameConfig(N=kw["N"], M=kw["M"], L_cp=kw["L_cp"], qam=16, zc_root=1, n_targets=kw["targets"],
+                           on_grid=False, amp_db=(-6.0, 0.0), snr_db=(0.0, 0.0), window=kw["window"], detect_k=4)
+    fr = []
+    for f in range(kw["frames"]):
+        d = syn.draw_frame(base, 8700 + f)
+        Xp = o.zc_precode(d.A, 1)
+        fr.append((d, Xp, syn.received(d, Xp)))
+    p = o.Params(N=kw["N"], M=kw["M"], L_cp=kw["L_cp"], zc_root=1, window=kw["window"], max_targets=4,
+                 M_pad=kw.get("M_pad", 0), detect_mode=kw.get("detect_mode", o.DETECT_TOPK))
+    res = run_chain(env, p, [f[2] for f in fr], [f[0].A for f in fr])
+    for i, (frm, Xp, Y) in enumerate(fr):
+        ref = o.process(Y, frm.A, p)
+        assert rel_l2(res["map"][i], ref["P"]) < MAP_TOL
+        n = int(res["n"][i])
+        rs = [(int(t["r"]), int(t["s"])) for t in res["tg"][i][:n]]
+        if p.detect_mode == o.DETECT_TOPK:
+            check_detections_vs_fp64(rs, res["tg"][i]["power"][:n], ref["det"], ref["P"])
+        P32 = res["map"][i]
+        eta = o.threshold(P32, ref["rows"], p.pfa, p.noise_var) if p.detect_mode == o.DETECT_THRESHOLD else None
+        det32 = o.detect(P32, p.detect_mode, p.max_targets, eta)
+        assert rs == list(zip(det32.r.tolist(), det32.s.tolist()))
+        assert np.array_equal(res["tg"][i]["power"][:n], det32.power.astype(np.float32))
+        assert int(res["status"][i]) == det32.status
