@@ -4,9 +4,7 @@
 // Doppler (Eq. (17)): the windowed DFT over the M OFDM symbols of every
 // support row of the range profile,
 //     D[r, s] = sum_{l < M} (w_l g[r, l]) e^{-2 pi i l s / M'},   P = |D|^2 / (N M),
-// as a complex matrix product on the CUDA cores: a CTA computes 32 rows x 64
-// Doppler bins, the symbols staged through shared memory 32 at a time with
-// the twiddles e^{-2 pi i (l s mod M') / M'} from a table of M' roots.
+// as a power-of-two-length DFT and an odd-length DFT (M' = P Q).
 //
 // Detection (Eq. (18)): 8-neighbour local maxima (circular), optionally above
 // the global threshold or the CFAR one, ordered by power then map index:
@@ -17,60 +15,64 @@
 
 namespace ofdm {
 
-constexpr int kGR = 32, kGS = 64, kGK = 32, kGThreads = 256;
+constexpr int kGThreads = 256;
 
+// Doppler (Eq. (17)) for M' = P Q with P the largest power of two dividing M'
+// and Q odd (Table I: 560 = 16 x 35), by two smaller DFTs (Good-Thomas is not
+// needed: the twiddles are applied between the stages):
+//   l = Q l1 + l2,  s = s1 + P s2,  w = e^{-2 pi i / M'}:
+//   A[s1][l2] = w^(l2 s1) sum_{l1 < P} x[Q l1 + l2] w^(Q l1 s1)          (P-point DFTs)
+//   D[s1 + P s2] = sum_{l2 < Q} A[s1][l2] w^(P l2 s2)                    (Q-point DFTs)
+// with x[l] = w_l g[r, l] for l < M and 0 up to M'.  M'(P + Q) complex
+// multiply-adds per row instead of M'^2 (28.6k instead of 313.6k for 560).
+// One CTA per (row, frame); the row and the intermediate A live in shared
+// memory; the roots w^m come from a table (all exponents reduced mod M').
 __global__ void __launch_bounds__(kGThreads)
-doppler_dft_kernel(const float2* __restrict__ strip, float* __restrict__ map, float* __restrict__ pow,
-                   DopplerArgs d, const float2* __restrict__ roots) {
-  __shared__ float2 Gs[kGK][kGR + 1];
-  __shared__ float2 Ws[kGK][kGS + 1];
-  const int f = blockIdx.z, r0 = blockIdx.y * kGR, s0 = blockIdx.x * kGS;
-  const int tid = threadIdx.x, tr = tid >> 4, ts = tid & 15;
+doppler_2factor_kernel(const float2* __restrict__ strip, float* __restrict__ map, float* __restrict__ pow,
+                       DopplerArgs d, const float2* __restrict__ roots, int P, int Q) {
+  extern __shared__ float2 dg_smem[];
+  float2* x = dg_smem;             // [M'] windowed row, zero-padded
+  float2* A = dg_smem + d.Mp;      // [P][Q] after the first stage
+  float2* w = A + d.Mp;            // [M'] roots
+  const int ri = blockIdx.x, f = blockIdx.y, tid = threadIdx.x;
   const int M = d.M, Mp = d.Mp;
-  const float2* g = strip + (size_t)f * d.rows * M;
-  float2 acc[2][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
-  for (int k0 = 0; k0 < M; k0 += kGK) {
-    __syncthreads();
-    for (int e = tid; e < kGR * kGK; e += kGThreads) {
-      const int rr = e / kGK, kk = e % kGK, r = r0 + rr, l = k0 + kk;
-      Gs[kk][rr] = (r < d.rows && l < M) ? cscale(g[(size_t)r * M + l], __ldg(d.wl + l)) : make_float2(0.f, 0.f);
-    }
-    for (int e = tid; e < kGK * kGS; e += kGThreads) {
-      const int kk = e / kGS, ss = e % kGS, l = k0 + kk, s = s0 + ss;
-      Ws[kk][ss] = (l < M && s < Mp) ? __ldg(roots + (int)(((long)l * s) % Mp)) : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-#pragma unroll 8
-    for (int kk = 0; kk < kGK; ++kk) {
-      const float2 a0 = Gs[kk][2 * tr], a1 = Gs[kk][2 * tr + 1];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const float2 w = Ws[kk][ts + 16 * j];
-        acc[0][j] = cadd(acc[0][j], cmul(a0, w));
-        acc[1][j] = cadd(acc[1][j], cmul(a1, w));
-      }
-    }
+  const float2* g = strip + ((size_t)f * d.rows + ri) * M;
+  for (int l = tid; l < Mp; l += kGThreads) {
+    x[l] = l < M ? cscale(g[l], __ldg(d.wl + l)) : make_float2(0.f, 0.f);
+    w[l] = __ldg(roots + l);
   }
-#pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const int ri = r0 + 2 * tr + i;
-    if (ri >= d.rows) continue;
-    const int row = (d.row0 + ri) % d.Np;
-    float* mrow = map ? map + (d.map_off ? (long)d.map_off[f] : (long)f * d.Np * Mp) + (long)row * Mp : nullptr;
-    float* prow = pow ? pow + ((size_t)f * d.rows + ri) * Mp : nullptr;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int s = s0 + ts + 16 * j;
-      if (s >= Mp) continue;
-      const float p = (acc[i][j].x * acc[i][j].x + acc[i][j].y * acc[i][j].y) * d.inv_nm;
-      const int c = (s + Mp / 2) % Mp;   // column of Doppler bin s (s >= M'/2 is negative)
-      if (mrow) mrow[c] = p;
-      if (prow) prow[c] = p;
+  __syncthreads();
+  for (int e = tid; e < Mp; e += kGThreads) {     // e = s1 Q + l2
+    const int s1 = e / Q, l2 = e % Q;
+    const int step = (int)(((long)Q * s1) % Mp);
+    float2 acc = make_float2(0.f, 0.f);
+    int m = 0;
+    for (int l1 = 0; l1 < P; ++l1) {
+      acc = cadd(acc, cmul(x[Q * l1 + l2], w[m]));
+      m += step;
+      if (m >= Mp) m -= Mp;
     }
+    A[e] = cmul(acc, w[(int)(((long)l2 * s1) % Mp)]);
+  }
+  __syncthreads();
+  const int row = (d.row0 + ri) % d.Np;
+  float* mrow = map ? map + (d.map_off ? (long)d.map_off[f] : (long)f * d.Np * Mp) + (long)row * Mp : nullptr;
+  float* prow = pow ? pow + ((size_t)f * d.rows + ri) * Mp : nullptr;
+  for (int e = tid; e < Mp; e += kGThreads) {     // e = s1 + P s2
+    const int s1 = e % P, s2 = e / P;
+    const int step = (int)(((long)P * s2) % Mp);
+    const float2* a = A + s1 * Q;
+    float2 acc = make_float2(0.f, 0.f);
+    int m = 0;
+    for (int l2 = 0; l2 < Q; ++l2) {
+      acc = cadd(acc, cmul(a[l2], w[m]));
+      m += step;
+      if (m >= Mp) m -= Mp;
+    }
+    const float p = (acc.x * acc.x + acc.y * acc.y) * d.inv_nm;
+    const int c = (e + Mp / 2) % Mp;   // column of Doppler bin e (e >= M'/2 is negative)
+    if (mrow) mrow[c] = p;
+    if (prow) prow[c] = p;
   }
 }
 
@@ -142,10 +144,13 @@ detect_general_block_kernel(const float* __restrict__ src, DetectArgs a, int blo
   }
   __syncthreads();
   if (tid == 0 && s_n) atomicAdd(counts + f, s_n);
-  // sort the block's candidates, keys descending (bitonic over the whole buffer)
-  for (int k = 2; k <= kGBlockCells; k <<= 1)
+  // sort the block's candidates, keys descending (bitonic over the filled
+  // prefix rounded up to a power of two; the rest of buf is zero)
+  int n = 32;
+  while (n < (int)s_n) n <<= 1;
+  for (int k = 2; k <= n; k <<= 1)
     for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = tid; i < kGBlockCells; i += kGThreads) {
+      for (int i = tid; i < n; i += kGThreads) {
         const int p2 = i ^ j;
         if (p2 > i) {
           const uint64_t x = buf[i], y = buf[p2];
@@ -260,9 +265,13 @@ __global__ void __launch_bounds__(1024) median_general_kernel(const float* __res
 
 cudaError_t launch_doppler_general(const float2* strip, float* map, float* pow, const DopplerArgs& a,
                                    const float2* roots, cudaStream_t s, int* launches) {
+  int P = 1;
+  while (a.Mp % (2 * P) == 0) P *= 2;
+  const int Q = a.Mp / P;
+  const size_t smem = (size_t)3 * a.Mp * sizeof(float2);
   ++*launches;
-  dim3 grid((unsigned)((a.Mp + kGS - 1) / kGS), (unsigned)((a.rows + kGR - 1) / kGR), (unsigned)a.frames);
-  doppler_dft_kernel<<<grid, kGThreads, 0, s>>>(strip, map, pow, a, roots);
+  doppler_2factor_kernel<<<dim3((unsigned)a.rows, (unsigned)a.frames), kGThreads, smem, s>>>(strip, map, pow, a, roots,
+                                                                                            P, Q);
   return cudaGetLastError();
 }
 

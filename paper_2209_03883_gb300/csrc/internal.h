@@ -4,9 +4,20 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/ofdm_radar.h"
 
 namespace ofdm {
+
+// Names the host-side span of an entry point for profilers (NVTX range;
+// free when no tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Arguments of the column kernel (steps a1-a5 on every OFDM symbol).
 struct ColumnArgs {
@@ -149,7 +160,7 @@ cudaError_t launch_range_pad(int N, int NP, const float2* taps, float2* strip, c
                              int* launches);
 
 // Doppler grid M' that is not a power of two (doppler_general.cu): the
-// windowed Doppler DFT as a complex matrix product (roots = e^{-2 pi i m / M'})
+// windowed Doppler DFT as a P-point then a Q-point DFT, M' = P Q (roots = e^{-2 pi i m / M'})
 // and detection by sorted block lists (a.part_keys holds detect_general_blocks
 // lists of 32 keys per frame).
 cudaError_t launch_doppler_general(const float2* strip, float* map, float* pow, const DopplerArgs& a,

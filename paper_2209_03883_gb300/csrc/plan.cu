@@ -20,7 +20,7 @@ constexpr int kHostChunks = 16;  // frame chunks of the host-buffer pipeline
 struct ofdm_radar_plan {
   ofdm_radar_params p;
   int Np, Mp;
-  int gen = 0;                 // M' not a power of two: matrix-product Doppler stage and general detection
+  int gen = 0;                 // M' not a power of two: two-factor Doppler DFT and general detection
   int rows, row0, full;        // DFT-CE support (Eqs. (17), (21))
   int z0, nz;                  // contiguous zero rows of the map
   int rinv;
@@ -253,6 +253,7 @@ void ofdm_radar_plan_destroy(ofdm_radar_plan* plan) {
 }
 
 int ofdm_radar_plan_create(const ofdm_radar_params* pin, ofdm_radar_plan** out) {
+  ofdm::NvtxRange nvtx_range("ofdm_radar_plan_create");
   if (!pin || !out) return OFDM_ERR_INVALID_ARG;
   *out = nullptr;
   const ofdm_radar_params& p = *pin;
@@ -350,7 +351,7 @@ int ofdm_radar_plan_create(const ofdm_radar_params* pin, ofdm_radar_plan** out) 
   std::vector<float2> twN, twM, twG;
   build_twiddles(twN, N, column_points_per_thread(N));
   if (N >= 1024) build_twiddles(twG, N, 16);   // column kernel in groups of N / 16 threads
-  if (!is_pow2(Mp)) {   // roots e^{-2 pi i m / M'} of the matrix-product Doppler stage
+  if (!is_pow2(Mp)) {   // roots e^{-2 pi i m / M'} of the two-factor Doppler DFT
     twM.resize(Mp);
     for (int m = 0; m < Mp; ++m) {
       const double a = -2.0 * M_PI * m / Mp;
@@ -691,6 +692,7 @@ extern "C" {
 int ofdm_radar_process(ofdm_radar_plan* pl, const ofdm_c32* Y, const ofdm_c32* X, int32_t frames,
                        float* out_map, ofdm_target* out_targets, int32_t* n_targets, uint32_t* status,
                        void* stream) {
+  ofdm::NvtxRange nvtx_range("ofdm_radar_process");
   if (!pl || !Y || !X || bad_frames(pl, frames) || tc_misaligned(pl, Y, X)) return OFDM_ERR_INVALID_ARG;
   int launches = 0;
   cudaError_t e = run_chain(pl, (const float2*)Y, (const float2*)X, frames, out_map, out_targets, n_targets,
@@ -700,6 +702,7 @@ int ofdm_radar_process(ofdm_radar_plan* pl, const ofdm_c32* Y, const ofdm_c32* X
 
 int ofdm_zc_precode(ofdm_radar_plan* pl, const ofdm_c32* in, ofdm_c32* out, int32_t frames, int32_t inverse,
                     void* stream) {
+  ofdm::NvtxRange nvtx_range("ofdm_zc_precode");
   if (!pl || !in || !out || in == out || bad_frames(pl, frames)) return OFDM_ERR_INVALID_ARG;
   if (pl->p.zc_root <= 0) return OFDM_ERR_INVALID_ARG;
   ZctArgs a;
@@ -722,6 +725,7 @@ int ofdm_zc_precode(ofdm_radar_plan* pl, const ofdm_c32* in, ofdm_c32* out, int3
 
 int ofdm_radar_range_profile(ofdm_radar_plan* pl, const ofdm_c32* Y, const ofdm_c32* X, int32_t frames,
                              ofdm_c32* strip, void* stream) {
+  ofdm::NvtxRange nvtx_range("ofdm_radar_range_profile");
   if (!pl || !Y || !X || !strip || bad_frames(pl, frames) || tc_misaligned(pl, Y, X) ||
       tc_misaligned(pl, strip, strip))
     return OFDM_ERR_INVALID_ARG;
@@ -736,6 +740,7 @@ int ofdm_radar_range_profile(ofdm_radar_plan* pl, const ofdm_c32* Y, const ofdm_
 
 int ofdm_radar_doppler(ofdm_radar_plan* pl, const ofdm_c32* strip, int32_t frames, float* out_map,
                        void* stream) {
+  ofdm::NvtxRange nvtx_range("ofdm_radar_doppler");
   if (!pl || !strip || !out_map || bad_frames(pl, frames)) return OFDM_ERR_INVALID_ARG;
   int launches = 0;
   cudaError_t e = ofdm::launch_zero_rows(out_map, frames, pl->Np, pl->Mp, pl->z0, pl->nz, (cudaStream_t)stream,
@@ -751,6 +756,7 @@ int ofdm_radar_doppler(ofdm_radar_plan* pl, const ofdm_c32* strip, int32_t frame
 
 int ofdm_radar_detect(ofdm_radar_plan* pl, const float* map, int32_t frames, ofdm_target* out_targets,
                       int32_t* n_targets, uint32_t* status, void* stream) {
+  ofdm::NvtxRange nvtx_range("ofdm_radar_detect");
   if (!pl || !map || bad_frames(pl, frames)) return OFDM_ERR_INVALID_ARG;
   int launches = 0;
   cudaError_t e = pl->gen ? ofdm::launch_detect_general(map, out_targets, n_targets, status, nullptr,
@@ -762,6 +768,7 @@ int ofdm_radar_detect(ofdm_radar_plan* pl, const float* map, int32_t frames, ofd
 
 int ofdm_radar_process_host(ofdm_radar_plan* pl, const ofdm_c32* Yh, const ofdm_c32* Xh, int32_t frames,
                             float* map_h, ofdm_target* tg_h, int32_t* nt_h, uint32_t* st_h, void* stream) {
+  ofdm::NvtxRange nvtx_range("ofdm_radar_process_host");
   if (!pl || !Yh || !Xh || bad_frames(pl, frames)) return OFDM_ERR_INVALID_ARG;
   const ofdm_radar_params& p = pl->p;
   const size_t grid = (size_t)p.N * p.M, mapn = (size_t)pl->Np * pl->Mp;
@@ -851,6 +858,7 @@ void ofdm_fps_default_params(ofdm_fps_params* fp) {
 int ofdm_fps_sft(ofdm_radar_plan* pl, const ofdm_c32* Y, const ofdm_c32* X, int32_t frames,
                  const ofdm_fps_params* fp, const int32_t* slices, ofdm_target* out_targets,
                  int32_t* n_targets, void* stream) {
+  ofdm::NvtxRange nvtx_range("ofdm_fps_sft");
   if (!pl || !Y || !X || !fp || !slices || bad_frames(pl, frames) || tc_misaligned(pl, Y, X))
     return OFDM_ERR_INVALID_ARG;
   const ofdm_radar_params& p = pl->p;
@@ -919,6 +927,7 @@ int ofdm_fps_sft(ofdm_radar_plan* pl, const ofdm_c32* Y, const ofdm_c32* X, int3
 
 int ofdm_tx_amplifier(ofdm_radar_plan* pl, const ofdm_c32* S, int32_t frames, int32_t oversample, float q,
                       float* papr, float* aci, void* stream) {
+  ofdm::NvtxRange nvtx_range("ofdm_tx_amplifier");
   if (!pl || !S || bad_frames(pl, frames) || !(q > -100.f && q < 100.f)) return OFDM_ERR_INVALID_ARG;
   const int N = pl->p.N, LN = N * oversample;
   if (oversample < 1 || oversample > 8 || (oversample & (oversample - 1)) || LN > 4096)
@@ -1168,6 +1177,7 @@ int ofdm_radar_batch_used_graph(const ofdm_radar_batch* b) { return b ? (b->used
 
 int ofdm_radar_batch_process(ofdm_radar_batch* b, const ofdm_c32* Yc, const ofdm_c32* Xc, float* map,
                              ofdm_target* tg, int32_t* nt, uint32_t* st, void* stream) {
+  ofdm::NvtxRange nvtx_range("ofdm_radar_batch_process");
   if (!b || !Yc || !Xc) return OFDM_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   const float2* Y = (const float2*)Yc;
@@ -1285,6 +1295,7 @@ int ofdm_radar_coarse_shape(const ofdm_radar_plan* pl, int32_t* h, int32_t* w) {
 
 int ofdm_radar_coarse_map(ofdm_radar_plan* pl, const ofdm_c32* Y, const ofdm_c32* X, int32_t frames, float* x_out,
                           void* stream) {
+  ofdm::NvtxRange nvtx_range("ofdm_radar_coarse_map");
   if (!pl || !Y || !X || !pl->d_cpow || bad_frames(pl, frames) || tc_misaligned(pl, Y, X)) return OFDM_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   int launches = 0;
@@ -1303,6 +1314,7 @@ int ofdm_radar_coarse_map(ofdm_radar_plan* pl, const ofdm_c32* Y, const ofdm_c32
 int ofdm_radar_process_learned(ofdm_radar_plan* pl, const float* theta, const ofdm_c32* Y, const ofdm_c32* X,
                                int32_t frames, float zthr, int32_t cap, ofdm_target* out, int32_t* nt,
                                uint32_t* st, void* stream) {
+  ofdm::NvtxRange nvtx_range("ofdm_radar_process_learned");
   if (!pl || !theta || !Y || !X || !pl->d_cpow || bad_frames(pl, frames) || cap < 1 || cap > 256 ||
       tc_misaligned(pl, Y, X))
     return OFDM_ERR_INVALID_ARG;

@@ -482,7 +482,7 @@ GENERAL_M = [
 @pytest.mark.parametrize("name,kw", GENERAL_M, ids=[c[0] for c in GENERAL_M])
 def test_doppler_grid_not_a_power_of_two(env, name, kw):
     """M' = 560 = 2^4 5 7 (Table I) and other non-power-of-two Doppler grids:
-    the matrix-product Doppler stage and the general detection against the
+    the two-factor Doppler DFT and the general detection against the
     oracle (map, bins; the detection itself exactly on the GPU's own map)."""
     base = syn.FrameConfig(N=kw["N"], M=kw["M"], L_cp=kw["L_cp"], qam=16, zc_root=1, n_targets=kw["targets"],
                            on_grid=False, amp_db=(-6.0, 0.0), snr_db=(0.0, 0.0), window=kw["window"], detect_k=4)
