@@ -371,17 +371,24 @@ struct GroupPipeCfg {
   static constexpr int T = TT;
   static constexpr int E = N / T;
   static constexpr int BUF = smem_elems(N);
-  static constexpr int FIT = (int)((227u * 1024u) / (3u * BUF * sizeof(float2)));  // 4 for 2048, 2 for 4096
+  // Row buffers per group.  Three (A, Y, next A) give every copy a whole
+  // symbol of lead.  With 16 points per thread and N >= 2048 two buffers are
+  // used instead (next A lands in the Y slot after the division, next Y in
+  // the A slot after the stencil: half a symbol of lead, several
+  // microseconds), so that the tables fit in shared memory beside them.
+  static constexpr int RING = (E < 32 && N >= 2048) ? 2 : 3;
+  static constexpr int FIT = (int)((227u * 1024u) / (RING * BUF * sizeof(float2)));
   static constexpr int GROUPS = (E < 32 && FIT > 512 / T) ? 512 / T : FIT;
   static constexpr int THREADS = T * GROUPS;
   // 16 points per thread: the pre-chirp and the pass twiddles live in shared
-  // memory behind the rings (18 KB for N = 1024)
-  static constexpr size_t RING_BYTES = (size_t)GROUPS * 3 * BUF * sizeof(float2);
+  // memory behind the rings (18 KB for N = 1024, 34 KB for 2048, 68 KB for 4096)
+  static constexpr size_t RING_BYTES = (size_t)GROUPS * RING * BUF * sizeof(float2);
   static constexpr bool SMEM_TABLES =
       E < 32 && RING_BYTES + (size_t)(N + tw_size(N, E)) * sizeof(float2) + 4096 <= 227u * 1024u;
   static constexpr int TABLE_ELEMS = SMEM_TABLES ? N + tw_size(N, E) : 0;
-  static constexpr size_t SMEM = (size_t)GROUPS * 3 * BUF * sizeof(float2) + (size_t)TABLE_ELEMS * sizeof(float2);
+  static constexpr size_t SMEM = RING_BYTES + (size_t)TABLE_ELEMS * sizeof(float2);
   static_assert(GROUPS >= 1 && GROUPS <= 15, "named barriers 1..15");
+  static_assert(SMEM <= 227u * 1024u, "shared memory");
   static_assert(T % 32 == 0, "whole warps");
 };
 
@@ -401,14 +408,14 @@ column_group_pipe_kernel(const float2* __restrict__ Y, const float2* __restrict_
   const float2* pre = a.pre;
   const float2* tw = a.tw;
   if constexpr (C::SMEM_TABLES) {
-    float2* tab = smem + (size_t)C::GROUPS * 3 * C::BUF;
+    float2* tab = smem + (size_t)C::GROUPS * C::RING * C::BUF;
     for (int i = threadIdx.x; i < N; i += C::THREADS) tab[i] = __ldg(a.pre + i);
     for (int i = threadIdx.x; i < tw_size(N, E); i += C::THREADS) tab[N + i] = __ldg(a.tw + i);
     pre = tab;
     tw = tab + N;
   }
   __syncthreads();
-  float2* ring = smem + (size_t)group * 3 * C::BUF;
+  float2* ring = smem + (size_t)group * C::RING * C::BUF;
   const long total = (long)a.frames * a.M;
   const uint64_t pol = evict_first_policy();
 
@@ -433,6 +440,9 @@ column_group_pipe_kernel(const float2* __restrict__ Y, const float2* __restrict_
     if (!a.frame_off) return sm * N;
     return (long)a.frame_off[sm / a.M] + (sm % a.M) * N;
   };
+  // Commit groups in flight at the top of a symbol, oldest first: A(sym),
+  // Y(sym) with two buffers; A(sym), Y(sym), A(next) with three.
+  constexpr int R2 = C::RING == 2 ? 1 : 0;
   int ia = 0, iy = 1, ifree = 2;
   long sym = ticket();
   if (sym < total) issue_row(X + row_off(sym), ring + ia * C::BUF);
@@ -441,8 +451,10 @@ column_group_pipe_kernel(const float2* __restrict__ Y, const float2* __restrict_
   cp_async_commit();
   long nxt = sym < total ? ticket() : total;
   for (; sym < total; sym = nxt, nxt = (nxt < total ? ticket() : total)) {
-    if (nxt < total) issue_row(X + row_off(nxt), ring + ifree * C::BUF);
-    cp_async_commit();
+    if constexpr (!R2) {
+      if (nxt < total) issue_row(X + row_off(nxt), ring + ifree * C::BUF);
+      cp_async_commit();
+    }
     const int f = (int)(sym / a.M);
     const int l = (int)(sym % a.M);
     float2* sa = ring + ia * C::BUF;        // A row, then the FFT exchange buffer
@@ -450,7 +462,7 @@ column_group_pipe_kernel(const float2* __restrict__ Y, const float2* __restrict_
     float2 v[E];
     uint32_t flags = 0;
     if (a.zc) {
-      cp_async_wait<2>();                   // A(sym) has landed (this thread's copies) ...
+      cp_async_wait<2 - R2>();              // A(sym) has landed (this thread's copies) ...
       group_sync<T>(group);                 // ... and every thread's
 #pragma unroll
       for (int q = 0; q < E; ++q) {
@@ -462,16 +474,16 @@ column_group_pipe_kernel(const float2* __restrict__ Y, const float2* __restrict_
       if (a.refine_tau > 0.f)
         flags |= refine_small_cells_group<N, T, E>(v, X + row_off(sym), a, t, lane, group, &s_rcnt[group],
                                                    s_rlist[group], s_rpart[group]);
-      cp_async_wait<1>();                   // Y(sym)
+      cp_async_wait<1 - R2>();              // Y(sym)
       group_sync<T>(group);
       flags |= divide_precoded<T, E>(v, sy, true, a, t);
     } else {
-      cp_async_wait<1>();                   // A(sym) and Y(sym)
+      cp_async_wait<1 - R2>();              // A(sym) and Y(sym)
       group_sync<T>(group);
       flags |= divide_plain<T, E>(v, sa, sy, true, t);
     }
     group_sync<T>(group);                   // every thread is done with the Y row
-    if (nxt < total) issue_row(Y + row_off(nxt), ring + iy * C::BUF);
+    if (nxt < total) issue_row((R2 ? X : Y) + row_off(nxt), ring + iy * C::BUF);   // next A (two) or Y (three)
     cp_async_commit();
     // DFT-CE keeps taps n = t + T q < L_cp only: for N = 1024 in two-warp
     // groups and L_cp <= 128 that is q < 2, so the last pass is pruned.
@@ -487,9 +499,17 @@ column_group_pipe_kernel(const float2* __restrict__ Y, const float2* __restrict_
     flags = __reduce_or_sync(0xffffffffu, flags);
     if (lane == 0 && flags) atomicOr(wstatus + f, flags);
     group_sync<T>(group);                   // every thread is done with sa before it is refilled
-    const int tmp = ia;
-    ia = ifree;
-    ifree = tmp;
+    if constexpr (R2) {
+      if (nxt < total) issue_row(Y + row_off(nxt), ring + ia * C::BUF);   // next Y into the A slot
+      cp_async_commit();
+      const int tmp = ia;                   // next symbol: A in the old Y slot, Y in the old A slot
+      ia = iy;
+      iy = tmp;
+    } else {
+      const int tmp = ia;
+      ia = ifree;
+      ifree = tmp;
+    }
   }
   cp_async_wait<0>();
 }
