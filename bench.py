@@ -276,6 +276,9 @@ def extra_batched(radar, torch, dev, stream, steps, n_frames=512):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
+    tv = radar.targets_view(tg.cpu().numpy(), n_frames, K)
+    nt_b = nt.cpu().numpy()
+    b_bins = [[(int(t["r"]), int(t["s"])) for t in tv[f][:int(nt_b[f])]] for f in range(n_frames)]
     peak, _ = load_peaks()
     byts = 20.0 * yx
     out = {"workload": "512 uneven frames (N 256-2048, M 64-256, L_cp N/8), one CUDA graph per step",
@@ -283,6 +286,42 @@ def extra_batched(radar, torch, dev, stream, steps, n_frames=512):
            "hbm_frac": byts / (ms / 1e3) / 1e9 / peak, "graph": b.used_graph(),
            "groups": [list(g) for g in b.groups()]}
     b.close()
+    # The same frames through the plain form: one plan per shape, the frames of
+    # each shape contiguous, one ofdm_radar_process call per shape per step.
+    by_shape = {}
+    for f, sh in enumerate(shapes):
+        by_shape.setdefault(sh, []).append(f)
+    plain = []
+    for (N, M, L), fl in by_shape.items():
+        pl = radar.Plan(N=N, M=M, L_cp=L, window=1, zc_root=1, max_targets=K, max_frames=len(fl))
+        Yg = torch.stack([Y[descs[f][3]:descs[f][3] + N * M] for f in fl]).view(len(fl), M, N).contiguous()
+        Xg = torch.stack([X[descs[f][3]:descs[f][3] + N * M] for f in fl]).view(len(fl), M, N).contiguous()
+        plain.append((pl, fl, Yg, Xg, radar.alloc_outputs(pl, len(fl), dev)))
+
+    def plain_step():
+        for pl, fl, Yg, Xg, o in plain:
+            radar.ofdm_radar_process(pl, Yg, Xg, len(fl), o["map"], o["targets"], o["n_targets"], o["status"],
+                                     stream)
+
+    for _ in range(3):
+        plain_step()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        plain_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    pms = e0.elapsed_time(e1) / steps
+    same = 0
+    for pl, fl, Yg, Xg, o in plain:
+        tvp = radar.targets_view(o["targets"].cpu().numpy(), len(fl), K)
+        ntp = o["n_targets"].cpu().numpy()
+        for i, f in enumerate(fl):
+            same += [(int(t["r"]), int(t["s"])) for t in tvp[i][:int(ntp[i])]] == b_bins[f]
+        pl.close()
+    out["plain_per_shape"] = {"value": n_frames / (pms / 1e3), "unit": "frames/s", "ms_per_step": pms,
+                              "calls_per_step": len(plain), "frames_with_same_targets": f"{same}/{n_frames}"}
+    out["gain_over_plain"] = pms / ms
     return out
 
 
