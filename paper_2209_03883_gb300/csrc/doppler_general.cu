@@ -4,12 +4,13 @@
 // Doppler (Eq. (17)): the windowed DFT over the M OFDM symbols of every
 // support row of the range profile,
 //     D[r, s] = sum_{l < M} (w_l g[r, l]) e^{-2 pi i l s / M'},   P = |D|^2 / (N M),
-// as a power-of-two-length DFT and an odd-length DFT (M' = P Q).
+// by a mixed-radix FFT when M' = 2^a 3^b 5^c 7^d, else as a power-of-two-length
+// DFT and an odd-length DFT (M' = P Q).
 //
 // Detection (Eq. (18)): 8-neighbour local maxima (circular), optionally above
 // the global threshold or the CFAR one, ordered by power then map index:
-// each CTA sorts the candidates of its block of cells and keeps its best K;
-// one CTA per frame merges the block lists.
+// each CTA takes a band of support rows and keeps its best K; one CTA per
+// frame merges the band lists.
 #include "fft.cuh"
 #include "internal.h"
 
@@ -76,9 +77,135 @@ doppler_2factor_kernel(const float2* __restrict__ strip, float* __restrict__ map
   }
 }
 
+// ---------------------------------------------------------------- mixed radix
+// M' = 2^a 3^b 5^c 7^d (Table I: 560 = 7 x 5 x 16): a Stockham auto-sort
+// transform, natural order in and out, with passes of radix 7, 5, 3 and then
+// 16, 8, 4, 2.  Pass p (radix R, Ns = product of the earlier radices) takes
+// butterfly j < M'/R with k = j mod Ns:
+//   a[m] = x[j + m M'/R] w^(m k M'/(Ns R)),  a <- DFT_R(a),
+//   y[(j / Ns) Ns R + k + m Ns] = a[m],      w = e^{-2 pi i / M'}.
+// One warp per (support row, frame) with two shared-memory row buffers; the
+// CTA shares the table of the M' roots.  At M' = 560 this is about 35 real
+// operations per point against 4 (P + Q) = 204 for the two-factor form, and
+// the operands of the small DFTs stay in registers.
+constexpr int kMixWarps = 4;
+
+template <int R, int K>
+struct Trig {
+  static constexpr float c = (float)cx_cos(2.0 * kPi * K / R);
+  static constexpr float s = (float)cx_sin(2.0 * kPi * K / R);
+};
+
+// Odd R, X[b] = sum_a v[a] e^{DIR 2 pi i a b / R}: with s_a = v_a + v_{R-a} and
+// d_a = v_a - v_{R-a} (a = 1 .. (R-1)/2), X[b] = A_b + DIR i C_b and
+// X[R-b] = A_b - DIR i C_b, where A_b = v_0 + sum_a s_a cos(2 pi a b / R) and
+// C_b = sum_a d_a sin(2 pi a b / R).
+template <int R, int DIR, int B, int... As>
+__device__ __forceinline__ void odd_pair(const float2* s, const float2* d, float2 v0, float2* X,
+                                         std::integer_sequence<int, As...>) {
+  float2 A = v0, C = make_float2(0.f, 0.f);
+  ((A.x = __fmaf_rn(Trig<R, ((As + 1) * B) % R>::c, s[As].x, A.x),
+    A.y = __fmaf_rn(Trig<R, ((As + 1) * B) % R>::c, s[As].y, A.y),
+    C.x = __fmaf_rn(Trig<R, ((As + 1) * B) % R>::s, d[As].x, C.x),
+    C.y = __fmaf_rn(Trig<R, ((As + 1) * B) % R>::s, d[As].y, C.y)),
+   ...);
+  X[B] = make_float2(A.x - DIR * C.y, A.y + DIR * C.x);
+  X[R - B] = make_float2(A.x + DIR * C.y, A.y - DIR * C.x);
+}
+template <int R, int DIR, int... Bs>
+__device__ __forceinline__ void odd_all(const float2* s, const float2* d, float2 v0, float2* X,
+                                        std::integer_sequence<int, Bs...>) {
+  (odd_pair<R, DIR, Bs + 1>(s, d, v0, X, std::make_integer_sequence<int, (R - 1) / 2>{}), ...);
+}
+template <int R, int DIR>
+__device__ __forceinline__ void dft_odd(float2* v) {
+  constexpr int H = (R - 1) / 2;
+  float2 s[H], d[H], X[R];
+  float2 x0 = v[0];
+#pragma unroll
+  for (int a = 0; a < H; ++a) {
+    s[a] = cadd(v[a + 1], v[R - 1 - a]);
+    d[a] = csub(v[a + 1], v[R - 1 - a]);
+    x0 = cadd(x0, s[a]);
+  }
+  odd_all<R, DIR>(s, d, v[0], X, std::make_integer_sequence<int, H>{});
+  X[0] = x0;
+#pragma unroll
+  for (int b = 0; b < R; ++b) v[b] = X[b];
+}
+
+template <int R>
+__device__ __forceinline__ void mixed_pass(const float2* __restrict__ x, float2* __restrict__ y, int L, int Ns,
+                                           const float2* __restrict__ roots, int lane) {
+  const int nb = L / R, step = L / (Ns * R);
+  for (int j = lane; j < nb; j += 32) {
+    const int k = j % Ns;
+    float2 a[R];
+#pragma unroll
+    for (int m = 0; m < R; ++m) a[m] = x[j + m * nb];
+    if (Ns > 1) {
+      const int e = k * step;
+#pragma unroll
+      for (int m = 1; m < R; ++m) a[m] = cmul(a[m], roots[m * e]);
+    }
+    if constexpr (R == 3 || R == 5 || R == 7) dft_odd<R, -1>(a);
+    else dft_reg<R, -1>(a);
+    const int o = j + (j / Ns) * Ns * (R - 1);
+#pragma unroll
+    for (int m = 0; m < R; ++m) y[o + m * Ns] = a[m];
+  }
+}
+
+__global__ void __launch_bounds__(32 * kMixWarps)
+doppler_mixed_kernel(const float2* __restrict__ strip, float* __restrict__ map, float* __restrict__ pow,
+                     DopplerArgs d, const float2* __restrict__ roots, MixedSchedule sch) {
+  extern __shared__ float2 mx_smem[];
+  const int Mp = d.Mp, M = d.M;
+  float2* w = mx_smem;                                            // [M'] roots
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float2* b0 = mx_smem + Mp + (size_t)warp * 2 * Mp;
+  float2* b1 = b0 + Mp;
+  for (int i = threadIdx.x; i < Mp; i += 32 * kMixWarps) w[i] = __ldg(roots + i);
+  __syncthreads();
+  const int f = blockIdx.y;
+  const int ri = blockIdx.x * kMixWarps + warp;
+  if (ri >= d.rows) return;                                       // no CTA-wide barrier below
+  const float2* g = strip + ((size_t)f * d.rows + ri) * M;
+  for (int l = lane; l < Mp; l += 32) b0[l] = l < M ? cscale(g[l], __ldg(d.wl + l)) : make_float2(0.f, 0.f);
+  __syncwarp();
+  float2* x = b0;
+  float2* y = b1;
+  int Ns = 1;
+  for (int p = 0; p < sch.n; ++p) {
+    const int R = sch.r[p];
+    switch (R) {
+      case 2: mixed_pass<2>(x, y, Mp, Ns, w, lane); break;
+      case 3: mixed_pass<3>(x, y, Mp, Ns, w, lane); break;
+      case 4: mixed_pass<4>(x, y, Mp, Ns, w, lane); break;
+      case 5: mixed_pass<5>(x, y, Mp, Ns, w, lane); break;
+      case 7: mixed_pass<7>(x, y, Mp, Ns, w, lane); break;
+      case 8: mixed_pass<8>(x, y, Mp, Ns, w, lane); break;
+      default: mixed_pass<16>(x, y, Mp, Ns, w, lane); break;
+    }
+    __syncwarp();
+    Ns *= R;
+    float2* t = x;
+    x = y;
+    y = t;
+  }
+  const int row = (d.row0 + ri) % d.Np;
+  float* mrow = map ? map + (d.map_off ? (long)d.map_off[f] : (long)f * d.Np * Mp) + (long)row * Mp : nullptr;
+  float* prow = pow ? pow + ((size_t)f * d.rows + ri) * Mp : nullptr;
+  const int half = Mp / 2;
+  for (int c = lane; c < Mp; c += 32) {                           // column c holds bin c - M'/2 (mod M')
+    const float2 v = x[c < half ? c + half : c - half];
+    const float pw = (v.x * v.x + v.y * v.y) * d.inv_nm;
+    if (mrow) __stcs(mrow + c, pw);
+    if (prow) prow[c] = pw;
+  }
+}
+
 // ---------------------------------------------------------------- detection
-constexpr int kGCells = 8;                      // cells per thread
-constexpr int kGBlockCells = kGThreads * kGCells;
 
 __device__ __forceinline__ float gval(const float* base, const DetectArgs& a, int rj, int c) {
   return base[(long)(a.compact ? rj : (a.row0 + rj) % a.Np) * a.Mp + c];
@@ -102,66 +229,114 @@ __device__ bool gcfar(const float* base, const DetectArgs& a, int ri, int c, flo
   return n > 0 && p >= a.cfar_alpha[n] * (sum / (float)n);
 }
 
-// Block b of a frame's support cells: candidates, sorted, best K to keys[f][b][0..K).
+// A band of support rows per CTA (kGBandCells cells, at least one row): the
+// rows and a halo row on each side are staged in shared memory (rows off a
+// partial support are zero, a full support wraps), every cell is tested
+// against its 8 neighbours (circular in s), the candidates go to a shared
+// list, and K rounds of a block-wide maximum write the band's best K keys,
+// descending, to keys[f][band][0..32).
+constexpr int kGBandCells = 4096;
+constexpr int kGListCap = kGBandCells / 4 + 64;   // strict local maxima are never 8-adjacent
+
+int detect_general_band_rows(int Mp) { return Mp >= kGBandCells ? 1 : kGBandCells / Mp; }
+
+// A neighbour with the same power and a smaller map index wins the tie (G).
+__device__ __noinline__ bool gtie_lost(const float* row, int Mp, int Np, uint32_t r, int c, float p) {
+  const uint32_t idx = r * (uint32_t)Mp + (uint32_t)c;
+  for (int dr = -1; dr <= 1; ++dr)
+    for (int dc = -1; dc <= 1; ++dc) {
+      if (dr == 0 && dc == 0) continue;
+      const int cn = c + dc < 0 ? Mp - 1 : (c + dc >= Mp ? 0 : c + dc);
+      if (row[dr * Mp + cn] == p) {
+        const uint32_t rn = (uint32_t)(((int)r + dr + Np) % Np);
+        if (rn * (uint32_t)Mp + (uint32_t)cn < idx) return true;
+      }
+    }
+  return false;
+}
+
 __global__ void __launch_bounds__(kGThreads)
-detect_general_block_kernel(const float* __restrict__ src, DetectArgs a, int blocks, unsigned* __restrict__ counts) {
-  __shared__ uint64_t buf[kGBlockCells];
+detect_general_band_kernel(const float* __restrict__ src, DetectArgs a, int blocks, int band_rows,
+                           unsigned* __restrict__ counts) {
+  extern __shared__ __align__(16) float gtile[];   // (band_rows + 2) rows of M'
+  __shared__ uint64_t s_list[kGListCap];
+  __shared__ uint64_t s_wmax[kGThreads / 32];
   __shared__ unsigned s_n;
-  const int b = blockIdx.x, f = blockIdx.y, tid = threadIdx.x;
-  const float* base = src + (long)f * a.frame_stride;
+  const int b = blockIdx.x, f = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int Mp = a.Mp;
-  const long cells = (long)a.rows * Mp;
+  const int t0 = b * band_rows;
+  const int tr = min(band_rows, a.rows - t0);
+  const float* base = src + (long)f * a.frame_stride;
   const bool thr = a.mode == OFDM_DETECT_THRESHOLD, cfar = a.mode == OFDM_DETECT_CFAR;
   const float eta = thr ? (a.use_fixed_eta ? a.eta_fixed : a.eta[f]) : 0.f;
   if (tid == 0) s_n = 0;
-  for (int i = tid; i < kGBlockCells; i += kGThreads) buf[i] = 0ull;
-  __syncthreads();
-  for (int k = 0; k < kGCells; ++k) {
-    const long e = (long)b * kGBlockCells + (long)k * kGThreads + tid;
-    if (e >= cells) break;
-    const int ri = (int)(e / Mp), c = (int)(e % Mp);
-    const int r = (a.row0 + ri) % a.Np;
-    const float p = gval(base, a, ri, c);
-    if (!(p > 0.f) || (thr && !(p >= eta))) continue;
-    const uint32_t idx = (uint32_t)r * (uint32_t)Mp + (uint32_t)c;
-    bool lm = true;
-    for (int dr = -1; dr <= 1 && lm; ++dr) {
-      int rj = ri + dr;
-      float q;
-      int rn = (r + dr + a.Np) % a.Np;
-      if (a.full) { rj = (rj + a.rows) % a.rows; }
-      for (int dc = -1; dc <= 1; ++dc) {
-        if (dr == 0 && dc == 0) continue;
-        const int cn = (c + dc + Mp) % Mp;
-        q = (rj >= 0 && rj < a.rows) ? gval(base, a, rj, cn) : 0.f;   // rows off the support are zero
-        const uint32_t nidx = (uint32_t)rn * (uint32_t)Mp + (uint32_t)cn;
-        if (q > p || (q == p && nidx < idx)) { lm = false; break; }
-      }
+  const int q4 = Mp >> 2;                            // float4 per row (M' % 4 == 0)
+  for (int v = tid; v < (tr + 2) * q4; v += kGThreads) {
+    const int i = v / q4, c4 = v - i * q4;
+    int rj = t0 - 1 + i;
+    if (a.full) rj = (rj + a.rows) % a.rows;
+    float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (rj >= 0 && rj < a.rows) {
+      const int row = a.compact ? rj : (a.row0 + rj) % a.Np;
+      x = __ldg(reinterpret_cast<const float4*>(base + (long)row * Mp) + c4);
     }
-    if (!lm || (cfar && !gcfar(base, a, ri, c, p))) continue;
-    const unsigned slot = atomicAdd(&s_n, 1u);
-    buf[slot] = ((uint64_t)__float_as_uint(p) << 32) | (uint64_t)(~idx);
+    reinterpret_cast<float4*>(gtile)[v] = x;
   }
   __syncthreads();
-  if (tid == 0 && s_n) atomicAdd(counts + f, s_n);
-  // sort the block's candidates, keys descending (bitonic over the filled
-  // prefix rounded up to a power of two; the rest of buf is zero)
-  int n = 32;
-  while (n < (int)s_n) n <<= 1;
-  for (int k = 2; k <= n; k <<= 1)
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = tid; i < n; i += kGThreads) {
-        const int p2 = i ^ j;
-        if (p2 > i) {
-          const uint64_t x = buf[i], y = buf[p2];
-          const bool desc = (i & k) == 0;
-          if (desc ? (x < y) : (x > y)) { buf[i] = y; buf[p2] = x; }
-        }
+  unsigned cnt = 0;
+  int i = tid / Mp, c = tid - (tid / Mp) * Mp;
+  const int di = kGThreads / Mp, dcol = kGThreads % Mp;
+  for (int e = tid; e < tr * Mp; e += kGThreads) {
+    const float* row = gtile + (i + 1) * Mp;
+    const float p = row[c];
+    bool cand = p > 0.f && (!thr || p >= eta);
+    if (cand) {
+      const int cm = c == 0 ? Mp - 1 : c - 1, cp = c == Mp - 1 ? 0 : c + 1;
+      const float* up = row - Mp;
+      const float* dn = row + Mp;
+      // fmaxf skips NaN, so this is "no neighbour compares greater"
+      const float nmax = fmaxf(fmaxf(fmaxf(up[cm], up[c]), fmaxf(up[cp], row[cm])),
+                               fmaxf(fmaxf(row[cp], dn[cm]), fmaxf(dn[c], dn[cp])));
+      cand = !(nmax > p);
+      const uint32_t r = (uint32_t)((a.row0 + t0 + i) % a.Np);
+      if (cand && nmax == p) cand = !gtie_lost(row, Mp, a.Np, r, c, p);
+      if (cand && cfar) cand = gcfar(base, a, t0 + i, c, p);
+      if (cand) {
+        ++cnt;
+        const uint32_t idx = r * (uint32_t)Mp + (uint32_t)c;
+        const unsigned pos = atomicAdd(&s_n, 1u);
+        if (pos < (unsigned)kGListCap) s_list[pos] = ((uint64_t)__float_as_uint(p) << 32) | (uint64_t)(~idx);
       }
-      __syncthreads();
     }
+    i += di;
+    c += dcol;
+    if (c >= Mp) { c -= Mp; ++i; }
+  }
+  cnt = __reduce_add_sync(0xffffffffu, cnt);
+  if (lane == 0 && cnt) atomicAdd(counts + f, cnt);
+  __syncthreads();
+  const int n = min((int)s_n, kGListCap);
   uint64_t* out = a.part_keys + ((size_t)f * blocks + b) * 32;
-  if (tid < 32) out[tid] = tid < a.K ? buf[tid] : 0ull;
+  for (int k = 0; k < a.K; ++k) {                   // the band's K best, descending
+    uint64_t m = 0;
+    for (int j = tid; j < n; j += kGThreads) m = s_list[j] > m ? s_list[j] : m;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      const uint64_t u = __shfl_xor_sync(0xffffffffu, m, o);
+      m = u > m ? u : m;
+    }
+    if (lane == 0) s_wmax[warp] = m;
+    __syncthreads();
+    m = s_wmax[0];
+#pragma unroll
+    for (int w = 1; w < kGThreads / 32; ++w) m = s_wmax[w] > m ? s_wmax[w] : m;
+    if (m != 0)
+      for (int j = tid; j < n; j += kGThreads)
+        if (s_list[j] == m) s_list[j] = 0;           // keys are unique (the map index)
+    if (tid == 0) out[k] = m;
+    __syncthreads();
+  }
+  for (int k = a.K + tid; k < 32; k += kGThreads) out[k] = 0ull;
 }
 
 // One CTA per frame: the K largest keys of the block lists (each sorted
@@ -263,8 +438,35 @@ __global__ void __launch_bounds__(1024) median_general_kernel(const float* __res
   if (tid == 0) a.eta[f] = __fmul_rn(__uint_as_float(s_prefix), a.eta_factor);
 }
 
+// Radices of the mixed-radix transform (7, 5, 3 first, then 16, 8, 4, 2), or
+// n = 0 when M' has a prime factor above 7.
+MixedSchedule mixed_schedule(int Mp) {
+  MixedSchedule m{};
+  int q = Mp;
+  for (int p : {7, 5, 3})
+    while (q % p == 0 && m.n < kMixedMaxPasses) { m.r[m.n++] = (int8_t)p; q /= p; }
+  while (q > 1 && m.n < kMixedMaxPasses) {
+    int r = (q % 16 == 0 && q != 32) ? 16 : (q % 8 == 0 ? 8 : (q % 4 == 0 ? 4 : (q % 2 == 0 ? 2 : 0)));
+    if (!r) break;
+    m.r[m.n++] = (int8_t)r;
+    q /= r;
+  }
+  if (q != 1) m.n = 0;
+  return m;
+}
+
 cudaError_t launch_doppler_general(const float2* strip, float* map, float* pow, const DopplerArgs& a,
                                    const float2* roots, cudaStream_t s, int* launches) {
+  const MixedSchedule sch = mixed_schedule(a.Mp);
+  if (sch.n > 0) {
+    const size_t smem = (size_t)(1 + 2 * kMixWarps) * a.Mp * sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(doppler_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    ++*launches;
+    doppler_mixed_kernel<<<dim3((unsigned)((a.rows + kMixWarps - 1) / kMixWarps), (unsigned)a.frames), 32 * kMixWarps,
+                           smem, s>>>(strip, map, pow, a, roots, sch);
+    return cudaGetLastError();
+  }
   int P = 1;
   while (a.Mp % (2 * P) == 0) P *= 2;
   const int Q = a.Mp / P;
@@ -275,7 +477,10 @@ cudaError_t launch_doppler_general(const float2* strip, float* map, float* pow, 
   return cudaGetLastError();
 }
 
-int detect_general_blocks(int rows, int Mp) { return (int)(((long)rows * Mp + kGBlockCells - 1) / kGBlockCells); }
+int detect_general_blocks(int rows, int Mp) {
+  const int br = detect_general_band_rows(Mp);
+  return (rows + br - 1) / br;
+}
 
 cudaError_t launch_detect_general(const float* pow, ofdm_target* out, int32_t* n_out, uint32_t* status,
                                   uint32_t* wstatus, const DetectArgs& a, cudaStream_t s, int* launches) {
@@ -284,10 +489,14 @@ cudaError_t launch_detect_general(const float* pow, ofdm_target* out, int32_t* n
     median_general_kernel<<<a.frames, 1024, 0, s>>>(pow, a);
     ++*launches;
   }
-  detect_general_block_kernel<<<dim3((unsigned)blocks, (unsigned)a.frames), kGThreads, 0, s>>>(pow, a, blocks,
-                                                                                              a.counts);
+  const int br = detect_general_band_rows(a.Mp);
+  const size_t tsm = (size_t)(br + 2) * a.Mp * sizeof(float);
+  cudaError_t e = cudaFuncSetAttribute(detect_general_band_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm);
+  if (e != cudaSuccess) return e;
+  detect_general_band_kernel<<<dim3((unsigned)blocks, (unsigned)a.frames), kGThreads, tsm, s>>>(pow, a, blocks, br,
+                                                                                               a.counts);
   ++*launches;
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const size_t smem = (size_t)blocks * sizeof(int);
   e = cudaFuncSetAttribute(detect_general_merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

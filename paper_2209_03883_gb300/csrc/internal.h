@@ -163,6 +163,12 @@ cudaError_t launch_range_pad(int N, int NP, const float2* taps, float2* strip, c
 // windowed Doppler DFT as a P-point then a Q-point DFT, M' = P Q (roots = e^{-2 pi i m / M'})
 // and detection by sorted block lists (a.part_keys holds detect_general_blocks
 // lists of 32 keys per frame).
+constexpr int kMixedMaxPasses = 12;
+struct MixedSchedule {
+  int n;                       // passes (0: M' has a prime factor above 7)
+  int8_t r[kMixedMaxPasses];   // radix of each pass
+};
+MixedSchedule mixed_schedule(int Mp);
 cudaError_t launch_doppler_general(const float2* strip, float* map, float* pow, const DopplerArgs& a,
                                    const float2* roots, cudaStream_t s, int* launches);
 int detect_general_blocks(int rows, int Mp);

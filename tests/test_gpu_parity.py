@@ -302,6 +302,38 @@ def test_detect_entry_point_on_given_map(env):
     assert [(int(t["r"]), int(t["s"])) for t in tg[:n]] == list(zip(det32.r.tolist(), det32.s.tolist()))
 
 
+@pytest.mark.parametrize("N,M,L,window", [(256, 100, 32, o.WINDOW_HANN), (64, 20, 64, o.WINDOW_RECT),
+                                         (128, 44, 16, o.WINDOW_HAMMING)])
+def test_detect_entry_point_general_grid(env, N, M, L, window):
+    """ofdm_radar_detect on a given full map of a Doppler grid that is not a
+    power of two (band detection on map rows, circular halo rows when the
+    support is every row): top-K and threshold mode (median-estimated noise)
+    exactly as the oracle's rule on the same float32 map."""
+    radar, torch, dev = env
+    base = syn.FrameConfig(N=N, M=M, L_cp=L, qam=16, zc_root=1, n_targets=3, on_grid=False, amp_db=(-6.0, 0.0),
+                           snr_db=(0.0, 0.0), window=window, detect_k=8)
+    d = syn.draw_frame(base, 8800 + N + M)
+    Xp = o.zc_precode(d.A, 1)
+    Y = syn.received(d, Xp)
+    for mode in (o.DETECT_TOPK, o.DETECT_THRESHOLD):
+        p = o.Params(N=N, M=M, L_cp=L, zc_root=1, window=window, max_targets=8, detect_mode=mode)
+        P32 = o.process(Y, d.A, p)["P"].astype(np.float32)
+        plan = radar.Plan(**plan_kwargs(p, 1))
+        out = radar.alloc_outputs(plan, 1, dev, with_map=False)
+        radar.ofdm_radar_detect(plan, to_dev(torch, dev, P32[None]), 1, out["targets"], out["n_targets"],
+                                out["status"])
+        torch.cuda.synchronize()
+        rows = o.support_rows(N, L, window)
+        eta = o.threshold(P32, rows, float(np.float32(p.pfa)), p.noise_var) if mode == o.DETECT_THRESHOLD else None
+        det32 = o.detect(P32, mode, p.max_targets, eta)
+        tg = radar.targets_view(out["targets"], 1, p.max_targets)[0]
+        n = int(out["n_targets"][0])
+        assert [(int(t["r"]), int(t["s"])) for t in tg[:n]] == list(zip(det32.r.tolist(), det32.s.tolist()))
+        assert np.array_equal(tg["power"][:n], det32.power.astype(np.float32))
+        assert int(out["status"][0]) == det32.status
+        plan.close()
+
+
 @pytest.mark.parametrize("config,frames", [(2, 8), (1, 37)])
 def test_host_buffer_path_matches_device_path(env, config, frames):
     """Host buffers through the chunked three-stream pipeline equal the device
@@ -432,7 +464,9 @@ def _cfar_ratio(P, rows, r, c, guard, train, pfa):
 
 
 @pytest.mark.parametrize("N,M,L,window,full", [(1024, 256, 128, o.WINDOW_HANN, False),
-                                               (256, 64, 256, o.WINDOW_RECT, True)])
+                                               (256, 64, 256, o.WINDOW_RECT, True),
+                                               (512, 100, 64, o.WINDOW_HANN, False),    # M' = 100: general grid
+                                               (128, 60, 128, o.WINDOW_RECT, True)])
 def test_cfar_detection(env, N, M, L, window, full):
     """CFAR mode: the map against the FP64 oracle, and the detections exactly
     those of the oracle's CFAR rule applied to the GPU's own map, except cells
@@ -476,13 +510,18 @@ GENERAL_M = [
     ("256x100_threshold", dict(N=256, M=100, L_cp=32, window=o.WINDOW_HANN, targets=3, frames=2,
                                detect_mode=o.DETECT_THRESHOLD)),
     ("256x100_full_rect", dict(N=256, M=100, L_cp=256, window=o.WINDOW_RECT, targets=3, frames=2)),
+    ("128x36_hann", dict(N=128, M=36, L_cp=16, window=o.WINDOW_HANN, targets=2, frames=2)),       # 3 x 3 x 4
+    ("64x44_rect_prime11", dict(N=64, M=44, L_cp=8, window=o.WINDOW_RECT, targets=2, frames=2)),  # 11: two-factor
+    ("512x1008_hamming", dict(N=512, M=1008, L_cp=64, window=o.WINDOW_HAMMING, targets=3, frames=1)),  # 7 3 3 16
 ]
 
 
 @pytest.mark.parametrize("name,kw", GENERAL_M, ids=[c[0] for c in GENERAL_M])
 def test_doppler_grid_not_a_power_of_two(env, name, kw):
     """M' = 560 = 2^4 5 7 (Table I) and other non-power-of-two Doppler grids:
-    the two-factor Doppler DFT and the general detection against the
+    the mixed-radix Doppler transform (radices 7, 5, 3, 16, 8, 4), the
+    two-factor form for a prime factor above 7 (M' = 44), and the general
+    detection against the
     oracle (map, bins; the detection itself exactly on the GPU's own map)."""
     base = syn.FrameConfig(N=kw["N"], M=kw["M"], L_cp=kw["L_cp"], qam=16, zc_root=1, n_targets=kw["targets"],
                            on_grid=False, amp_db=(-6.0, 0.0), snr_db=(0.0, 0.0), window=kw["window"], detect_k=4)
