@@ -13,6 +13,10 @@
  *   frame, M OFDM symbols l of N subcarriers k each, k contiguous.
  * - Unless a function says "host", every pointer is a DEVICE pointer owned by
  *   the caller; the plan owns only its tables and workspace.
+ * - Device grids (Y, X, transmit grids), maps and range-profile strips must
+ *   start on a 16-byte boundary (cudaMalloc and PyTorch allocations do): they
+ *   are moved in 16-byte pieces.  A misaligned one is rejected with
+ *   OFDM_ERR_INVALID_ARG; so is a batch frame whose yx_offset is odd.
  * - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
  *   Calls are asynchronous on it; no output is valid before the caller syncs.
  * - Return value: OFDM_OK (0) or a negative OFDM_ERR_* code.  Invalid sizes
@@ -61,9 +65,8 @@ enum { OFDM_DETECT_TOPK = 0, OFDM_DETECT_THRESHOLD = 1, OFDM_DETECT_CFAR = 2 };
  *   OFDM_PREC_SPLIT_FP16  32-point DFT matrix products on the tensor cores
  *                         with FP16 hi + lo operands (three products, FP32
  *                         accumulation; about 2^-21 relative).  N = 1024,
- *                         M a multiple of 4, L_cp <= 256, Y and X 16-byte
- *                         aligned.  Everything after the column stage is the
- *                         FP32 path's. */
+ *                         M a multiple of 4, L_cp <= 256.  Everything after
+ *                         the column stage is the FP32 path's. */
 enum { OFDM_PREC_FP32 = 0, OFDM_PREC_SPLIT_BF16 = 1, OFDM_PREC_SPLIT_FP16 = 2 };
 
 enum {

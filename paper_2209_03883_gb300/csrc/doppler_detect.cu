@@ -16,6 +16,7 @@
 
 #include "fft.cuh"
 #include "internal.h"
+#include "keys.cuh"
 
 namespace ofdm {
 
@@ -220,14 +221,6 @@ __device__ __forceinline__ uint64_t warp_sort_desc(uint64_t v, int lane) {
     }
   }
   return v;
-}
-
-// Largest key of the warp: the larger power word, then the larger index word.
-__device__ __forceinline__ uint64_t warp_max_key(uint64_t v) {
-  const unsigned hi = (unsigned)(v >> 32);
-  const unsigned mh = __reduce_max_sync(0xffffffffu, hi);
-  const unsigned ml = __reduce_max_sync(0xffffffffu, hi == mh ? (unsigned)v : 0u);
-  return ((uint64_t)mh << 32) | ml;
 }
 
 // Merge of up to 32 key lists, each sorted descending with its first K

@@ -13,6 +13,7 @@
 // frame merges the band lists.
 #include "fft.cuh"
 #include "internal.h"
+#include "keys.cuh"
 
 namespace ofdm {
 
@@ -138,8 +139,9 @@ template <int R>
 __device__ __forceinline__ void mixed_pass(const float2* __restrict__ x, float2* __restrict__ y, int L, int Ns,
                                            const float2* __restrict__ roots, int lane) {
   const int nb = L / R, step = L / (Ns * R);
+  int jq = lane / Ns, k = lane - (lane / Ns) * Ns;                // j = jq Ns + k, stepped by 32
+  const int dq = 32 / Ns, dk = 32 % Ns;
   for (int j = lane; j < nb; j += 32) {
-    const int k = j % Ns;
     float2 a[R];
 #pragma unroll
     for (int m = 0; m < R; ++m) a[m] = x[j + m * nb];
@@ -150,9 +152,12 @@ __device__ __forceinline__ void mixed_pass(const float2* __restrict__ x, float2*
     }
     if constexpr (R == 3 || R == 5 || R == 7) dft_odd<R, -1>(a);
     else dft_reg<R, -1>(a);
-    const int o = j + (j / Ns) * Ns * (R - 1);
+    const int o = j + jq * Ns * (R - 1);
 #pragma unroll
     for (int m = 0; m < R; ++m) y[o + m * Ns] = a[m];
+    jq += dq;
+    k += dk;
+    if (k >= Ns) { k -= Ns; ++jq; }
   }
 }
 
@@ -171,7 +176,22 @@ doppler_mixed_kernel(const float2* __restrict__ strip, float* __restrict__ map, 
   const int ri = blockIdx.x * kMixWarps + warp;
   if (ri >= d.rows) return;                                       // no CTA-wide barrier below
   const float2* g = strip + ((size_t)f * d.rows + ri) * M;
-  for (int l = lane; l < Mp; l += 32) b0[l] = l < M ? cscale(g[l], __ldg(d.wl + l)) : make_float2(0.f, 0.f);
+  constexpr int kLd = 8;                                          // loads in flight per lane
+  for (int l0 = 0; l0 < Mp; l0 += 32 * kLd) {
+    float2 t[kLd];
+    float wv[kLd];
+#pragma unroll
+    for (int u = 0; u < kLd; ++u) {
+      const int l = l0 + lane + 32 * u;
+      t[u] = l < M ? g[l] : make_float2(0.f, 0.f);
+      wv[u] = l < M ? __ldg(d.wl + l) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < kLd; ++u) {
+      const int l = l0 + lane + 32 * u;
+      if (l < Mp) b0[l] = cscale(t[u], wv[u]);
+    }
+  }
   __syncwarp();
   float2* x = b0;
   float2* y = b1;
@@ -260,7 +280,7 @@ detect_general_band_kernel(const float* __restrict__ src, DetectArgs a, int bloc
                            unsigned* __restrict__ counts) {
   extern __shared__ __align__(16) float gtile[];   // (band_rows + 2) rows of M'
   __shared__ uint64_t s_list[kGListCap];
-  __shared__ uint64_t s_wmax[kGThreads / 32];
+  __shared__ uint64_t s_wk[kGThreads / 32][32];   // each warp's K best, descending
   __shared__ unsigned s_n;
   const int b = blockIdx.x, f = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int Mp = a.Mp;
@@ -271,35 +291,51 @@ detect_general_band_kernel(const float* __restrict__ src, DetectArgs a, int bloc
   const float eta = thr ? (a.use_fixed_eta ? a.eta_fixed : a.eta[f]) : 0.f;
   if (tid == 0) s_n = 0;
   const int q4 = Mp >> 2;                            // float4 per row (M' % 4 == 0)
-  for (int v = tid; v < (tr + 2) * q4; v += kGThreads) {
-    const int i = v / q4, c4 = v - i * q4;
-    int rj = t0 - 1 + i;
-    if (a.full) rj = (rj + a.rows) % a.rows;
-    float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (rj >= 0 && rj < a.rows) {
-      const int row = a.compact ? rj : (a.row0 + rj) % a.Np;
-      x = __ldg(reinterpret_cast<const float4*>(base + (long)row * Mp) + c4);
+  {
+    int i = tid / q4, c4 = tid - (tid / q4) * q4;    // stepped without divisions
+    const int di = kGThreads / q4, dc4 = kGThreads % q4;
+    for (int v = tid; v < (tr + 2) * q4; v += kGThreads) {
+      int rj = t0 - 1 + i;
+      if (a.full) rj = rj < 0 ? rj + a.rows : (rj >= a.rows ? rj - a.rows : rj);
+      float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (rj >= 0 && rj < a.rows) {
+        const int row = a.compact ? rj : (a.row0 + rj) % a.Np;
+        x = __ldg(reinterpret_cast<const float4*>(base + (long)row * Mp) + c4);
+      }
+      reinterpret_cast<float4*>(gtile)[v] = x;
+      i += di;
+      c4 += dc4;
+      if (c4 >= q4) { c4 -= q4; ++i; }
     }
-    reinterpret_cast<float4*>(gtile)[v] = x;
   }
   __syncthreads();
+  // Scan: a task is (column c, segment of the band rows); it walks down the
+  // segment keeping the 3-wide maxima of the rows above and below in
+  // registers.  With few columns the rows are split into segments so that
+  // every thread has a task.
   unsigned cnt = 0;
-  int i = tid / Mp, c = tid - (tid / Mp) * Mp;
-  const int di = kGThreads / Mp, dcol = kGThreads % Mp;
-  for (int e = tid; e < tr * Mp; e += kGThreads) {
-    const float* row = gtile + (i + 1) * Mp;
-    const float p = row[c];
-    bool cand = p > 0.f && (!thr || p >= eta);
-    if (cand) {
-      const int cm = c == 0 ? Mp - 1 : c - 1, cp = c == Mp - 1 ? 0 : c + 1;
-      const float* up = row - Mp;
-      const float* dn = row + Mp;
+  const int segs = max(1, min(tr, kGThreads / Mp));
+  const int seg_len = (tr + segs - 1) / segs;
+  const uint32_t Np = (uint32_t)a.Np;
+  for (int task = tid; task < segs * Mp; task += kGThreads) {
+    const int sg = task / Mp, c = task - sg * Mp;
+    const int ia = sg * seg_len, ib = min(tr, ia + seg_len);
+    if (ia >= ib) continue;
+    const int cm = c == 0 ? Mp - 1 : c - 1, cp = c == Mp - 1 ? 0 : c + 1;
+    const float* row = gtile + ia * Mp;               // tile row ia = band row ia - 1
+    float up3 = fmaxf(row[c], fmaxf(row[cm], row[cp]));
+    row += Mp;
+    float ml = row[cm], mc = row[c], mr = row[cp];
+    uint32_t r = (uint32_t)((a.row0 + t0 + ia) % a.Np);
+    for (int i = ia; i < ib; ++i) {
+      row += Mp;                                       // band row i + 1
+      const float dl = row[cm], dc = row[c], dr = row[cp];
+      const float mid2 = fmaxf(ml, mr);
       // fmaxf skips NaN, so this is "no neighbour compares greater"
-      const float nmax = fmaxf(fmaxf(fmaxf(up[cm], up[c]), fmaxf(up[cp], row[cm])),
-                               fmaxf(fmaxf(row[cp], dn[cm]), fmaxf(dn[c], dn[cp])));
-      cand = !(nmax > p);
-      const uint32_t r = (uint32_t)((a.row0 + t0 + i) % a.Np);
-      if (cand && nmax == p) cand = !gtie_lost(row, Mp, a.Np, r, c, p);
+      const float nmax = fmaxf(up3, fmaxf(mid2, fmaxf(dc, fmaxf(dl, dr))));
+      const float p = mc;
+      bool cand = p > 0.f && !(nmax > p) && (!thr || p >= eta);
+      if (cand && nmax == p) cand = !gtie_lost(row - Mp, Mp, a.Np, r, c, p);
       if (cand && cfar) cand = gcfar(base, a, t0 + i, c, p);
       if (cand) {
         ++cnt;
@@ -307,36 +343,50 @@ detect_general_band_kernel(const float* __restrict__ src, DetectArgs a, int bloc
         const unsigned pos = atomicAdd(&s_n, 1u);
         if (pos < (unsigned)kGListCap) s_list[pos] = ((uint64_t)__float_as_uint(p) << 32) | (uint64_t)(~idx);
       }
+      up3 = fmaxf(mid2, mc);
+      ml = dl;
+      mc = dc;
+      mr = dr;
+      r = r + 1 == Np ? 0u : r + 1;
     }
-    i += di;
-    c += dcol;
-    if (c >= Mp) { c -= Mp; ++i; }
   }
   cnt = __reduce_add_sync(0xffffffffu, cnt);
   if (lane == 0 && cnt) atomicAdd(counts + f, cnt);
   __syncthreads();
+  // The band's K best, descending: each warp takes the K best of its slice
+  // of the list by repeated warp maxima (keys in registers, no block
+  // barriers), then warp 0 merges the eight sorted lists.
   const int n = min((int)s_n, kGListCap);
-  uint64_t* out = a.part_keys + ((size_t)f * blocks + b) * 32;
-  for (int k = 0; k < a.K; ++k) {                   // the band's K best, descending
-    uint64_t m = 0;
-    for (int j = tid; j < n; j += kGThreads) m = s_list[j] > m ? s_list[j] : m;
+  constexpr int kPer = (kGListCap + kGThreads - 1) / kGThreads;   // keys per lane
+  const int per_w = (n + kGThreads / 32 - 1) / (kGThreads / 32);
+  const int j0 = warp * per_w, j1 = min(n, j0 + per_w);
+  uint64_t v[kPer];
 #pragma unroll
-    for (int o = 16; o; o >>= 1) {
-      const uint64_t u = __shfl_xor_sync(0xffffffffu, m, o);
-      m = u > m ? u : m;
-    }
-    if (lane == 0) s_wmax[warp] = m;
-    __syncthreads();
-    m = s_wmax[0];
-#pragma unroll
-    for (int w = 1; w < kGThreads / 32; ++w) m = s_wmax[w] > m ? s_wmax[w] : m;
-    if (m != 0)
-      for (int j = tid; j < n; j += kGThreads)
-        if (s_list[j] == m) s_list[j] = 0;           // keys are unique (the map index)
-    if (tid == 0) out[k] = m;
-    __syncthreads();
+  for (int q = 0; q < kPer; ++q) {
+    const int j = j0 + lane + 32 * q;
+    v[q] = j < j1 ? s_list[j] : 0ull;
   }
-  for (int k = a.K + tid; k < 32; k += kGThreads) out[k] = 0ull;
+  for (int k = 0; k < a.K; ++k) {
+    uint64_t best = v[0];
+#pragma unroll
+    for (int q = 1; q < kPer; ++q) best = v[q] > best ? v[q] : best;
+    const uint64_t m = warp_max_key(best);
+    if (lane == 0) s_wk[warp][k] = m;
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) v[q] = v[q] == m ? 0ull : v[q];   // keys are unique (the map index)
+  }
+  __syncthreads();
+  if (warp == 0) {
+    uint64_t* out = a.part_keys + ((size_t)f * blocks + b) * 32;
+    int h = 0;
+    uint64_t head = lane < kGThreads / 32 ? s_wk[lane][0] : 0ull, key = 0;
+    for (int k = 0; k < a.K; ++k) {
+      const uint64_t m = warp_max_key(head);
+      if (lane == k) key = m;
+      if (m != 0 && head == m) { ++h; head = h < a.K ? s_wk[lane][h] : 0ull; }
+    }
+    out[lane] = lane < a.K ? key : 0ull;
+  }
 }
 
 // One CTA per frame: the K largest keys of the block lists (each sorted

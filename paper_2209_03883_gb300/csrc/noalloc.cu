@@ -177,7 +177,7 @@ extern "C" int ofdm_radar_process_noalloc(const ofdm_radar_params* pin, const of
                                           int32_t frames, float* out_map, ofdm_target* out_targets,
                                           int32_t* n_targets, uint32_t* status, void* stream) {
   using namespace ofdm;
-  if (!pin || !Y || !X) return OFDM_ERR_INVALID_ARG;
+  if (!pin || !Y || !X || (((uintptr_t)Y | (uintptr_t)X | (uintptr_t)out_map) & 15u)) return OFDM_ERR_INVALID_ARG;
   const ofdm_radar_params& p = *pin;
   int rc = validate(p);
   if (rc != OFDM_OK) return rc;

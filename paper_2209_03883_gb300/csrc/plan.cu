@@ -552,10 +552,12 @@ ColumnArgs column_args(const ofdm_radar_plan* pl, int frames) {
   return a;
 }
 
-// The split-FP16 column kernel moves Y and X rows with bulk copies, which
-// need 16-byte aligned addresses.
-bool tc_misaligned(const ofdm_radar_plan* pl, const void* Y, const void* X) {
-  return pl->d_tc && (((uintptr_t)Y | (uintptr_t)X) & 15u);
+// Grids, maps and strips are moved in 16-byte pieces (row copies into shared
+// memory, bulk copies of the split-FP16 kernel, float4 loads and stores), so
+// every such device buffer must start on a 16-byte boundary.  Null pointers
+// (optional outputs) pass.
+bool misaligned16(const void* a, const void* b = nullptr, const void* c = nullptr) {
+  return (((uintptr_t)a | (uintptr_t)b | (uintptr_t)c) & 15u) != 0;
 }
 
 DopplerArgs doppler_args(const ofdm_radar_plan* pl, int frames) {
@@ -693,7 +695,7 @@ int ofdm_radar_process(ofdm_radar_plan* pl, const ofdm_c32* Y, const ofdm_c32* X
                        float* out_map, ofdm_target* out_targets, int32_t* n_targets, uint32_t* status,
                        void* stream) {
   ofdm::NvtxRange nvtx_range("ofdm_radar_process");
-  if (!pl || !Y || !X || bad_frames(pl, frames) || tc_misaligned(pl, Y, X)) return OFDM_ERR_INVALID_ARG;
+  if (!pl || !Y || !X || bad_frames(pl, frames) || misaligned16(Y, X, out_map)) return OFDM_ERR_INVALID_ARG;
   int launches = 0;
   cudaError_t e = run_chain(pl, (const float2*)Y, (const float2*)X, frames, out_map, out_targets, n_targets,
                             status, (cudaStream_t)stream, &launches);
@@ -703,7 +705,7 @@ int ofdm_radar_process(ofdm_radar_plan* pl, const ofdm_c32* Y, const ofdm_c32* X
 int ofdm_zc_precode(ofdm_radar_plan* pl, const ofdm_c32* in, ofdm_c32* out, int32_t frames, int32_t inverse,
                     void* stream) {
   ofdm::NvtxRange nvtx_range("ofdm_zc_precode");
-  if (!pl || !in || !out || in == out || bad_frames(pl, frames)) return OFDM_ERR_INVALID_ARG;
+  if (!pl || !in || !out || in == out || bad_frames(pl, frames) || misaligned16(in, out)) return OFDM_ERR_INVALID_ARG;
   if (pl->p.zc_root <= 0) return OFDM_ERR_INVALID_ARG;
   ZctArgs a;
   a.frames = frames;
@@ -726,9 +728,7 @@ int ofdm_zc_precode(ofdm_radar_plan* pl, const ofdm_c32* in, ofdm_c32* out, int3
 int ofdm_radar_range_profile(ofdm_radar_plan* pl, const ofdm_c32* Y, const ofdm_c32* X, int32_t frames,
                              ofdm_c32* strip, void* stream) {
   ofdm::NvtxRange nvtx_range("ofdm_radar_range_profile");
-  if (!pl || !Y || !X || !strip || bad_frames(pl, frames) || tc_misaligned(pl, Y, X) ||
-      tc_misaligned(pl, strip, strip))
-    return OFDM_ERR_INVALID_ARG;
+  if (!pl || !Y || !X || !strip || bad_frames(pl, frames) || misaligned16(Y, X, strip)) return OFDM_ERR_INVALID_ARG;
   int launches = 0;
   cudaError_t e = run_column(pl, (const float2*)Y, (const float2*)X, frames, (float2*)strip, (cudaStream_t)stream,
                              &launches);
@@ -741,7 +741,7 @@ int ofdm_radar_range_profile(ofdm_radar_plan* pl, const ofdm_c32* Y, const ofdm_
 int ofdm_radar_doppler(ofdm_radar_plan* pl, const ofdm_c32* strip, int32_t frames, float* out_map,
                        void* stream) {
   ofdm::NvtxRange nvtx_range("ofdm_radar_doppler");
-  if (!pl || !strip || !out_map || bad_frames(pl, frames)) return OFDM_ERR_INVALID_ARG;
+  if (!pl || !strip || !out_map || bad_frames(pl, frames) || misaligned16(strip, out_map)) return OFDM_ERR_INVALID_ARG;
   int launches = 0;
   cudaError_t e = ofdm::launch_zero_rows(out_map, frames, pl->Np, pl->Mp, pl->z0, pl->nz, (cudaStream_t)stream,
                                          &launches);
@@ -757,7 +757,7 @@ int ofdm_radar_doppler(ofdm_radar_plan* pl, const ofdm_c32* strip, int32_t frame
 int ofdm_radar_detect(ofdm_radar_plan* pl, const float* map, int32_t frames, ofdm_target* out_targets,
                       int32_t* n_targets, uint32_t* status, void* stream) {
   ofdm::NvtxRange nvtx_range("ofdm_radar_detect");
-  if (!pl || !map || bad_frames(pl, frames)) return OFDM_ERR_INVALID_ARG;
+  if (!pl || !map || bad_frames(pl, frames) || misaligned16(map)) return OFDM_ERR_INVALID_ARG;
   int launches = 0;
   cudaError_t e = pl->gen ? ofdm::launch_detect_general(map, out_targets, n_targets, status, nullptr,
                                                         detect_args(pl, frames, 0), (cudaStream_t)stream, &launches)
@@ -859,7 +859,7 @@ int ofdm_fps_sft(ofdm_radar_plan* pl, const ofdm_c32* Y, const ofdm_c32* X, int3
                  const ofdm_fps_params* fp, const int32_t* slices, ofdm_target* out_targets,
                  int32_t* n_targets, void* stream) {
   ofdm::NvtxRange nvtx_range("ofdm_fps_sft");
-  if (!pl || !Y || !X || !fp || !slices || bad_frames(pl, frames) || tc_misaligned(pl, Y, X))
+  if (!pl || !Y || !X || !fp || !slices || bad_frames(pl, frames) || misaligned16(Y, X))
     return OFDM_ERR_INVALID_ARG;
   const ofdm_radar_params& p = pl->p;
   const int N = p.N, M = p.M, Q = N > M ? N : M;
@@ -928,7 +928,7 @@ int ofdm_fps_sft(ofdm_radar_plan* pl, const ofdm_c32* Y, const ofdm_c32* X, int3
 int ofdm_tx_amplifier(ofdm_radar_plan* pl, const ofdm_c32* S, int32_t frames, int32_t oversample, float q,
                       float* papr, float* aci, void* stream) {
   ofdm::NvtxRange nvtx_range("ofdm_tx_amplifier");
-  if (!pl || !S || bad_frames(pl, frames) || !(q > -100.f && q < 100.f)) return OFDM_ERR_INVALID_ARG;
+  if (!pl || !S || bad_frames(pl, frames) || !(q > -100.f && q < 100.f) || misaligned16(S)) return OFDM_ERR_INVALID_ARG;
   const int N = pl->p.N, LN = N * oversample;
   if (oversample < 1 || oversample > 8 || (oversample & (oversample - 1)) || LN > 4096)
     return OFDM_ERR_UNSUPPORTED_SIZE;
@@ -1106,7 +1106,8 @@ int ofdm_radar_batch_create(const ofdm_radar_params* base, const ofdm_frame_desc
   *out = nullptr;
   for (int f = 0; f < nframes; ++f) {
     if (!valid_shape(desc[f].N, desc[f].M, desc[f].L_cp)) return OFDM_ERR_UNSUPPORTED_SIZE;
-    if (desc[f].yx_offset < 0 || desc[f].map_offset < 0 || (desc[f].map_offset & 3)) return OFDM_ERR_INVALID_ARG;
+    if (desc[f].yx_offset < 0 || (desc[f].yx_offset & 1) || desc[f].map_offset < 0 || (desc[f].map_offset & 3))
+      return OFDM_ERR_INVALID_ARG;
   }
   ofdm_radar_batch* b = new ofdm_radar_batch();
   b->base = *base;
@@ -1178,7 +1179,7 @@ int ofdm_radar_batch_used_graph(const ofdm_radar_batch* b) { return b ? (b->used
 int ofdm_radar_batch_process(ofdm_radar_batch* b, const ofdm_c32* Yc, const ofdm_c32* Xc, float* map,
                              ofdm_target* tg, int32_t* nt, uint32_t* st, void* stream) {
   ofdm::NvtxRange nvtx_range("ofdm_radar_batch_process");
-  if (!b || !Yc || !Xc) return OFDM_ERR_INVALID_ARG;
+  if (!b || !Yc || !Xc || misaligned16(Yc, Xc, map)) return OFDM_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   const float2* Y = (const float2*)Yc;
   const float2* X = (const float2*)Xc;
@@ -1296,7 +1297,7 @@ int ofdm_radar_coarse_shape(const ofdm_radar_plan* pl, int32_t* h, int32_t* w) {
 int ofdm_radar_coarse_map(ofdm_radar_plan* pl, const ofdm_c32* Y, const ofdm_c32* X, int32_t frames, float* x_out,
                           void* stream) {
   ofdm::NvtxRange nvtx_range("ofdm_radar_coarse_map");
-  if (!pl || !Y || !X || !pl->d_cpow || bad_frames(pl, frames) || tc_misaligned(pl, Y, X)) return OFDM_ERR_INVALID_ARG;
+  if (!pl || !Y || !X || !pl->d_cpow || bad_frames(pl, frames) || misaligned16(Y, X)) return OFDM_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   int launches = 0;
   unsigned long long tk = 0;
@@ -1316,7 +1317,7 @@ int ofdm_radar_process_learned(ofdm_radar_plan* pl, const float* theta, const of
                                uint32_t* st, void* stream) {
   ofdm::NvtxRange nvtx_range("ofdm_radar_process_learned");
   if (!pl || !theta || !Y || !X || !pl->d_cpow || bad_frames(pl, frames) || cap < 1 || cap > 256 ||
-      tc_misaligned(pl, Y, X))
+      misaligned16(Y, X))
     return OFDM_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   int launches = 0;

@@ -334,6 +334,39 @@ def test_detect_entry_point_general_grid(env, N, M, L, window):
         plan.close()
 
 
+def test_misaligned_buffers_rejected(env):
+    """Grids, maps and strips move in 16-byte pieces: a buffer that starts
+    8 bytes off a 16-byte boundary is rejected before any launch, at every
+    entry point that takes one (and the call after it still works)."""
+    radar, torch, dev = env
+    cfg, fr = make_frames(1, 1)
+    p = oracle_params(cfg)
+    plan = radar.Plan(**plan_kwargs(p, 1))
+    n = cfg.N * cfg.M
+    G = torch.zeros((2 * n + 2,), dtype=torch.complex64, device=dev)
+    good, bad = G[:n], G[n + 1:2 * n + 1]                         # bad starts 8 bytes past a boundary
+    mp = torch.zeros((plan.Np * plan.Mp + 4,), dtype=torch.float32, device=dev)
+    out = radar.alloc_outputs(plan, 1, dev, with_map=False)
+    calls = [
+        lambda: radar.ofdm_radar_process(plan, bad, good, 1),
+        lambda: radar.ofdm_radar_process(plan, good, bad, 1),
+        lambda: radar.ofdm_radar_process(plan, good, good, 1, mp[2:2 + plan.Np * plan.Mp], out["targets"],
+                                         out["n_targets"], out["status"]),
+        lambda: radar.ofdm_radar_detect(plan, mp[2:2 + plan.Np * plan.Mp], 1, out["targets"], out["n_targets"],
+                                        out["status"]),
+        lambda: radar.ofdm_zc_precode(plan, bad, good, 1),
+    ]
+    for call in calls:
+        with pytest.raises(radar.OfdmError) as ei:
+            call()
+        assert ei.value.code == -1
+    Y, X = to_dev(torch, dev, stack_lk([fr[0][2]])), to_dev(torch, dev, stack_lk([fr[0][0].A]))
+    radar.ofdm_radar_process(plan, Y, X, 1, None, out["targets"], out["n_targets"], out["status"])
+    torch.cuda.synchronize()
+    assert int(out["n_targets"][0]) > 0
+    plan.close()
+
+
 @pytest.mark.parametrize("config,frames", [(2, 8), (1, 37)])
 def test_host_buffer_path_matches_device_path(env, config, frames):
     """Host buffers through the chunked three-stream pipeline equal the device
