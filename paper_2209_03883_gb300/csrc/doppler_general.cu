@@ -9,8 +9,9 @@
 //
 // Detection (Eq. (18)): 8-neighbour local maxima (circular), optionally above
 // the global threshold or the CFAR one, ordered by power then map index:
-// each CTA takes a band of support rows and keeps its best K; one CTA per
-// frame merges the band lists.
+// each CTA takes a band of support rows, keeps its best K and zeroes its
+// share of the map rows outside the support; the last CTA of a frame merges
+// the band lists.
 #include "fft.cuh"
 #include "internal.h"
 #include "keys.cuh"
@@ -277,7 +278,9 @@ __device__ __noinline__ bool gtie_lost(const float* row, int Mp, int Np, uint32_
 
 __global__ void __launch_bounds__(kGThreads)
 detect_general_band_kernel(const float* __restrict__ src, DetectArgs a, int blocks, int band_rows,
-                           unsigned* __restrict__ counts) {
+                           unsigned* __restrict__ counts, ofdm_target* __restrict__ out_t,
+                           int32_t* __restrict__ n_out, uint32_t* __restrict__ status,
+                           uint32_t* __restrict__ wstatus) {
   extern __shared__ __align__(16) float gtile[];   // (band_rows + 2) rows of M'
   __shared__ uint64_t s_list[kGListCap];
   __shared__ uint64_t s_wk[kGThreads / 32][32];   // each warp's K best, descending
@@ -307,6 +310,15 @@ detect_general_band_kernel(const float* __restrict__ src, DetectArgs a, int bloc
       c4 += dc4;
       if (c4 >= q4) { c4 -= q4; ++i; }
     }
+  }
+  // The map rows outside the support are zero: this CTA's share of its frame
+  // (streaming stores, issued before the scan so that they overlap it).
+  if (a.zmap) {
+    const long per = a.z_floats >> 2;
+    float4* zp = reinterpret_cast<float4*>(a.zmap + (a.zmap_off ? (long)a.zmap_off[f] : (long)f * a.zframe) +
+                                           a.z_off);
+    for (long j = per * b / blocks + tid; j < per * (b + 1) / blocks; j += kGThreads)
+      __stcs(zp + j, make_float4(0.f, 0.f, 0.f, 0.f));
   }
   __syncthreads();
   // Scan: a task is (column c, segment of the band rows); it walks down the
@@ -387,70 +399,54 @@ detect_general_band_kernel(const float* __restrict__ src, DetectArgs a, int bloc
     }
     out[lane] = lane < a.K ? key : 0ull;
   }
-}
 
-// One CTA per frame: the K largest keys of the block lists (each sorted
-// descending) by K rounds of a block-wide maximum over the lists' heads; then
-// the targets and status.
-__global__ void __launch_bounds__(kGThreads)
-detect_general_merge_kernel(DetectArgs a, int blocks, unsigned* __restrict__ counts, ofdm_target* __restrict__ out,
-                            int32_t* __restrict__ n_out, uint32_t* __restrict__ status,
-                            uint32_t* __restrict__ wstatus) {
-  extern __shared__ int heads[];                 // [blocks] position of each list's head
-  __shared__ uint64_t s_key[kGThreads / 32];
-  __shared__ int s_list[kGThreads / 32];
-  __shared__ uint64_t s_top[32];
-  const int f = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint64_t* src = a.part_keys + (size_t)f * blocks * 32;
-  const int K = a.K;
-  for (int b = tid; b < blocks; b += kGThreads) heads[b] = 0;
+  // The last CTA of the frame (atomic ticket, no waiting) merges the band
+  // lists: directly for up to 32 bands, else per group of 32 bands and then
+  // the groups (at most 1024 bands: band_rows >= 4 rows of at most 4096).
+  __shared__ int s_last;
+  __threadfence();
   __syncthreads();
-  for (int k = 0; k < K; ++k) {
-    uint64_t best = 0;
-    int bl = -1;
-    for (int b = tid; b < blocks; b += kGThreads) {
-      const uint64_t v = heads[b] < 32 ? src[b * 32 + heads[b]] : 0ull;
-      if (v > best) { best = v; bl = b; }
-    }
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-      const uint64_t ov = __shfl_xor_sync(0xffffffffu, best, o);
-      const int ob = __shfl_xor_sync(0xffffffffu, bl, o);
-      if (ov > best) { best = ov; bl = ob; }
-    }
-    if (lane == 0) { s_key[warp] = best; s_list[warp] = bl; }
-    __syncthreads();
-    if (tid == 0) {
-      uint64_t m = s_key[0];
-      int mb = s_list[0];
-      for (int w = 1; w < kGThreads / 32; ++w)
-        if (s_key[w] > m) { m = s_key[w]; mb = s_list[w]; }
-      s_top[k] = m;
-      if (m != 0 && mb >= 0) ++heads[mb];
+  if (tid == 0) s_last = atomicAdd(a.tickets + f, 1u) == (unsigned)(blocks - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const volatile uint64_t* all = a.part_keys + (size_t)f * blocks * 32;
+  uint64_t key = 0;
+  if (blocks <= 32) {
+    if (warp == 0) key = warp_merge_lists(all, blocks, a.K, lane);
+  } else {
+    const int groups = (blocks + 31) >> 5;
+    for (int g = warp; g < groups; g += kGThreads / 32) {
+      const uint64_t v = warp_merge_lists(all + ((size_t)g << 10), min(32, blocks - (g << 5)), a.K, lane);
+      s_list[(g << 5) + lane] = lane < a.K ? v : 0ull;
     }
     __syncthreads();
+    if (warp == 0) key = warp_merge_lists(s_list, groups, a.K, lane);
   }
-  if (tid == 0) {
-    const unsigned total = counts[f];
-    const int nv = (int)(total < (unsigned)K ? total : (unsigned)K);
+  if (warp == 0) {
+    const bool valid = lane < a.K && key != 0;
+    const int nv = __popc(__ballot_sync(0xffffffffu, valid));
     const int oi = a.out_idx ? a.out_idx[f] : f;
-    for (int i = 0; i < nv; ++i) {
-      const uint32_t idx = ~(uint32_t)(s_top[i] & 0xffffffffu);
+    if (valid && out_t) {
+      const uint32_t idx = ~(uint32_t)(key & 0xffffffffu);
       ofdm_target t;
-      t.r = (int32_t)(idx / (uint32_t)a.Mp);
-      t.s = (int32_t)(idx % (uint32_t)a.Mp) - a.Mp / 2;
-      t.power = __uint_as_float((uint32_t)(s_top[i] >> 32));
+      t.r = (int32_t)(idx / (uint32_t)Mp);
+      t.s = (int32_t)(idx % (uint32_t)Mp) - Mp / 2;
+      t.power = __uint_as_float((uint32_t)(key >> 32));
       t.range_m = (float)t.r * a.dd;
       t.vel_mps = (float)t.s * a.dv;
-      if (out) out[(size_t)oi * K + i] = t;
+      out_t[(size_t)oi * a.K + lane] = t;
     }
-    uint32_t st = wstatus ? wstatus[f] : 0u;
-    if (a.mode == OFDM_DETECT_TOPK && total < (unsigned)K) st |= OFDM_STATUS_FEW_PEAKS;
-    if (a.mode != OFDM_DETECT_TOPK && total > (unsigned)K) st |= OFDM_STATUS_OVERFLOW;
-    if (n_out) n_out[oi] = nv;
-    if (status) status[oi] = st;
-    if (wstatus) wstatus[f] = 0u;
-    counts[f] = 0u;
+    if (lane == 0) {
+      const unsigned total = atomicExch(counts + f, 0u);
+      uint32_t st = wstatus ? wstatus[f] : 0u;
+      if (a.mode == OFDM_DETECT_TOPK && total < (unsigned)a.K) st |= OFDM_STATUS_FEW_PEAKS;
+      if (a.mode != OFDM_DETECT_TOPK && total > (unsigned)a.K) st |= OFDM_STATUS_OVERFLOW;
+      if (status) status[oi] = st;
+      if (n_out) n_out[oi] = nv;
+      if (wstatus) wstatus[f] = 0u;   // ready for the next call
+      a.tickets[f] = 0u;
+    }
   }
 }
 
@@ -543,15 +539,8 @@ cudaError_t launch_detect_general(const float* pow, ofdm_target* out, int32_t* n
   const size_t tsm = (size_t)(br + 2) * a.Mp * sizeof(float);
   cudaError_t e = cudaFuncSetAttribute(detect_general_band_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm);
   if (e != cudaSuccess) return e;
-  detect_general_band_kernel<<<dim3((unsigned)blocks, (unsigned)a.frames), kGThreads, tsm, s>>>(pow, a, blocks, br,
-                                                                                               a.counts);
-  ++*launches;
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  const size_t smem = (size_t)blocks * sizeof(int);
-  e = cudaFuncSetAttribute(detect_general_merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  detect_general_merge_kernel<<<a.frames, kGThreads, smem, s>>>(a, blocks, a.counts, out, n_out, status, wstatus);
+  detect_general_band_kernel<<<dim3((unsigned)blocks, (unsigned)a.frames), kGThreads, tsm, s>>>(
+      pow, a, blocks, br, a.counts, out, n_out, status, wstatus);
   ++*launches;
   return cudaGetLastError();
 }

@@ -160,9 +160,12 @@ cudaError_t launch_range_pad(int N, int NP, const float2* taps, float2* strip, c
                              int* launches);
 
 // Doppler grid M' that is not a power of two (doppler_general.cu): the
-// windowed Doppler DFT as a P-point then a Q-point DFT, M' = P Q (roots = e^{-2 pi i m / M'})
-// and detection by sorted block lists (a.part_keys holds detect_general_blocks
-// lists of 32 keys per frame).
+// windowed Doppler DFT by a mixed-radix FFT (radices 2, 3, 4, 5, 7, 8, 16) or,
+// for other M', a P-point then a Q-point DFT, M' = P Q (roots = e^{-2 pi i m / M'});
+// detection by bands of support rows whose sorted top-K lists the last CTA
+// of each frame merges (a.part_keys holds detect_general_blocks lists of 32
+// keys per frame); the detection launch also zeroes the map rows outside the
+// support (a.zmap).
 constexpr int kMixedMaxPasses = 12;
 struct MixedSchedule {
   int n;                       // passes (0: M' has a prime factor above 7)

@@ -661,18 +661,16 @@ cudaError_t run_chain(ofdm_radar_plan* pl, const float2* Y, const float2* X, int
   }
   if (e != cudaSuccess) return e;
   DetectArgs ta = detect_args(pl, frames, 1);
+  set_zero_rows(pl, map, nullptr, &ta);   // the detection launch zeroes the rows outside the support
   if (pl->gen) {   // M' not a power of two
     {
       ScopedTimer tm(pl, s, K_DOPPLER);
-      if (map) e = ofdm::launch_zero_rows(map, frames, pl->Np, pl->Mp, pl->z0, pl->nz, s, launches);
-      if (e == cudaSuccess)
-        e = ofdm::launch_doppler_general(pl->d_strip, map, pl->d_pow, doppler_args(pl, frames), pl->twM, s, launches);
+      e = ofdm::launch_doppler_general(pl->d_strip, map, pl->d_pow, doppler_args(pl, frames), pl->twM, s, launches);
     }
     if (e != cudaSuccess) return e;
     ScopedTimer tm(pl, s, K_DETECT);
     return ofdm::launch_detect_general(pl->d_pow, tg, nt, st, pl->d_wstatus, ta, s, launches);
   }
-  set_zero_rows(pl, map, nullptr, &ta);   // the detection launch zeroes the rows outside the support
   if (ofdm::doppler_detect_fusable(ta, pl->Mp)) {
     ScopedTimer tm(pl, s, K_DETECT);      // Doppler stage included
     return ofdm::launch_doppler_detect(pl->Mp, pl->d_strip, map, tg, nt, st, pl->d_wstatus, ta,
