@@ -42,8 +42,8 @@ COLUMN_BYTES_PER_FRAME = 16 * CFG.N * CFG.M    # the column kernel reads Y and X
 
 # DRAM traffic of the column kernel from one ncu capture of this workload,
 # valid only while its sources are byte-identical to the captured ones.
-TRAFFIC = {"bytes": 268.747520e6 + 5.859072e6,
-           "sources": {"paper_2209_03883_gb300/csrc/column.cu": "7e8ff9e9fc7136727ead73dbe38bd7c865422c38",
+TRAFFIC = {"bytes": 268.767232e6 + 5.530112e6,
+           "sources": {"paper_2209_03883_gb300/csrc/column.cu": "7739e046ea929c5c53245db464e7b88bf372bb9c",
                        "paper_2209_03883_gb300/csrc/fft.cuh": "be6a0ab259f107f9f03afd0cdec7d675d6bb08b2",
                        "paper_2209_03883_gb300/csrc/refine.cuh": "cd4a12e621e0713ccbb4e9a483c65f5bd7eb2b32"}}
 
@@ -566,10 +566,10 @@ def rmse_sweep(radar, torch, dev, snrs=(-50.0, -45.0, -40.0, -35.0, -30.0, -25.0
     return out
 
 
-def extra_table1(radar, torch, dev, stream, steps, frames=16):
+def extra_table1(radar, torch, dev, stream, steps, frames=16, sweep=True):
     """Throughput of the chain at Table I's size (N = 2048, M = M' = 560: the
-    Doppler stage as a two-factor DFT, 560 = 16 x 35, not a power-of-two FFT) and the RMSE
-    sweep."""
+    Doppler stage as a mixed-radix FFT, 560 = 7 x 5 x 16, not a power-of-two
+    FFT) and, unless sweep is False, the RMSE sweep."""
     N, M, L = 2048, 560, 512
     cfg = syn.FrameConfig(N=N, M=M, L_cp=L, qam=16, zc_root=1, n_targets=5, on_grid=False, amp_db=(-6.0, 0.0),
                           snr_db=(0.0, 0.0), window=2, detect_k=5)
@@ -601,9 +601,11 @@ def extra_table1(radar, torch, dev, stream, steps, frames=16):
     stage = {k: round(v[0], 4) for k, v in plan.timing_read().items() if v[1]}
     plan.timing_enable(False)
     plan.close()
-    return {"workload": f"{frames} frames N=2048, M=M'=560, L_cp=N_cp=512, Hamming, ZC precoding",
-            "value": frames / (ms / 1e3), "unit": "frames/s", "ms_per_step": ms, "stage_ms": stage,
-            "rmse_vs_snr": rmse_sweep(radar, torch, dev)}
+    out = {"workload": f"{frames} frames N=2048, M=M'=560, L_cp=N_cp=512, Hamming, ZC precoding",
+           "value": frames / (ms / 1e3), "unit": "frames/s", "ms_per_step": ms, "stage_ms": stage}
+    if sweep:
+        out["rmse_vs_snr"] = rmse_sweep(radar, torch, dev)
+    return out
 
 
 def _hits(tv, nt, truth, M):
@@ -898,6 +900,32 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+LEGS = ("table1_2048x560", "batched_uneven", "sparse_fps_ls_vs_periodogram", "learned_vs_plain")
+
+
+def run_leg(args):
+    """One secondary measurement alone, on one GPU, printed as one JSON line
+    (for profiling a workload without the headline run around it)."""
+    import torch
+    from paper_2209_03883_gb300 import radar
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    steps = max(3, min(args.steps, 10))
+    if args.leg == "batched_uneven":
+        stream = torch.cuda.Stream(device=dev)   # a graph needs a capturable (non-legacy) stream
+        with torch.cuda.stream(stream):
+            out = extra_batched(radar, torch, dev, stream, steps)
+    else:
+        stream = torch.cuda.current_stream()
+        if args.leg == "table1_2048x560":
+            out = extra_table1(radar, torch, dev, stream, steps, sweep=not args.no_sweep)
+        elif args.leg == "sparse_fps_ls_vs_periodogram":
+            out = extra_fps_ls(radar, torch, dev, stream, steps)
+        else:
+            out = extra_learned(radar, torch, dev, stream, steps)
+    print(json.dumps({"leg": args.leg, **out}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -908,8 +936,12 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and FPS-SFT measurements")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "split_fp16"],
                     help="column stage of the headline chain: FP32 FFTs or split-FP16 tensor cores")
+    ap.add_argument("--leg", choices=LEGS, help="run only this secondary measurement and print its JSON line")
+    ap.add_argument("--no-sweep", action="store_true", help="with --leg table1_2048x560: skip the RMSE sweep")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.leg:
+        run_leg(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
