@@ -31,7 +31,7 @@ namespace {
 constexpr int kNoallocMaxCells = 1 << 20;    // frames * support rows * M' (and * M)
 constexpr int kNoallocMaxFrames = 4096;
 constexpr int kMaxN = 4096, kMaxM = 1024;
-constexpr float kNoallocRefineTau = 1e-4f;   // same threshold as the plan path
+constexpr float kNoallocRefineTau = 5e-5f;   // same threshold as the plan path
 
 // Byte layout of the scratch array (every region 256-byte aligned).
 constexpr size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }

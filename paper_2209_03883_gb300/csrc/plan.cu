@@ -85,11 +85,13 @@ struct ofdm_radar_plan {
 
 namespace {
 // Precoded cells with |X_p|^2 below this fraction of the symbol's mean power
-// are recomputed in double-float (about 1e-4 of the cells for a ZC-precoded
-// QAM grid), which keeps the FP32 chain's error near FP32 rounding even when
-// the LS division meets a near-zero precoded cell.
+// are recomputed in double-float (about 5e-5 of the cells for a ZC-precoded
+// QAM grid), which keeps the FP32 chain's map error within half of the 1e-5
+// gate even when the LS division meets a near-zero precoded cell.  Each
+// recomputed cell costs an N-term double-float sum, so the threshold trades
+// the column stage's time against that margin.
 #ifndef OFDM_REFINE_TAU
-#define OFDM_REFINE_TAU 1e-4f
+#define OFDM_REFINE_TAU 5e-5f
 #endif
 constexpr float kRefineTau = OFDM_REFINE_TAU;
 constexpr int kMaxTimed = 4096;
