@@ -187,6 +187,48 @@ def test_training_lowers_loss_and_checkpoint_roundtrip(env):
         assert torch.equal(tr2.logits(Y, A), z1)
 
 
+def test_checkpoint_resume_continues_the_loss_trajectory(env):
+    """Resuming from a checkpoint (parameters, Adam moments and step count)
+    continues training as if it had never stopped: a run interrupted after
+    8 of 16 steps, reloaded into a trainer with other initial weights,
+    reproduces the uninterrupted run's losses on the remaining steps and ends
+    on the same parameters (up to the summation order of the gradient
+    atomics)."""
+    radar, torch, dev = env
+    from paper_2209_03883_gb300.learned import Trainer, coarse_labels
+    cfg = syn.FrameConfig(N=1024, M=256, L_cp=128, qam=16, zc_root=1, n_targets=8, on_grid=False,
+                          amp_db=(-10.0, 0.0), snr_db=(-10.0, 0.0), window=1)
+    plan = radar.Plan(N=1024, M=256, L_cp=128, max_frames=4, max_targets=8)
+    rows = plan.support_rows()
+
+    def precode(A):
+        out = torch.empty_like(A)
+        radar.ofdm_zc_precode(plan, A, out, A.shape[0])
+        return out
+
+    full = Trainer(plan, torch, dev, seed=3)
+    batches = []
+    for step in range(16):
+        Y, A, truth = syn.draw_frames_torch(cfg, [95000 + 4 * step + i for i in range(4)], dev, precode)
+        batches.append((Y, A, coarse_labels(truth, 1024, 256, len(rows), rows[0], full.Hc, full.Mc)))
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "cnn.bin")
+        loss_full = []
+        for step, (Y, A, lab) in enumerate(batches):
+            loss_full.append(float(full.train_step(Y, A, lab)))
+            if step == 7:
+                full.save(path)
+        resumed = Trainer(plan, torch, dev, seed=11)
+        assert not torch.equal(resumed.theta, full.theta)
+        resumed.load(path)
+        assert resumed.step == 8
+        loss_resumed = [float(resumed.train_step(Y, A, lab)) for Y, A, lab in batches[8:]]
+    assert resumed.step == full.step == 16
+    np.testing.assert_allclose(loss_resumed, loss_full[8:], rtol=1e-3)
+    rel = float(torch.linalg.vector_norm(resumed.theta - full.theta) / torch.linalg.vector_norm(full.theta))
+    assert rel < 1e-3, rel
+
+
 def test_trained_network_gain_over_the_plain_chain(env, capsys):
     """What the trained network gains over the chain without it, on held-out
     frames of the learned workload's shape (4096 x 1024, L_cp 512, 32 off-grid
