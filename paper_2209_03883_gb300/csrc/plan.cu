@@ -5,6 +5,9 @@
 #include <string.h>
 
 #include <complex>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "fft.cuh"
@@ -167,9 +170,38 @@ void build_twiddles(std::vector<float2>& out, int n, int e) {
 
 int column_points_per_thread(int N) { return N <= 1024 ? N / 32 : 32; }
 
+// Every device buffer the library allocates ends in a 256-byte canary of
+// all-ones bytes (a NaN for float data), written at allocation and never by a
+// kernel; ofdm_radar_workspace_intact() checks that no launch wrote past the
+// end of its buffer.  The tail also covers reads of up to 16 bytes past it.
+constexpr size_t kCanaryBytes = 256;
+std::mutex g_canary_mu;
+std::map<const char*, size_t> g_canary;   // allocation -> bytes before its canary
+
 template <class T>
 cudaError_t dalloc(T** p, size_t count) {
-  return cudaMalloc((void**)p, count * sizeof(T) + 16);
+  const size_t bytes = count * sizeof(T);
+  cudaError_t e = cudaMalloc((void**)p, bytes + kCanaryBytes);
+  if (e != cudaSuccess) return e;
+  e = cudaMemset(reinterpret_cast<char*>(*p) + bytes, 0xFF, kCanaryBytes);
+  if (e != cudaSuccess) {
+    cudaFree(*p);
+    *p = nullptr;
+    return e;
+  }
+  std::lock_guard<std::mutex> lk(g_canary_mu);
+  g_canary[reinterpret_cast<const char*>(*p)] = bytes;
+  return cudaSuccess;
+}
+
+// Frees a dalloc buffer (null: nothing).
+void dfree(void* p) {
+  if (!p) return;
+  {
+    std::lock_guard<std::mutex> lk(g_canary_mu);
+    g_canary.erase(reinterpret_cast<const char*>(p));
+  }
+  cudaFree(p);
 }
 
 }  // namespace
@@ -205,43 +237,57 @@ const char* ofdm_radar_strerror(int code) {
   }
 }
 
+int ofdm_radar_workspace_intact(void) {
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e);
+  std::lock_guard<std::mutex> lk(g_canary_mu);
+  unsigned char tail[kCanaryBytes];
+  for (const auto& a : g_canary) {
+    e = cudaMemcpy(tail, a.first + a.second, kCanaryBytes, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e);
+    for (size_t i = 0; i < kCanaryBytes; ++i)
+      if (tail[i] != 0xFF) return 0;
+  }
+  return 1;
+}
+
 void ofdm_radar_plan_destroy(ofdm_radar_plan* plan) {
   if (!plan) return;
-  cudaFree(plan->d_tables);
-  cudaFree(plan->d_df);
-  cudaFree(plan->d_tc);
-  cudaFree(plan->d_fps);
-  cudaFree(plan->d_twL);
-  cudaFree(plan->d_taps);
-  cudaFree(plan->d_padtab);
-  cudaFree(plan->d_wk);
-  cudaFree(plan->d_alpha);
-  cudaFree(plan->d_wl);
-  cudaFree(plan->d_strip);
-  cudaFree(plan->d_pow);
-  cudaFree(plan->d_wstatus);
-  cudaFree(plan->d_ctr);
-  cudaFree(plan->d_detkeys);
-  cudaFree(plan->d_dettick);
-  cudaFree(plan->d_eta);
-  cudaFree(plan->d_cpow);
-  cudaFree(plan->d_cx);
-  cudaFree(plan->d_a1);
-  cudaFree(plan->d_a2);
-  cudaFree(plan->d_logit);
-  cudaFree(plan->d_w4);
-  cudaFree(plan->d_twMc);
-  cudaFree(plan->d_rootsM);
-  cudaFree(plan->d_mask);
-  cudaFree(plan->d_cand);
-  cudaFree(plan->d_ncand);
-  cudaFree(plan->d_keys);
-  cudaFree(plan->d_Y);
-  cudaFree(plan->d_X);
-  cudaFree(plan->d_map);
-  cudaFree(plan->d_tg);
-  cudaFree(plan->d_nt);
-  cudaFree(plan->d_st);
+  dfree(plan->d_tables);
+  dfree(plan->d_df);
+  dfree(plan->d_tc);
+  dfree(plan->d_fps);
+  dfree(plan->d_twL);
+  dfree(plan->d_taps);
+  dfree(plan->d_padtab);
+  dfree(plan->d_wk);
+  dfree(plan->d_alpha);
+  dfree(plan->d_wl);
+  dfree(plan->d_strip);
+  dfree(plan->d_pow);
+  dfree(plan->d_wstatus);
+  dfree(plan->d_ctr);
+  dfree(plan->d_detkeys);
+  dfree(plan->d_dettick);
+  dfree(plan->d_eta);
+  dfree(plan->d_cpow);
+  dfree(plan->d_cx);
+  dfree(plan->d_a1);
+  dfree(plan->d_a2);
+  dfree(plan->d_logit);
+  dfree(plan->d_w4);
+  dfree(plan->d_twMc);
+  dfree(plan->d_rootsM);
+  dfree(plan->d_mask);
+  dfree(plan->d_cand);
+  dfree(plan->d_ncand);
+  dfree(plan->d_keys);
+  dfree(plan->d_Y);
+  dfree(plan->d_X);
+  dfree(plan->d_map);
+  dfree(plan->d_tg);
+  dfree(plan->d_nt);
+  dfree(plan->d_st);
   for (auto& s : plan->hs)
     if (s) cudaStreamDestroy(s);
   for (auto& e : plan->ev)
@@ -784,7 +830,7 @@ int ofdm_radar_process_host(ofdm_radar_plan* pl, const ofdm_c32* Yh, const ofdm_
     for (int i = 0; i < 2 + 2 * kHostChunks && e == cudaSuccess; ++i)
       e = cudaEventCreateWithFlags(&pl->ev[i], cudaEventDisableTiming);
     if (e != cudaSuccess) {
-      cudaFree(pl->d_Y); pl->d_Y = nullptr;
+      dfree(pl->d_Y); pl->d_Y = nullptr;
       cudaGetLastError();
       return e == cudaErrorMemoryAllocation ? OFDM_ERR_NO_MEMORY : cuda_fail(e);
     }
@@ -874,7 +920,7 @@ int ofdm_fps_sft(ofdm_radar_plan* pl, const ofdm_c32* Y, const ofdm_c32* X, int3
   if (need > pl->fps_elems) {
     cudaError_t ea = cudaStreamSynchronize(s);   // the old workspace may still be in use
     if (ea != cudaSuccess) return cuda_fail(ea);
-    cudaFree(pl->d_fps);
+    dfree(pl->d_fps);
     pl->d_fps = nullptr;
     pl->fps_elems = 0;
     ea = dalloc(&pl->d_fps, need);
@@ -938,7 +984,7 @@ int ofdm_tx_amplifier(ofdm_radar_plan* pl, const ofdm_c32* S, int32_t frames, in
     build_twiddles(tw, LN, ofdm::tx_points_per_thread(LN));
     cudaError_t e = cudaStreamSynchronize(s);   // the previous table may still be in use
     if (e == cudaSuccess) {
-      cudaFree(pl->d_twL);
+      dfree(pl->d_twL);
       pl->d_twL = nullptr;
       pl->twL_n = 0;
       e = dalloc(&pl->d_twL, tw.size());
@@ -964,9 +1010,6 @@ int ofdm_tx_amplifier(ofdm_radar_plan* pl, const ofdm_c32* S, int32_t frames, in
 }  // extern "C"
 
 // ---------------------------------------------------------------- batches of uneven frames
-#include <map>
-#include <mutex>
-#include <tuple>
 
 namespace {
 
@@ -1090,9 +1133,9 @@ void ofdm_radar_batch_destroy(ofdm_radar_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   for (auto& g : b->groups) {
     ofdm_radar_plan_destroy(g.plan);
-    cudaFree(g.d_frame_off);
-    cudaFree(g.d_map_off);
-    cudaFree(g.d_idx);
+    dfree(g.d_frame_off);
+    dfree(g.d_map_off);
+    dfree(g.d_idx);
     if (g.stream) cudaStreamDestroy(g.stream);
     if (g.done) cudaEventDestroy(g.done);
   }

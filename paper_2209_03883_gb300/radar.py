@@ -79,6 +79,7 @@ def _load():
     lib.ofdm_radar_plan_create.argtypes = [P(Params), P(vp)]
     lib.ofdm_radar_plan_destroy.argtypes = [vp]
     lib.ofdm_radar_plan_destroy.restype = None
+    lib.ofdm_radar_workspace_intact.argtypes = []
     lib.ofdm_radar_support_rows.argtypes = [vp, vp]
     lib.ofdm_radar_process.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp, vp]
     lib.ofdm_radar_process_host.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp, vp]
@@ -349,6 +350,13 @@ def targets_view(raw, frames, max_targets):
 
 
 # ------------------------------------------------------------- torch helpers
+def ofdm_radar_workspace_intact() -> bool:
+    """True if no launch wrote past the end of any device buffer the library
+    allocated (the 256-byte canaries behind every plan and batch buffer).
+    Waits for all work on the current device."""
+    return _check(_lib.ofdm_radar_workspace_intact(), "ofdm_radar_workspace_intact") == 1
+
+
 def alloc_outputs(plan: Plan, frames: int, device="cuda", with_map=True):
     import torch
     out = {
