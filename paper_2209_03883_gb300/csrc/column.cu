@@ -146,7 +146,10 @@ __device__ __forceinline__ uint32_t refine_small_cells_group(float2* v, const fl
 
 // F_i = Y_i / X_p,i with X_p,i = post_i B_i / sqrt(N), B in v:
 //   F_i = Y_i conj(post_i) sqrt(N) conj(B_i) / |B_i|^2   (Eq. (16)).
-template <int T, int E>
+// R1Q0: r' = 1 and q' = 0 known at compile time, so the post factor is (-1)^i
+// (no table) -- the form the group kernel is instantiated for when the
+// plan's ZC parameters allow it.
+template <int T, int E, bool R1Q0 = false>
 __device__ __forceinline__ uint32_t divide_precoded(float2* v, const float2* yrow, bool y_in_smem,
                                                     const ColumnArgs& a, int t) {
   uint32_t flags = 0;
@@ -155,7 +158,7 @@ __device__ __forceinline__ uint32_t divide_precoded(float2* v, const float2* yro
   for (int q = 0; q < E; ++q) {
     const int i = t + T * q;
     float2 yv = y_in_smem ? yrow[i] : ld_stream(yrow + i);
-    if (!a.post_sign) yv = cmul(yv, __ldg(a.post_conj + i));
+    if (!R1Q0 && !a.post_sign) yv = cmul(yv, __ldg(a.post_conj + i));
     const float d2 = v[q].x * v[q].x + v[q].y * v[q].y;
     flags |= (d2 == 0.f) ? OFDM_STATUS_ZERO_X : 0u;
     const float inv = (d2 > 0.f) ? sgn * rcp_approx(d2) : 0.f;
@@ -392,7 +395,11 @@ struct GroupPipeCfg {
   static_assert(T % 32 == 0, "whole warps");
 };
 
-template <int N, int TT = N / 32>
+// R1Q0: instantiated for r' = 1, q' = 0 (the ZC transform's input permutation
+// is the identity and its post factor is (-1)^i): the per-point index and
+// table branches, which the unrolled loops would otherwise issue predicated,
+// are gone.
+template <int N, int TT = N / 32, bool R1Q0 = false>
 __global__ void __launch_bounds__(GroupPipeCfg<N, TT>::THREADS, 1)
 column_group_pipe_kernel(const float2* __restrict__ Y, const float2* __restrict__ X, float2* __restrict__ strip,
                          uint32_t* __restrict__ wstatus, ColumnArgs a) {
@@ -467,7 +474,7 @@ column_group_pipe_kernel(const float2* __restrict__ Y, const float2* __restrict_
 #pragma unroll
       for (int q = 0; q < E; ++q) {
         const int k = t + T * q;
-        const int s2 = (a.rinv == 1) ? k : (int)(((unsigned)a.rinv * (unsigned)k) & (N - 1));
+        const int s2 = (R1Q0 || a.rinv == 1) ? k : (int)(((unsigned)a.rinv * (unsigned)k) & (N - 1));
         v[q] = cmul(sa[s2], C::SMEM_TABLES ? pre[s2] : __ldg(pre + s2));   // the row lands unpadded
       }
       group_fft<N, T, +1, C::SMEM_TABLES>(v, sa, tw, t, group);
@@ -476,7 +483,7 @@ column_group_pipe_kernel(const float2* __restrict__ Y, const float2* __restrict_
                                                    s_rlist[group], s_rpart[group]);
       cp_async_wait<1 - R2>();              // Y(sym)
       group_sync<T>(group);
-      flags |= divide_precoded<T, E>(v, sy, true, a, t);
+      flags |= divide_precoded<T, E, R1Q0>(v, sy, true, a, t);
     } else {
       cp_async_wait<1 - R2>();              // A(sym) and Y(sym)
       group_sync<T>(group);
@@ -570,16 +577,17 @@ static cudaError_t launch_group_pipe(const float2* Y, const float2* X, float2* s
                                      const ColumnArgs& a, cudaStream_t s, unsigned long long* tickets, int sms,
                                      long total) {
   using C = GroupPipeCfg<N, TT>;
-  cudaError_t e = cudaFuncSetAttribute(column_group_pipe_kernel<N, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)C::SMEM);
+  const bool r1q0 = a.rinv == 1 && a.post_sign;
+  auto kern = r1q0 ? column_group_pipe_kernel<N, TT, true> : column_group_pipe_kernel<N, TT, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, column_group_pipe_kernel<N, TT>, C::THREADS, C::SMEM);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::THREADS, C::SMEM);
   if (e != cudaSuccess) return e;
   long blocks = (long)sms * (per_sm > 0 ? per_sm : 1);
   const long need = (total + C::GROUPS - 1) / C::GROUPS;
   if (blocks > need) blocks = need;
-  column_group_pipe_kernel<N, TT><<<(unsigned)blocks, C::THREADS, C::SMEM, s>>>(Y, X, strip, wstatus, a);
+  kern<<<(unsigned)blocks, C::THREADS, C::SMEM, s>>>(Y, X, strip, wstatus, a);
   *tickets = (unsigned long long)total + (unsigned long long)blocks * C::GROUPS;
   return cudaGetLastError();
 }

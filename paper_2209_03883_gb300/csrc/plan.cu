@@ -12,6 +12,7 @@
 
 #include "fft.cuh"
 #include "internal.h"
+#include "refine.cuh"
 
 using ofdm::ColumnArgs;
 using ofdm::DetectArgs;
@@ -87,16 +88,7 @@ struct ofdm_radar_plan {
 };
 
 namespace {
-// Precoded cells with |X_p|^2 below this fraction of the symbol's mean power
-// are recomputed in double-float (about 5e-5 of the cells for a ZC-precoded
-// QAM grid), which keeps the FP32 chain's map error within half of the 1e-5
-// gate even when the LS division meets a near-zero precoded cell.  Each
-// recomputed cell costs an N-term double-float sum, so the threshold trades
-// the column stage's time against that margin.
-#ifndef OFDM_REFINE_TAU
-#define OFDM_REFINE_TAU 5e-5f
-#endif
-constexpr float kRefineTau = OFDM_REFINE_TAU;
+
 constexpr int kMaxTimed = 4096;
 constexpr int kKinds = 8;  // column, zero_rows, doppler, detect, zct, coarse, cnn, refine
 enum { K_COLUMN = 0, K_ZERO = 1, K_DOPPLER = 2, K_DETECT = 3, K_ZCT = 4, K_COARSE = 5, K_CNN = 6, K_REFINE = 7 };
@@ -578,7 +570,7 @@ ColumnArgs column_args(const ofdm_radar_plan* pl, int frames) {
   a.tw = pl->twN;
   a.post_sign = (mod_ll(pl->p.zc_q, pl->p.N) == 0) ? 1 : 0;
   a.rprime = pl->p.zc_root > 0 ? pl->p.zc_root : 1;
-  a.refine_tau = kRefineTau;
+  a.refine_tau = ofdm::kRefineTau;
   a.pre_df = pl->d_df;
   a.w_df = pl->d_df + pl->p.N;
   a.work_ctr = pl->d_ctr + pl->ctr_slot;

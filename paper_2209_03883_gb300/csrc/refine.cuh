@@ -6,6 +6,17 @@
 
 namespace ofdm {
 
+// Precoded cells with |X_p|^2 below this fraction of the symbol's mean power
+// are recomputed in double-float (about 5e-5 of the cells for a ZC-precoded
+// QAM grid), which keeps the FP32 chain's map error within half of the 1e-5
+// gate even when the LS division meets a near-zero precoded cell.  Each
+// recomputed cell costs an N-term double-float sum, so the threshold trades
+// the column stage's time against that margin.
+#ifndef OFDM_REFINE_TAU
+#define OFDM_REFINE_TAU 5e-5f
+#endif
+constexpr float kRefineTau = OFDM_REFINE_TAU;
+
 // B_i = sum_k pre_k A_k exp(+2 pi i r' i k / N) in double-float by the whole
 // warp (lane handles k = lane, lane + 32, ...), rounded once to float.  Used
 // for precoded cells so small that the FP32 FFT's normwise rounding would be
