@@ -186,12 +186,14 @@ __device__ __forceinline__ uint32_t divide_plain(float2* v, const float2* xrow, 
 
 // Keep taps n < L_cp (Eq. (21)) and write the support rows of the windowed
 // range profile, g[r] = c0 h[r] + c1 (h[r-1] + h[r+1]) (Eqs. (17), (22)).
-template <int N, int T, int E>
+// QMAX: only v[q], q < QMAX, can hold kept taps (E, or 2 after an
+// output-pruned inverse DFT).
+template <int N, int T, int E, int QMAX = E>
 __device__ __forceinline__ uint32_t stencil_write(const float2* v, float2* sm, float2* __restrict__ strip,
                                                   const ColumnArgs& a, int f, int l, int t, int group) {
   group_sync<T>(group);  // the last FFT pass finished reading sm
 #pragma unroll
-  for (int q = 0; q < E; ++q) {
+  for (int q = 0; q < QMAX; ++q) {
     const int n = t + T * q;
     if (n < a.L_cp) sm[pad32(n)] = v[q];
   }
@@ -398,8 +400,9 @@ struct GroupPipeCfg {
 // R1Q0: instantiated for r' = 1, q' = 0 (the ZC transform's input permutation
 // is the identity and its post factor is (-1)^i): the per-point index and
 // table branches, which the unrolled loops would otherwise issue predicated,
-// are gone.
-template <int N, int TT = N / 32, bool R1Q0 = false>
+// are gone.  PRUNE: L_cp <= 2 T with 16 points per thread, so the DFT-CE
+// inverse DFT computes only the outputs q < 2 (the launcher picks the form).
+template <int N, int TT = N / 32, bool R1Q0 = false, bool PRUNE = false>
 __global__ void __launch_bounds__(GroupPipeCfg<N, TT>::THREADS, 1)
 column_group_pipe_kernel(const float2* __restrict__ Y, const float2* __restrict__ X, float2* __restrict__ strip,
                          uint32_t* __restrict__ wstatus, ColumnArgs a) {
@@ -495,14 +498,13 @@ column_group_pipe_kernel(const float2* __restrict__ Y, const float2* __restrict_
     // DFT-CE keeps taps n = t + T q < L_cp only: for N = 1024 in two-warp
     // groups and L_cp <= 128 that is q < 2, so the last pass is pruned.
     // (same for N = 2048 in four-warp groups, whose last pass is radix 8, G = 2)
-    constexpr int LASTG = E / pass_radix(N, E, num_passes(N, E) - 1);
-    if constexpr (E == 16 && LASTG >= 2) {
-      if (a.L_cp <= 2 * T) group_fft_pruned<N, T, +1, C::SMEM_TABLES, 2>(v, sa, tw, t, group);
-      else group_fft<N, T, +1, C::SMEM_TABLES>(v, sa, tw, t, group);
+    if constexpr (PRUNE) {
+      group_fft_pruned<N, T, +1, C::SMEM_TABLES, 2>(v, sa, tw, t, group);
+      flags |= stencil_write<N, T, E, 2>(v, sa, strip, a, f, l, t, group);
     } else {
       group_fft<N, T, +1, C::SMEM_TABLES>(v, sa, tw, t, group);
+      flags |= stencil_write<N, T, E>(v, sa, strip, a, f, l, t, group);
     }
-    flags |= stencil_write<N, T, E>(v, sa, strip, a, f, l, t, group);
     flags = __reduce_or_sync(0xffffffffu, flags);
     if (lane == 0 && flags) atomicOr(wstatus + f, flags);
     group_sync<T>(group);                   // every thread is done with sa before it is refilled
@@ -577,8 +579,14 @@ static cudaError_t launch_group_pipe(const float2* Y, const float2* X, float2* s
                                      const ColumnArgs& a, cudaStream_t s, unsigned long long* tickets, int sms,
                                      long total) {
   using C = GroupPipeCfg<N, TT>;
+  constexpr int E = N / TT;
+  constexpr bool CAN_PRUNE = E == 16 && E / pass_radix(N, E, num_passes(N, E) - 1) >= 2;
   const bool r1q0 = a.rinv == 1 && a.post_sign;
   auto kern = r1q0 ? column_group_pipe_kernel<N, TT, true> : column_group_pipe_kernel<N, TT, false>;
+  if constexpr (CAN_PRUNE) {
+    if (a.L_cp <= 2 * TT)
+      kern = r1q0 ? column_group_pipe_kernel<N, TT, true, true> : column_group_pipe_kernel<N, TT, false, true>;
+  }
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
