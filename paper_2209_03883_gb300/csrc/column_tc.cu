@@ -167,6 +167,10 @@ __device__ __forceinline__ void load_acc32(uint32_t taddr, float2* v) {
   tc::tmem_wait_ld();
 }
 
+// R1Q0: instantiated for r' = 1, q' = 0 (identity input permutation, post
+// factor (-1)^i), without the per-point post-chirp table multiply that the
+// unrolled division loop would otherwise issue predicated.
+template <bool R1Q0>
 __global__ void __launch_bounds__(kThreads, 1)
 column_tc_kernel(const float2* __restrict__ Y, const float2* __restrict__ X, float2* __restrict__ strip,
                  uint32_t* __restrict__ wstatus, ColumnArgs a) {
@@ -277,7 +281,7 @@ column_tc_kernel(const float2* __restrict__ Y, const float2* __restrict__ X, flo
       if (wt == 0) pendX = 0;
       // ---- stage 1: rows (symbol q, k2 = lane), K = (k1, re/im), k1 = 16 h + i
       float mx = 0.f;
-      if (a.rinv == 1) {
+      if (R1Q0 || a.rinv == 1) {
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           const int k = 32 * (16 * h + i) + lane;
@@ -375,7 +379,7 @@ column_tc_kernel(const float2* __restrict__ Y, const float2* __restrict__ X, flo
       for (int j = 0; j < 16; ++j) {
         const int i = lane + 32 * (16 * h + j);
         float2 yv = Ys[i];
-        if (a.zc && !a.post_sign) yv = cmul(yv, __ldg(a.post_conj + i));
+        if (!R1Q0 && a.zc && !a.post_sign) yv = cmul(yv, __ldg(a.post_conj + i));
         const float d2 = v[j].x * v[j].x + v[j].y * v[j].y;
         flags |= (d2 == 0.f) ? OFDM_STATUS_ZERO_X : 0u;
         const float inv = (d2 > 0.f) ? mul * rcp_fast(d2) : 0.f;
@@ -530,7 +534,8 @@ void build_tc_tables(unsigned char* b, float2* t12) {
 cudaError_t launch_column_tc(const float2* Y, const float2* X, float2* strip, uint32_t* wstatus, const ColumnArgs& a,
                              cudaStream_t s, unsigned long long* tickets) {
   *tickets = 0;
-  cudaError_t e = cudaFuncSetAttribute(column_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+  auto kern = (a.rinv == 1 && a.post_sign) ? column_tc_kernel<true> : column_tc_kernel<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -539,7 +544,7 @@ cudaError_t launch_column_tc(const float2* Y, const float2* X, float2* strip, ui
   long blocks = sms;
   const long need = (tiles + kWG - 1) / kWG;
   if (blocks > need) blocks = need;
-  column_tc_kernel<<<(unsigned)blocks, kThreads, kSmemBytes, s>>>(Y, X, strip, wstatus, a);
+  kern<<<(unsigned)blocks, kThreads, kSmemBytes, s>>>(Y, X, strip, wstatus, a);
   *tickets = (unsigned long long)tiles + (unsigned long long)blocks * kWG;
   return cudaGetLastError();
 }
