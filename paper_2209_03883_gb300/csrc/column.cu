@@ -1,8 +1,12 @@
 // column.cu -- the per-OFDM-symbol half of the chain (steps a1-a5) and the
 // stand-alone ZC transform.
 //
-// One thread group (a warp for N <= 1024, N/32 threads above) owns one OFDM
-// symbol l of one frame at a time:
+// One thread group owns one OFDM symbol l of one frame at a time: a warp for
+// N <= 512 (and the one-warp form at N = 1024), N/16 threads with 16 points
+// each for N >= 1024 (the default), N/32 threads in the no-allocation path.
+// The group kernel is instantiated for the default ZC parameters (r' = 1,
+// q' = 0) and for the output-pruned inverse DFT (L_cp <= 2 T) as well as in
+// general form, so that its unrolled loops carry no per-point runtime choice.
 //   1. load the known grid X[l, :] (coalesced, streaming) and apply the ZC
 //      transform of Sec. III-B, X_p = Z_m A / sqrt(N), written as
 //      pre-chirp -> N-point DFT (+) -> post factor (Eqs. (23)-(24));
