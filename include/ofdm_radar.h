@@ -253,8 +253,11 @@ int ofdm_radar_batch_process(ofdm_radar_batch* b, const ofdm_c32* Y, const ofdm_
                              ofdm_target* out_targets, int32_t* n_targets, uint32_t* status, void* stream);
 
 /* Number of groups and, if shapes != NULL, [groups][5] = N, M, L_cp, frames,
- * chosen column-kernel variant (0 = widest CTA, 4 = 4-warp CTAs, -1 = not
- * tuned yet / not applicable).  Returns the group count. */
+ * chosen column-kernel variant: for N <= 1024, 0 = one warp per symbol in the
+ * widest CTA, 4 = one warp per symbol in 4-warp CTAs, 2 = groups of N / 16
+ * threads (N = 1024); for N >= 2048, 2 = groups of N / 16 threads (16 points
+ * each), 0 = groups of N / 32 threads (32 points each); -1 = not tuned yet.
+ * Returns the group count. */
 int ofdm_radar_batch_groups(const ofdm_radar_batch* b, int32_t* shapes);
 
 /* 1 if the last ofdm_radar_batch_process replayed or captured a graph, 0 if

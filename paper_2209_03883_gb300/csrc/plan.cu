@@ -1071,9 +1071,14 @@ cudaError_t tune_group(BatchGroup& g, const float2* Y, const float2* X, cudaStre
     auto it = g_tune.find(key);
     if (it != g_tune.end()) { g.pipe_warps = it->second; return cudaSuccess; }
   }
-  if (g.N > 1024) { g.pipe_warps = -1; return cudaSuccess; }
-  const int variants[3] = {0, 4, 2};   // widest one-warp CTA, 4-warp CTAs, two-warp groups (N = 1024)
-  const int nvar = g.plan->twG ? 3 : 2;
+  // N <= 1024: the widest one-warp CTA, 4-warp CTAs, or (N = 1024) groups of
+  // N / 16 threads; N >= 2048: groups of N / 16 threads with 16 points each
+  // or of N / 32 threads with 32 points each (points per thread, and with
+  // them the FFT's pass radices, exchanges and registers).
+  const int small_variants[3] = {0, 4, 2}, big_variants[2] = {2, 0};
+  const bool big = g.N > 1024;
+  const int* variants = big ? big_variants : small_variants;
+  const int nvar = big ? 2 : (g.plan->twG ? 3 : 2);
   float best = 1e30f;
   int pick = 0;
   cudaEvent_t e0, e1;
