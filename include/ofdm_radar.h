@@ -381,10 +381,12 @@ int ofdm_radar_process_noalloc(const ofdm_radar_params* p, const ofdm_c32* Y, co
  * which has no software).  Every device buffer the library allocates -- plan
  * tables and workspace, the host path's staging buffers, batch offset tables
  * -- ends in a 256-byte canary of 0xFF bytes (a NaN for float data) that no
- * kernel writes.  Returns 1 if the canary of every live buffer is intact, 0 if
- * some launch wrote past the end of one, or a negative OFDM_ERR_* code.
- * Waits for all work on the current device (cudaDeviceSynchronize) and copies
- * 256 bytes per buffer to the host: not for the timed path. */
+ * kernel writes.  Returns 1 if the canary of every live buffer on the current
+ * device is intact, 0 if some launch wrote past the end of one, or a negative
+ * OFDM_ERR_* code.  Waits for all work on the current device
+ * (cudaDeviceSynchronize) and copies 256 bytes per buffer to the host: not for
+ * the timed path.  Buffers on other devices are checked with that device
+ * current. */
 int ofdm_radar_workspace_intact(void);
 
 /* Static description of an error code; for OFDM_ERR_CUDA the last CUDA

@@ -168,7 +168,7 @@ int column_points_per_thread(int N) { return N <= 1024 ? N / 32 : 32; }
 // end of its buffer.  The tail also covers reads of up to 16 bytes past it.
 constexpr size_t kCanaryBytes = 256;
 std::mutex g_canary_mu;
-std::map<const char*, size_t> g_canary;   // allocation -> bytes before its canary
+std::map<const char*, std::pair<size_t, int>> g_canary;   // allocation -> (bytes before its canary, device)
 
 template <class T>
 cudaError_t dalloc(T** p, size_t count) {
@@ -181,8 +181,10 @@ cudaError_t dalloc(T** p, size_t count) {
     *p = nullptr;
     return e;
   }
+  int dev = 0;
+  cudaGetDevice(&dev);
   std::lock_guard<std::mutex> lk(g_canary_mu);
-  g_canary[reinterpret_cast<const char*>(*p)] = bytes;
+  g_canary[reinterpret_cast<const char*>(*p)] = std::make_pair(bytes, dev);
   return cudaSuccess;
 }
 
@@ -230,12 +232,15 @@ const char* ofdm_radar_strerror(int code) {
 }
 
 int ofdm_radar_workspace_intact(void) {
-  cudaError_t e = cudaDeviceSynchronize();
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail(e);
   std::lock_guard<std::mutex> lk(g_canary_mu);
   unsigned char tail[kCanaryBytes];
   for (const auto& a : g_canary) {
-    e = cudaMemcpy(tail, a.first + a.second, kCanaryBytes, cudaMemcpyDeviceToHost);
+    if (a.second.second != dev) continue;   // other devices' work is not synchronised here
+    e = cudaMemcpy(tail, a.first + a.second.first, kCanaryBytes, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e);
     for (size_t i = 0; i < kCanaryBytes; ++i)
       if (tail[i] != 0xFF) return 0;

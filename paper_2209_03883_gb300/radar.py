@@ -352,8 +352,8 @@ def targets_view(raw, frames, max_targets):
 # ------------------------------------------------------------- torch helpers
 def ofdm_radar_workspace_intact() -> bool:
     """True if no launch wrote past the end of any device buffer the library
-    allocated (the 256-byte canaries behind every plan and batch buffer).
-    Waits for all work on the current device."""
+    allocated on the current device (the 256-byte canaries behind every plan
+    and batch buffer).  Waits for all work on the current device."""
     return _check(_lib.ofdm_radar_workspace_intact(), "ofdm_radar_workspace_intact") == 1
 
 
